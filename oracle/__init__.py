@@ -1,0 +1,237 @@
+"""CPU oracle for deterministic Jet refinement -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The CUDA
+library never calls it, and the two share no code.
+
+``jet_oracle.c`` is plain single-threaded integer C that follows the paper
+(arXiv 2504.12013) step by step: Section 2 (definitions), Algorithm 1 (Jet
+loop), Algorithm 2 (hypergraph afterburner), Section 4.3 (deterministic
+rebalancing) and the schedule of Section 7.2.  Its readings of points the
+paper leaves open are listed in the C file's header (R1..R12).
+
+Parity pins: every oracle function is checked by ``tests/test_oracle_pins.py``
+against brute force, closed forms, invariants and hand-worked fixtures.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jet_oracle.c")
+_lock = threading.Lock()
+_libs: dict = {}
+
+I32P = ctypes.POINTER(ctypes.c_int32)
+I64P = ctypes.POINTER(ctypes.c_int64)
+U8P = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(source=None, force: bool = False) -> str:
+    """Compile the oracle (or a variant source file, used by the mutation tests)."""
+    src = source or _SRC
+    if source is None:
+        out = os.path.join(_HERE, "_build", "libjet_oracle.so")
+    else:
+        out = os.path.join(os.path.dirname(os.path.abspath(source)), "libjet_oracle_variant.so")
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, out)
+    return out
+
+
+class OHG(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("m", ctypes.c_int32), ("P", ctypes.c_int64),
+        ("eptr", I64P), ("pins", I32P), ("vptr", I64P), ("inc", I32P), ("vwgt", I32P), ("ewgt", I32P),
+    ]
+
+
+class OParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("eps_num", ctypes.c_int32), ("eps_den", ctypes.c_int32),
+                ("d_num", ctypes.c_int32), ("d_den", ctypes.c_int32), ("max_rebalance_rounds", ctypes.c_int32)]
+
+
+class OStats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int64), ("approved", ctypes.c_int64),
+                ("rebalance_rounds", ctypes.c_int64), ("rebalance_moves", ctypes.c_int64),
+                ("objective", ctypes.c_int64), ("max_block_weight", ctypes.c_int64),
+                ("imbalanced", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+def load(source=None):
+    key = source
+    with _lock:
+        if key not in _libs:
+            lib = ctypes.CDLL(build(source))
+            H, Pp, S = ctypes.POINTER(OHG), ctypes.POINTER(OParams), ctypes.POINTER(OStats)
+            i32, i64 = ctypes.c_int32, ctypes.c_int64
+            lib.ojet_total_weight.argtypes = [H]; lib.ojet_total_weight.restype = i64
+            lib.ojet_avg_block.argtypes = [H, i32]; lib.ojet_avg_block.restype = i64
+            lib.ojet_lmax.argtypes = [H, Pp]; lib.ojet_lmax.restype = i64
+            lib.ojet_pincounts.argtypes = [H, i32, I32P, I32P, I64P]; lib.ojet_pincounts.restype = None
+            lib.ojet_connectivity.argtypes = [H, i32, I32P]; lib.ojet_connectivity.restype = i64
+            lib.ojet_gain.argtypes = [H, i32, I32P, I32P, i32, i32]; lib.ojet_gain.restype = i64
+            lib.ojet_affinity.argtypes = [H, i32, I32P, I32P, i32]; lib.ojet_affinity.restype = i64
+            lib.ojet_candidates.argtypes = [H, i32, I32P, I32P, U8P, i32, i32, I32P, I64P, U8P]
+            lib.ojet_candidates.restype = i64
+            lib.ojet_afterburner.argtypes = [H, i32, I32P, I32P, I32P, I64P, U8P, I64P, U8P]
+            lib.ojet_afterburner.restype = i64
+            lib.ojet_apply.argtypes = [H, i32, I32P, I32P, I64P, U8P, I32P]; lib.ojet_apply.restype = None
+            lib.ojet_rebalance_round.argtypes = [H, Pp, I32P, I32P, I64P, U8P, I32P]
+            lib.ojet_rebalance_round.restype = i64
+            lib.ojet_rebalance.argtypes = [H, Pp, I32P, I32P, I64P, I64P]; lib.ojet_rebalance.restype = i64
+            lib.ojet_refine_round.argtypes = [H, Pp, i32, i32, I32P, I32P, I64P, U8P, S]
+            lib.ojet_refine_round.restype = None
+            lib.ojet_refine.argtypes = [H, Pp, I32P, i32, i32, I32P, I64P, I64P]; lib.ojet_refine.restype = i64
+            _libs[key] = lib
+    return _libs[key]
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+@dataclass
+class Params:
+    k: int
+    eps: tuple = (3, 100)
+    d: tuple = (1, 10)
+    max_rebalance_rounds: int = 32
+
+    def c(self) -> OParams:
+        return OParams(self.k, self.eps[0], self.eps[1], self.d[0], self.d[1], self.max_rebalance_rounds)
+
+
+TAU_SCHEDULE = ((3, 4), (3, 8), (0, 1))  # three temperatures 0.75 -> 0, equidistant (Section 7.2)
+ITERATION_LIMIT = 8                      # iterations without improvement (Section 7.2)
+
+
+class Oracle:
+    """Bound oracle for one hypergraph.  Arrays are numpy; state is updated in place."""
+
+    def __init__(self, hg, source=None):
+        self.lib = load(source)
+        self.source = source
+        self.hg = hg
+        # keep contiguous copies alive
+        self._arrs = [np.ascontiguousarray(a) for a in (hg.eptr, hg.pins, hg.vptr, hg.inc, hg.vwgt, hg.ewgt)]
+        e, p, vp, inc, vw, ew = self._arrs
+        self.h = OHG(hg.n, hg.m, int(e[-1]) if e.size else 0, _p(e, I64P), _p(p, I32P), _p(vp, I64P),
+                     _p(inc, I32P), _p(vw, I32P), _p(ew, I32P))
+
+    # Section 2
+    def total_weight(self):
+        return self.lib.ojet_total_weight(ctypes.byref(self.h))
+
+    def avg_block(self, k):
+        return self.lib.ojet_avg_block(ctypes.byref(self.h), k)
+
+    def lmax(self, params: Params):
+        return self.lib.ojet_lmax(ctypes.byref(self.h), ctypes.byref(params.c()))
+
+    def pincounts(self, k, part):
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        phi = np.zeros(self.hg.m * k, dtype=np.int32)
+        bw = np.zeros(k, dtype=np.int64)
+        self.lib.ojet_pincounts(ctypes.byref(self.h), k, _p(part, I32P), _p(phi, I32P), _p(bw, I64P))
+        return phi.reshape(self.hg.m, k), bw
+
+    def connectivity(self, k, phi):
+        phi = np.ascontiguousarray(phi, dtype=np.int32)
+        return self.lib.ojet_connectivity(ctypes.byref(self.h), k, _p(phi, I32P))
+
+    def objective(self, k, part):
+        return self.connectivity(k, self.pincounts(k, part)[0])
+
+    def gain(self, k, part, phi, v, b):
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        phi = np.ascontiguousarray(phi, dtype=np.int32)
+        return self.lib.ojet_gain(ctypes.byref(self.h), k, _p(part, I32P), _p(phi, I32P), v, b)
+
+    def affinity(self, k, part, phi, v):
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        phi = np.ascontiguousarray(phi, dtype=np.int32)
+        return self.lib.ojet_affinity(ctypes.byref(self.h), k, _p(part, I32P), _p(phi, I32P), v)
+
+    # Section 4.1
+    def candidates(self, k, part, phi, locked, tau):
+        n = self.hg.n
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        phi = np.ascontiguousarray(phi, dtype=np.int32)
+        locked = np.ascontiguousarray(locked, dtype=np.uint8)
+        target = np.empty(n, np.int32); gain = np.empty(n, np.int64); in_m = np.empty(n, np.uint8)
+        cnt = self.lib.ojet_candidates(ctypes.byref(self.h), k, _p(part, I32P), _p(phi, I32P), _p(locked, U8P),
+                                       tau[0], tau[1], _p(target, I32P), _p(gain, I64P), _p(in_m, U8P))
+        return cnt, target, gain, in_m
+
+    # Section 4.2
+    def afterburner(self, k, part, phi, target, gain, in_m):
+        n = self.hg.n
+        part = np.ascontiguousarray(part, dtype=np.int32)
+        phi = np.ascontiguousarray(phi, dtype=np.int32)
+        target = np.ascontiguousarray(target, dtype=np.int32)
+        gain = np.ascontiguousarray(gain, dtype=np.int64)
+        in_m = np.ascontiguousarray(in_m, dtype=np.uint8)
+        rg = np.empty(n, np.int64); approved = np.empty(n, np.uint8)
+        cnt = self.lib.ojet_afterburner(ctypes.byref(self.h), k, _p(part, I32P), _p(phi, I32P), _p(target, I32P),
+                                        _p(gain, I64P), _p(in_m, U8P), _p(rg, I64P), _p(approved, U8P))
+        return cnt, rg, approved
+
+    def apply(self, k, part, phi, bw, move, target):
+        """In place on part (int32[n]), phi (int32[m,k]), bw (int64[k])."""
+        move = np.ascontiguousarray(move, dtype=np.uint8)
+        target = np.ascontiguousarray(target, dtype=np.int32)
+        self.lib.ojet_apply(ctypes.byref(self.h), k, _p(part, I32P), _p(phi, I32P), _p(bw, I64P), _p(move, U8P),
+                            _p(target, I32P))
+
+    # Section 4.3
+    def rebalance_round(self, params: Params, part, phi, bw):
+        n = self.hg.n
+        flag = np.empty(n, np.uint8); tgt = np.empty(n, np.int32)
+        moved = self.lib.ojet_rebalance_round(ctypes.byref(self.h), ctypes.byref(params.c()), _p(part, I32P),
+                                              _p(phi, I32P), _p(bw, I64P), _p(flag, U8P), _p(tgt, I32P))
+        return moved, flag, tgt
+
+    def rebalance(self, params: Params, part, phi, bw):
+        moves = ctypes.c_int64(0)
+        rounds = self.lib.ojet_rebalance(ctypes.byref(self.h), ctypes.byref(params.c()), _p(part, I32P),
+                                         _p(phi, I32P), _p(bw, I64P), ctypes.byref(moves))
+        return rounds, moves.value
+
+    # Algorithm 1
+    def refine_round(self, params: Params, tau, part, phi, bw, locked):
+        st = OStats()
+        self.lib.ojet_refine_round(ctypes.byref(self.h), ctypes.byref(params.c()), tau[0], tau[1], _p(part, I32P),
+                                   _p(phi, I32P), _p(bw, I64P), _p(locked, U8P), ctypes.byref(st))
+        return st.as_dict()
+
+    def refine(self, params: Params, part, schedule=TAU_SCHEDULE, limit=ITERATION_LIMIT):
+        pairs = np.array([x for t in schedule for x in t], dtype=np.int32)
+        obj = ctypes.c_int64(0)
+        phase = np.zeros(len(schedule), np.int64)
+        iters = self.lib.ojet_refine(ctypes.byref(self.h), ctypes.byref(params.c()), _p(pairs, I32P),
+                                     len(schedule), limit, _p(part, I32P), ctypes.byref(obj), _p(phase, I64P))
+        return iters, obj.value, phase
+
+
+class State:
+    """Mutable Jet state (Pi, phi, c(V_i), locks) for stepping the oracle round by round."""
+
+    def __init__(self, orc: Oracle, k: int, part):
+        self.part = np.array(part, dtype=np.int32, copy=True)
+        phi, bw = orc.pincounts(k, self.part)
+        self.phi = np.ascontiguousarray(phi)
+        self.bw = bw
+        self.locked = np.zeros(orc.hg.n, dtype=np.uint8)

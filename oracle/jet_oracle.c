@@ -1,0 +1,461 @@
+/*
+ * CPU ORACLE for deterministic Jet refinement (connectivity metric).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this code.  The product path (the
+ * CUDA library) never calls it and shares no code, header, table or constant
+ * with it.
+ *
+ * Plain, slow, single-threaded, integer-only.  Every function follows the
+ * paper (arXiv 2504.12013) step by step, in its order and notation:
+ *   Section 2 ("Preliminaries")         hypergraph, partition, balance, (lambda-1)
+ *   Section 4.1, Algorithm 1            Jet loop: candidates, afterburner, apply, rebalance
+ *   Section 4.2, Algorithm 2            hypergraph afterburner (sort + replay)
+ *   Section 4.3                         deterministic rebalancing, deadzone, heavy vertices
+ *   Section 7.2                         three temperatures 0.75 -> 0, 8 iterations
+ * Readings where the paper is silent or ambiguous (each marked READING below):
+ *   R1  blocks are 0-based, [k] = {0..k-1}.
+ *   R2  L_max = floor((1+eps) * ceil(c(V)/k)), eps = eps_num/eps_den exactly.
+ *   R3  gain(v,b) is the connectivity gain: sum over e in I(v) of
+ *       omega(e) * ([phi_e(s) = 1] - [phi_e(b) = 0]), s = Pi(v)  (the +-omega
+ *       rule of Algorithm 2).
+ *   R4  move candidates consider blocks b != s adjacent to v (phi_e(b) >= 1 for
+ *       some e in I(v)); t(v) = argmax gain, ties to the smallest block id; a
+ *       vertex with no adjacent block is not a candidate.
+ *   R5  the temperature test is  gain >= -tau * A(v)  with tau = tau_num/tau_den
+ *       and A(v) = sum of omega(e) over e in I(v) with |e cap V_s| > 1,
+ *       evaluated exactly in integers.
+ *   R6  the afterburner order is gain descending, ties to the smaller vertex id.
+ *   R7  locking: the vertices moved by the afterburner-approved moves of an
+ *       iteration are excluded from the candidates of the next iteration; the
+ *       rebalancer ignores locks; locks are cleared at the start of each
+ *       temperature phase.
+ *   R8  rebalancing targets: all blocks b != s with c(V_b) + c(v) <= L_max that
+ *       are not in the deadzone (c(V_b) >= L_max - d*eps*ceil(c(V)/k), with the
+ *       real-valued L_max = (1+eps)*ceil(c(V)/k), compared exactly); ties of the
+ *       best gain go to the smallest block id; non-adjacent blocks count.
+ *   R9  rebalancing priority: gain*c(v) if gain >= 0, gain/c(v) otherwise,
+ *       compared exactly; every gain >= 0 vertex precedes every gain < 0 one;
+ *       ties to the smaller vertex id; per overloaded block the minimal prefix
+ *       of this order whose weight reaches c(V_s) - L_max is moved (all
+ *       candidates if the prefix never reaches it).
+ *   R10 rebalancing rounds stop when no block is overloaded, when a round moves
+ *       nothing, or after max_rebalance_rounds rounds.
+ *   R11 "quality improved" means balanced and strictly smaller (lambda-1) than
+ *       the best balanced partition seen so far; at the end of each temperature
+ *       phase the best balanced partition is restored (rollback).
+ *   R12 an empty hyperedge contributes 0 to (lambda-1).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+  int32_t n, m;
+  int64_t P;
+  const int64_t *eptr; /* pins of e: pins[eptr[e] .. eptr[e+1]) */
+  const int32_t *pins;
+  const int64_t *vptr; /* I(v): inc[vptr[v] .. vptr[v+1]) */
+  const int32_t *inc;
+  const int32_t *vwgt; /* c(v)     */
+  const int32_t *ewgt; /* omega(e) */
+} ojet_hg;
+
+typedef struct {
+  int32_t k;
+  int32_t eps_num, eps_den;
+  int32_t d_num, d_den;
+  int32_t max_rebalance_rounds;
+} ojet_params;
+
+typedef struct {
+  int64_t candidates;       /* |M| after the temperature filter      */
+  int64_t approved;         /* moves kept by the afterburner          */
+  int64_t rebalance_rounds; /* rounds that found an overloaded block  */
+  int64_t rebalance_moves;  /* vertices moved by the rebalancer       */
+  int64_t objective;        /* (lambda-1) after the iteration         */
+  int64_t max_block_weight;
+  int64_t imbalanced;       /* 1 if some block is above L_max          */
+} ojet_stats;
+
+/* ------------------------------------------------------------ Section 2 */
+
+/* c(V) */
+int64_t ojet_total_weight(const ojet_hg *h) {
+  int64_t W = 0;
+  for (int32_t v = 0; v < h->n; ++v) W += h->vwgt[v];
+  return W;
+}
+
+/* ceil(c(V)/k), the average block weight rounded up (Section 2, R2) */
+int64_t ojet_avg_block(const ojet_hg *h, int32_t k) {
+  int64_t W = ojet_total_weight(h);
+  return (W + k - 1) / k;
+}
+
+/* L_max = floor((1 + eps) * ceil(c(V)/k))  (Section 2, R2) */
+int64_t ojet_lmax(const ojet_hg *h, const ojet_params *p) {
+  __int128 A = ojet_avg_block(h, p->k);
+  return (int64_t)(((__int128)(p->eps_den + p->eps_num) * A) / p->eps_den);
+}
+
+/* phi_e[i] = |e cap V_i| for every edge and block; c(V_i) for every block (Section 2) */
+void ojet_pincounts(const ojet_hg *h, int32_t k, const int32_t *part, int32_t *phi, int64_t *bw) {
+  memset(phi, 0, sizeof(int32_t) * (size_t)h->m * (size_t)k);
+  for (int32_t e = 0; e < h->m; ++e)
+    for (int64_t p = h->eptr[e]; p < h->eptr[e + 1]; ++p) phi[(int64_t)e * k + part[h->pins[p]]] += 1;
+  for (int32_t b = 0; b < k; ++b) bw[b] = 0;
+  for (int32_t v = 0; v < h->n; ++v) bw[part[v]] += h->vwgt[v];
+}
+
+/* (lambda-1)(Pi) = sum_e (lambda(e) - 1) omega(e), lambda(e) = |{i : phi_e[i] > 0}| (Section 2, R12) */
+int64_t ojet_connectivity(const ojet_hg *h, int32_t k, const int32_t *phi) {
+  int64_t total = 0;
+  for (int32_t e = 0; e < h->m; ++e) {
+    int64_t lambda = 0;
+    for (int32_t b = 0; b < k; ++b)
+      if (phi[(int64_t)e * k + b] > 0) lambda += 1;
+    if (lambda > 0) total += (lambda - 1) * (int64_t)h->ewgt[e];
+  }
+  return total;
+}
+
+/* gain of moving v from its block to b (Section 4.1 "gain", R3) */
+int64_t ojet_gain(const ojet_hg *h, int32_t k, const int32_t *part, const int32_t *phi, int32_t v, int32_t b) {
+  int32_t s = part[v];
+  int64_t g = 0;
+  for (int64_t j = h->vptr[v]; j < h->vptr[v + 1]; ++j) {
+    int32_t e = h->inc[j];
+    if (phi[(int64_t)e * k + s] == 1) g += h->ewgt[e];
+    if (phi[(int64_t)e * k + b] == 0) g -= h->ewgt[e];
+  }
+  return g;
+}
+
+/* A(v) = sum of omega(e), e in I(v), with |e cap V_s| > 1  (threshold of Section 4.1, R5) */
+int64_t ojet_affinity(const ojet_hg *h, int32_t k, const int32_t *part, const int32_t *phi, int32_t v) {
+  int32_t s = part[v];
+  int64_t a = 0;
+  for (int64_t j = h->vptr[v]; j < h->vptr[v + 1]; ++j) {
+    int32_t e = h->inc[j];
+    if (phi[(int64_t)e * k + s] > 1) a += h->ewgt[e];
+  }
+  return a;
+}
+
+/* ------------------------------------------------------------ Section 4.1 */
+
+/*
+ * ComputeMoveCandidates (Section 4.1): for every unlocked v, the target t(v)
+ * with the highest gain ignoring balance (R4), against the current partition
+ * as if no other vertex moved; v joins M iff gain >= -tau * A(v) (R5).
+ * Returns |M|.  target[v]/gain[v] hold t(v) and its gain for every unlocked
+ * vertex with an adjacent block (in M or not); target[v] = -1 otherwise.
+ */
+int64_t ojet_candidates(const ojet_hg *h, int32_t k, const int32_t *part, const int32_t *phi, const uint8_t *locked,
+                        int32_t tau_num, int32_t tau_den, int32_t *target, int64_t *gain, uint8_t *in_m) {
+  uint8_t *adjacent = (uint8_t *)malloc((size_t)k);
+  int64_t count = 0;
+  for (int32_t v = 0; v < h->n; ++v) {
+    target[v] = -1;
+    gain[v] = 0;
+    in_m[v] = 0;
+    if (locked[v]) continue;
+    int32_t s = part[v];
+    memset(adjacent, 0, (size_t)k);
+    for (int64_t j = h->vptr[v]; j < h->vptr[v + 1]; ++j) {
+      int32_t e = h->inc[j];
+      for (int32_t b = 0; b < k; ++b)
+        if (phi[(int64_t)e * k + b] > 0) adjacent[b] = 1;
+    }
+    int32_t best = -1;
+    int64_t best_gain = 0;
+    for (int32_t b = 0; b < k; ++b) {
+      if (b == s || !adjacent[b]) continue;
+      int64_t g = ojet_gain(h, k, part, phi, v, b);
+      if (best < 0 || g > best_gain) { best = b; best_gain = g; }
+    }
+    if (best < 0) continue;
+    int64_t A = ojet_affinity(h, k, part, phi, v);
+    target[v] = best;
+    gain[v] = best_gain;
+    if ((__int128)tau_den * best_gain >= -(__int128)tau_num * A) {
+      in_m[v] = 1;
+      count += 1;
+    }
+  }
+  free(adjacent);
+  return count;
+}
+
+/* ------------------------------------------------------------ Section 4.2 */
+
+typedef struct { int64_t gain; int32_t v; } ab_item;
+
+/* the move order of M: gain descending, ties to the smaller vertex id (R6) */
+static int ab_order(const void *a, const void *b) {
+  const ab_item *x = (const ab_item *)a, *y = (const ab_item *)b;
+  if (x->gain != y->gain) return x->gain > y->gain ? -1 : 1;
+  return (x->v > y->v) - (x->v < y->v);
+}
+
+/*
+ * Hypergraph afterburner (Algorithm 2).  For every edge: start from the pin
+ * counts of the current partition, sort e cap M by the move order, replay the
+ * moves; a pin whose departure empties its block in e earns +omega(e), a pin
+ * whose arrival makes its target non-empty in e pays -omega(e).  Every earlier
+ * pin of M counts as moved, whether or not it is approved itself.
+ * rg[] receives the recomputed gains; approved[v] = v in M and rg[v] > 0.
+ * Returns the number of approved moves.
+ */
+int64_t ojet_afterburner(const ojet_hg *h, int32_t k, const int32_t *part, const int32_t *phi, const int32_t *target,
+                         const int64_t *gain, const uint8_t *in_m, int64_t *rg, uint8_t *approved) {
+  int32_t *phi_e = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+  int64_t max_size = 0;
+  for (int32_t e = 0; e < h->m; ++e)
+    if (h->eptr[e + 1] - h->eptr[e] > max_size) max_size = h->eptr[e + 1] - h->eptr[e];
+  ab_item *L = (ab_item *)malloc(sizeof(ab_item) * (size_t)(max_size > 0 ? max_size : 1));
+  for (int32_t v = 0; v < h->n; ++v) rg[v] = 0;
+  for (int32_t e = 0; e < h->m; ++e) {
+    for (int32_t b = 0; b < k; ++b) phi_e[b] = phi[(int64_t)e * k + b];
+    int64_t len = 0;
+    for (int64_t p = h->eptr[e]; p < h->eptr[e + 1]; ++p) {
+      int32_t v = h->pins[p];
+      if (in_m[v]) { L[len].gain = gain[v]; L[len].v = v; ++len; }
+    }
+    qsort(L, (size_t)len, sizeof(ab_item), ab_order);
+    for (int64_t i = 0; i < len; ++i) {
+      int32_t v = L[i].v;
+      phi_e[part[v]] -= 1;
+      if (phi_e[part[v]] == 0) rg[v] += h->ewgt[e];
+      phi_e[target[v]] += 1;
+      if (phi_e[target[v]] == 1) rg[v] -= h->ewgt[e];
+    }
+  }
+  int64_t count = 0;
+  for (int32_t v = 0; v < h->n; ++v) {
+    approved[v] = (uint8_t)(in_m[v] && rg[v] > 0);
+    count += approved[v];
+  }
+  free(phi_e);
+  free(L);
+  return count;
+}
+
+/* ApplyMoves (Algorithm 1): move every flagged v to target[v] at once; update phi and c(V_i). */
+void ojet_apply(const ojet_hg *h, int32_t k, int32_t *part, int32_t *phi, int64_t *bw, const uint8_t *move,
+                const int32_t *target) {
+  for (int32_t v = 0; v < h->n; ++v) {
+    if (!move[v]) continue;
+    int32_t s = part[v], t = target[v];
+    for (int64_t j = h->vptr[v]; j < h->vptr[v + 1]; ++j) {
+      int32_t e = h->inc[j];
+      phi[(int64_t)e * k + s] -= 1;
+      phi[(int64_t)e * k + t] += 1;
+    }
+    bw[s] -= h->vwgt[v];
+    bw[t] += h->vwgt[v];
+    part[v] = t;
+  }
+}
+
+/* ------------------------------------------------------------ Section 4.3 */
+
+/* deadzone test: c(V_b) >= L_max - d*eps*ceil(c(V)/k) with the real L_max = (1+eps)ceil(c(V)/k) (R8) */
+static int in_deadzone(const ojet_params *p, int64_t A, int64_t bwb) {
+  __int128 lhs = (__int128)p->eps_den * p->d_den * bwb;
+  __int128 rhs = (__int128)p->d_den * (p->eps_den + p->eps_num) * A - (__int128)p->d_num * p->eps_num * A;
+  return lhs >= rhs;
+}
+
+typedef struct { int64_t gain; int32_t c; int32_t v; int32_t t; } rb_item;
+
+/* priority order (R9): higher priority first, ties to the smaller vertex id */
+static int rb_order(const void *a, const void *b) {
+  const rb_item *x = (const rb_item *)a, *y = (const rb_item *)b;
+  int cx = x->gain >= 0, cy = y->gain >= 0;
+  if (cx != cy) return cx ? -1 : 1;
+  __int128 lx, ly;
+  if (cx) { /* gain * c(v) */
+    lx = (__int128)x->gain * x->c;
+    ly = (__int128)y->gain * y->c;
+  } else { /* gain / c(v):  gx/cx > gy/cy  <=>  gx*cy > gy*cx  (c > 0) */
+    lx = (__int128)x->gain * y->c;
+    ly = (__int128)y->gain * x->c;
+  }
+  if (lx != ly) return lx > ly ? -1 : 1;
+  return (x->v > y->v) - (x->v < y->v);
+}
+
+/*
+ * One rebalancing round (Section 4.3), computed from the state at the start
+ * of the round.  Per vertex v of an overloaded block s that is not too heavy
+ * (2 c(v) <= 3 (c(V_s) - ceil(c(V)/k))): its best valid target (R8) and
+ * priority (R9).  Per overloaded block: sort by priority, prefix sums of c(v),
+ * the minimal prefix restoring balance.  All selected vertices move at once.
+ * Returns the number of moved vertices, or -1 if no block is overloaded.
+ * moved_flag/moved_target (n entries, may be NULL) receive the selection.
+ */
+int64_t ojet_rebalance_round(const ojet_hg *h, const ojet_params *p, int32_t *part, int32_t *phi, int64_t *bw,
+                             uint8_t *moved_flag, int32_t *moved_target) {
+  const int32_t k = p->k;
+  const int64_t A = ojet_avg_block(h, k);
+  const int64_t Lmax = ojet_lmax(h, p);
+  int any = 0;
+  for (int32_t b = 0; b < k; ++b) any |= bw[b] > Lmax;
+  if (moved_flag) memset(moved_flag, 0, (size_t)h->n);
+  if (!any) return -1;
+
+  int64_t *cnt = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+  for (int32_t v = 0; v < h->n; ++v) cnt[part[v]] += 1;
+  rb_item **list = (rb_item **)calloc((size_t)k, sizeof(rb_item *));
+  int64_t *len = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+  for (int32_t b = 0; b < k; ++b)
+    if (bw[b] > Lmax) list[b] = (rb_item *)malloc(sizeof(rb_item) * (size_t)(cnt[b] > 0 ? cnt[b] : 1));
+
+  for (int32_t v = 0; v < h->n; ++v) {
+    int32_t s = part[v];
+    if (bw[s] <= Lmax) continue;
+    int64_t c = h->vwgt[v];
+    if (2 * c > 3 * (bw[s] - A)) continue; /* heavy vertex: never moved */
+    int32_t best = -1;
+    int64_t best_gain = 0;
+    for (int32_t b = 0; b < k; ++b) {
+      if (b == s) continue;
+      if (bw[b] + c > Lmax) continue;
+      if (in_deadzone(p, A, bw[b])) continue;
+      int64_t g = ojet_gain(h, k, part, phi, v, b);
+      if (best < 0 || g > best_gain) { best = b; best_gain = g; }
+    }
+    if (best < 0) continue;
+    rb_item it = {best_gain, (int32_t)c, v, best};
+    list[s][len[s]++] = it;
+  }
+
+  size_t nn = (size_t)(h->n > 0 ? h->n : 1);
+  uint8_t *mv = (uint8_t *)calloc(nn, 1);
+  int32_t *tg = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int64_t moved = 0;
+  for (int32_t s = 0; s < k; ++s) {
+    if (!list[s]) continue;
+    qsort(list[s], (size_t)len[s], sizeof(rb_item), rb_order);
+    int64_t excess = bw[s] - Lmax, prefix = 0;
+    for (int64_t i = 0; i < len[s] && prefix < excess; ++i) {
+      prefix += list[s][i].c;
+      mv[list[s][i].v] = 1;
+      tg[list[s][i].v] = list[s][i].t;
+      moved += 1;
+    }
+  }
+  ojet_apply(h, k, part, phi, bw, mv, tg);
+  if (moved_flag) memcpy(moved_flag, mv, (size_t)h->n);
+  if (moved_target)
+    for (int32_t v = 0; v < h->n; ++v) moved_target[v] = mv[v] ? tg[v] : -1;
+  for (int32_t b = 0; b < k; ++b) free(list[b]);
+  free(list); free(len); free(cnt); free(mv); free(tg);
+  return moved;
+}
+
+/* Rebalancing rounds until balanced, a round moves nothing, or the round cap (R10). */
+int64_t ojet_rebalance(const ojet_hg *h, const ojet_params *p, int32_t *part, int32_t *phi, int64_t *bw,
+                       int64_t *moves_out) {
+  int64_t rounds = 0, moves = 0;
+  while (rounds < p->max_rebalance_rounds) {
+    int64_t moved = ojet_rebalance_round(h, p, part, phi, bw, NULL, NULL);
+    if (moved < 0) break;
+    rounds += 1;
+    moves += moved;
+    if (moved == 0) break;
+  }
+  if (moves_out) *moves_out = moves;
+  return rounds;
+}
+
+/* ------------------------------------------------------------ Algorithm 1 */
+
+static void fill_stats(const ojet_hg *h, const ojet_params *p, const int32_t *phi, const int64_t *bw,
+                       ojet_stats *st) {
+  int64_t Lmax = ojet_lmax(h, p), mx = 0;
+  for (int32_t b = 0; b < p->k; ++b) mx = bw[b] > mx ? bw[b] : mx;
+  st->objective = ojet_connectivity(h, p->k, phi);
+  st->max_block_weight = mx;
+  st->imbalanced = mx > Lmax;
+}
+
+/*
+ * One Jet iteration (the body of Algorithm 1): candidates, afterburner, apply
+ * (locking the approved vertices, R7), and rebalancing if a block is above
+ * L_max.  part/phi/bw/locked are updated in place.
+ */
+void ojet_refine_round(const ojet_hg *h, const ojet_params *p, int32_t tau_num, int32_t tau_den, int32_t *part,
+                       int32_t *phi, int64_t *bw, uint8_t *locked, ojet_stats *st) {
+  const int32_t n = h->n, k = p->k;
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  int32_t *target = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int64_t *gain = (int64_t *)malloc(sizeof(int64_t) * nn);
+  int64_t *rg = (int64_t *)malloc(sizeof(int64_t) * nn);
+  uint8_t *in_m = (uint8_t *)malloc(nn);
+  uint8_t *approved = (uint8_t *)malloc(nn);
+  memset(st, 0, sizeof(*st));
+  st->candidates = ojet_candidates(h, k, part, phi, locked, tau_num, tau_den, target, gain, in_m);
+  st->approved = ojet_afterburner(h, k, part, phi, target, gain, in_m, rg, approved);
+  ojet_apply(h, k, part, phi, bw, approved, target);
+  for (int32_t v = 0; v < n; ++v) locked[v] = approved[v];
+  int64_t Lmax = ojet_lmax(h, p);
+  int over = 0;
+  for (int32_t b = 0; b < k; ++b) over |= bw[b] > Lmax;
+  if (over) st->rebalance_rounds = ojet_rebalance(h, p, part, phi, bw, &st->rebalance_moves);
+  fill_stats(h, p, phi, bw, st);
+  free(target); free(gain); free(rg); free(in_m); free(approved);
+}
+
+/*
+ * Algorithm 1 with the temperature schedule of Section 7.2: for each tau in
+ * the schedule, iterate until `limit` iterations pass without a strictly
+ * better balanced partition (R11), then roll back to the best balanced
+ * partition seen.  tau is given as pairs (num, den).  part is updated in
+ * place.  Returns the number of iterations executed; *best_objective gets the
+ * (lambda-1) of the returned partition.
+ */
+int64_t ojet_refine(const ojet_hg *h, const ojet_params *p, const int32_t *tau_pairs, int32_t n_tau, int32_t limit,
+                    int32_t *part, int64_t *objective_out, int64_t *phase_iters) {
+  const int32_t n = h->n, k = p->k;
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  int32_t *phi = (int32_t *)malloc(sizeof(int32_t) * (size_t)h->m * (size_t)k + 4);
+  int64_t *bw = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+  uint8_t *locked = (uint8_t *)malloc(nn);
+  int32_t *best = (int32_t *)malloc(sizeof(int32_t) * nn);
+  ojet_pincounts(h, k, part, phi, bw);
+  int64_t Lmax = ojet_lmax(h, p);
+  int have_best = 1;
+  for (int32_t b = 0; b < k; ++b) have_best &= bw[b] <= Lmax;
+  int64_t best_obj = have_best ? ojet_connectivity(h, k, phi) : 0;
+  if (have_best) memcpy(best, part, sizeof(int32_t) * (size_t)n);
+  int64_t iterations = 0;
+  for (int32_t ti = 0; ti < n_tau; ++ti) {
+    memset(locked, 0, nn);
+    int32_t it = 0;
+    int64_t in_phase = 0;
+    while (it < limit) {
+      ojet_stats st;
+      ojet_refine_round(h, p, tau_pairs[2 * ti], tau_pairs[2 * ti + 1], part, phi, bw, locked, &st);
+      iterations += 1;
+      in_phase += 1;
+      it += 1;
+      if (!st.imbalanced && (!have_best || st.objective < best_obj)) {
+        have_best = 1;
+        best_obj = st.objective;
+        memcpy(best, part, sizeof(int32_t) * (size_t)n);
+        it = 0;
+      }
+    }
+    if (phase_iters) phase_iters[ti] = in_phase;
+    if (have_best) { /* rollback to the best balanced partition */
+      memcpy(part, best, sizeof(int32_t) * (size_t)n);
+      ojet_pincounts(h, k, part, phi, bw);
+    }
+  }
+  if (objective_out) *objective_out = ojet_connectivity(h, k, phi);
+  free(phi); free(bw); free(locked); free(best);
+  return iterations;
+}
