@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of deterministic Jet refinement rounds (connectivity metric) on GB300.
+
+A step is one Jet iteration (the body of Algorithm 1: candidates,
+afterburner, apply, rebalancing if needed, objective) on the whole
+hypergraph; the metric is pins/s = P * steps / time.  The default workload is
+the VLSI-netlist-shaped hypergraph (n = 2,000,000, m = 2,200,000,
+power-law 2.5 sizes on [2, 5000], 80 % of pins within +-20,000 ids,
+c(v) in 1..4, k = 64, eps = 3/100), started from a seeded balanced
+partition; the timed steps are the first K iterations at temperature 3/4.
+
+One JSON line on stdout (rank 0).  --impl reference times the CPU oracle
+(single-threaded, test infrastructure) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_12013_gb300 import synth  # noqa: E402
+
+WORKLOADS = {
+    "vlsi_2m": ("VLSI-shaped hypergraph n=2,000,000 m=2,200,000 power-law(2.5)[2,5000] sizes, 80% pins "
+                "within +-20,000, c in 1..4, k=64, eps=3/100", synth.config_vlsi_2m),
+    "rownet_4m": ("sparse-matrix row-net n=m=4,000,000, log-normal(2,1) rows + 200 hubs of 50k-200k pins, "
+                  "k=128, eps=3/100", synth.config_rownet_4m),
+    "random_10k": ("random hypergraph n=10,000 m=12,000 |e|=2+Geometric(1/2)<=64, k=8, eps=3/100",
+                   synth.config_random_10k),
+}
+TAU = (3, 4)
+SCHEDULE = ((3, 4), (3, 8), (0, 1))
+LIMIT = 8
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], f[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- byte model
+def kernel_bytes(hg, k, deg, st_before, round_stats):
+    """Compulsory (algorithmic) bytes of the candidate kernels for one round.
+
+    Each array counts once per launch: the streamed CSR arrays by the bytes
+    read, and every gathered table by min(gathers x element, table size).
+    st_before: locked (bool[n]) before the round.
+    """
+    n, m, P = hg.n, hg.m, hg.P
+    kw = (k + 31) // 32
+    unlocked = ~st_before
+    Pu = int(deg[unlocked].sum())
+    b = 8 * (n + 1) + 4 * n + n + 4 * int(unlocked.sum())  # vptr, vertex list, locks, own block
+    b += 4 * Pu                                              # incidences of unlocked vertices
+    b += min(4 * Pu, 4 * m)                                  # omega(e) gathers
+    b += min(4 * kw * Pu, 4 * kw * m)                        # Lambda(e) bitmask gathers
+    b += min(4 * Pu, 4 * m * k)                              # phi_e[s] gathers
+    b += 8 * n                                               # candidate records written
+    return b
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2504_12013_gb300 import jet
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    desc, make = WORKLOADS[args.workload]
+    t0 = time.time()
+    hg, k, part0 = make(args.seed)
+    log(f"[rank {rank}] workload {args.workload}: n={hg.n} m={hg.m} P={hg.P} k={k} (generated in "
+        f"{time.time() - t0:.1f}s)")
+    dh = jet.DeviceHypergraph(hg, dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = jet.jet_ctx_create(dh, jet.params(k), stream)
+    st = jet.JetState(ctx, part0)
+    part_init = st.part.clone()
+    phi_init = st.phi.clone()
+    bw_init = st.block_w.clone()
+
+    def reset():
+        st.part.copy_(part_init)
+        st.phi.copy_(phi_init)
+        st.block_w.copy_(bw_init)
+        st.locked.zero_()
+        jet.jet_build_pincounts(ctx, st.part, st.phi, st.block_w)  # also refreshes the context's bitmasks
+
+    for _ in range(args.warmup):
+        st.round(TAU)
+    reset()
+    torch.cuda.synchronize(dev)
+    jet.jet_profile_read(ctx, reset=True)
+    jet.jet_profile_enable(ctx, True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st.round(TAU)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    prof = jet.jet_profile_read(ctx, reset=True)
+    jet.jet_profile_enable(ctx, False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    final_stats = st.stats_dict()
+
+    # untimed deterministic replay of the same K steps: per-step locks and stats for the byte model
+    reset()
+    deg = np.diff(hg.vptr)
+    model_bytes = 0
+    trace = []
+    for _ in range(args.steps):
+        locked_before = st.locked.cpu().numpy()[: hg.n].astype(bool)
+        st.round(TAU)
+        s = st.stats_dict()
+        trace.append(s)
+        model_bytes += kernel_bytes(hg, k, deg, locked_before, s)
+    assert trace[-1] == final_stats, "replay diverged from the timed run"
+
+    result = {"ms": ms, "prof": prof, "model_bytes": model_bytes, "trace": trace, "clocks": clk.summary(),
+              "hg": hg, "k": k, "part0": part0, "desc": desc, "dev": dev}
+    ctx.close()
+    return result
+
+
+def run_e2e(args, hg, k, part0, dev):
+    """jet_refine_host on pinned host buffers: H2D of the hypergraph and partition, the whole temperature
+    schedule, D2H of the refined partition, per call."""
+    import torch
+
+    from paper_2504_12013_gb300 import jet
+    pinned = {}
+    for name in ("eptr", "pins", "vptr", "inc", "vwgt", "ewgt"):
+        a = getattr(hg, name)
+        t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True)
+        t.numpy()[:] = a
+        pinned[name] = t.numpy()
+    hp = synth.Hypergraph(hg.n, hg.m, **pinned)
+    part_t = torch.empty(hg.n, dtype=torch.int32, pin_memory=True)
+    part = part_t.numpy()
+    part[:] = part0
+    jet.jet_refine_host(hp, jet.params(k), SCHEDULE, LIMIT, part)  # warm-up (allocator pools, module load)
+    times, iters = [], []
+    for _ in range(args.e2e_steps):
+        part[:] = part0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        res = jet.jet_refine_host(hp, jet.params(k), SCHEDULE, LIMIT, part)
+        times.append(time.perf_counter() - t0)
+        iters.append(res["iterations"])
+    bi = hg.nbytes() + 4 * hg.n
+    bo = 4 * hg.n
+    return {"value": hg.P * sum(iters) / sum(times), "unit": "pins/s", "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bo, "iterations_per_call": iters[-1], "seconds_per_call": min(times),
+            "objective": res["objective"]}
+
+
+def cpu_baseline(hg, k, part0, budget_s):
+    """The oracle as it stands (single thread), rounds at tau = 3/4 from the same start until budget_s."""
+    import oracle
+    orc = oracle.Oracle(hg)
+    st = oracle.State(orc, k, part0)
+    prm = oracle.Params(k)
+    rounds, t0 = 0, time.perf_counter()
+    while True:
+        orc.refine_round(prm, TAU, st.part, st.phi, st.bw, st.locked)
+        rounds += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": hg.P * rounds / el, "unit": "pins/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rounds} Jet iteration(s) at tau=3/4 of the same workload, {el:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="vlsi_2m", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    r = run_gpu(args, rank, world)
+    hg, k = r["hg"], r["k"]
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    e2e = None if args.no_e2e else run_e2e(args, hg, k, r["part0"], r["dev"])
+    cpu = None if args.no_cpu_baseline else cpu_baseline(hg, k, r["part0"], args.cpu_budget)
+
+    import json as _j
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _j.load(open(pk))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    ms = r["ms"]
+    value = hg.P * args.steps * world / (ms / 1e3)
+    prof = r["prof"]
+    fam_ms = {f: v["ms"] for f, v in prof.items()}
+    total_fam = sum(fam_ms.values())
+    dom = max(fam_ms, key=fam_ms.get)
+    cand_ms = fam_ms["candidates"]
+    achieved = r["model_bytes"] / (cand_ms / 1e3) / 1e9 if cand_ms > 0 else None
+    launches = sum(v["launches"] for v in prof.values())
+    line = {
+        "metric": "Jet-round pins/s (bit-exact vs oracle)",
+        "value": value,
+        "unit": "pins/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic (seeded generator shaped like the paper's VLSI benchmark instances)",
+        "config": {"workload": r["desc"], "n": hg.n, "m": hg.m, "pins": hg.P, "k": k, "tau": "3/4",
+                   "step": "one Jet iteration (candidates, afterburner, apply, rebalancing, objective)",
+                   "l2": "inputs larger than L2 (phi %d MB)" % (hg.m * k * 4 // 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "candidates (k_cand_light/k_cand_heavy)",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_source": peak_src,
+                     "dominant_family": dom, "family_share": {f: round(v / total_fam, 4) for f, v in fam_ms.items()}
+                     if total_fam > 0 else {}},
+        "clocks": r["clocks"],
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "trace_first_steps": r["trace"][:3],
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The oracle (single thread) as the reference arm: each step one oracle Jet iteration."""
+    if rank != 0:
+        return
+    import oracle
+    desc, make = WORKLOADS[args.workload]
+    hg, k, part0 = make(args.seed)
+    orc = oracle.Oracle(hg)
+    st = oracle.State(orc, k, part0)
+    prm = oracle.Params(k)
+    for _ in range(args.warmup):
+        orc.refine_round(prm, TAU, st.part, st.phi, st.bw, st.locked)
+    st = oracle.State(orc, k, part0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.refine_round(prm, TAU, st.part, st.phi, st.bw, st.locked)
+    el = time.perf_counter() - t0
+    value = hg.P * args.steps / el
+    line = {"impl": "reference", "metric": "Jet-round pins/s (bit-exact vs oracle)", "value": value,
+            "unit": "pins/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": desc, "n": hg.n, "m": hg.m, "pins": hg.P, "k": k, "tau": "3/4"},
+            "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {args.steps} Jet iterations at tau=3/4 (after {args.warmup} "
+                                       "warm-up iterations from the same start)"},
+            "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

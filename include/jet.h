@@ -1,0 +1,237 @@
+/*
+ * libjet -- deterministic Jet refinement for the connectivity metric on one
+ * GB300 (sm_103a), after "Deterministic Parallel High-Quality Hypergraph
+ * Partitioning" (arXiv 2504.12013).
+ *
+ * C ABI.  Plain pointers and sizes only.  Unless a function says otherwise:
+ *   - every pointer argument is a DEVICE pointer owned by the caller; the
+ *     library never frees it and never keeps it beyond the call, except the
+ *     hypergraph arrays, which must stay valid and unchanged for the lifetime
+ *     of the context;
+ *   - work is enqueued on the context's stream; the call returns without
+ *     waiting for the GPU unless its comment says it synchronizes;
+ *   - the return value is JET_OK (0) or a negative JET_ERR_* code, and
+ *     jet_last_error() gives a one-line reason.  On error nothing has been
+ *     written to caller buffers, except where the comment says so.
+ *   - results are bit-identical from run to run: all accumulation is integer
+ *     and order-independent.
+ *
+ * Notation (Section 2 of the paper): H = (V, E, c, omega), n = |V|, m = |E|,
+ * P = sum of |e| (pins), k blocks, Pi : V -> {0..k-1} (blocks are 0-based),
+ * phi_e[i] = |e cap V_i|, lambda(e) = |{i : phi_e[i] > 0}|,
+ * (lambda-1)(Pi) = sum_e (lambda(e) - 1) omega(e),
+ * L_max = floor((1 + eps) * ceil(c(V)/k)).
+ */
+#ifndef JET_H
+#define JET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JET_OK 0
+#define JET_ERR_INVALID_ARG (-1) /* bad size, pointer, parameter or unsupported k        */
+#define JET_ERR_OOM (-2)         /* device allocation failed                              */
+#define JET_ERR_CUDA (-3)        /* a CUDA call failed (message in jet_last_error)        */
+#define JET_ERR_OVERFLOW (-4)    /* a weight sum would leave the exact integer ranges     */
+#define JET_ERR_DATA (-5)        /* device check found a bad index/weight in the inputs   */
+
+/*
+ * Hypergraph in two CSR views (Section 2).  All arrays are device memory.
+ *   eptr[m+1], pins[P]   pins of edge e are pins[eptr[e] .. eptr[e+1]),
+ *                        distinct vertex ids in [0, n), any order
+ *   vptr[n+1], inc[P]    incident edges I(v) are inc[vptr[v] .. vptr[v+1]);
+ *                        must be the exact transpose of (eptr, pins)
+ *   vwgt[n]              c(v) >= 1
+ *   ewgt[m]              omega(e) >= 1
+ * Empty edges are allowed and contribute 0 to (lambda-1).
+ */
+typedef struct {
+  int32_t n, m;
+  int64_t P;
+  const int64_t *eptr;
+  const int32_t *pins;
+  const int64_t *vptr;
+  const int32_t *inc;
+  const int32_t *vwgt;
+  const int32_t *ewgt;
+} jet_hypergraph;
+
+/*
+ * Parameters.  eps = eps_num/eps_den (the balance bound, Section 2; 3/100 in
+ * Section 7.1); d = d_num/d_den (deadzone size, Section 4.3; 1/10).  The
+ * rebalancer runs at most max_rebalance_rounds rounds per call.
+ * k must be in [2, 256].
+ */
+typedef struct {
+  int32_t k;
+  int32_t eps_num, eps_den;
+  int32_t d_num, d_den;
+  int32_t max_rebalance_rounds;
+} jet_params;
+
+/*
+ * Per-iteration statistics, written to DEVICE memory by jet_refine_round and
+ * jet_rebalance (eight int64 fields, 64 bytes).
+ */
+typedef struct {
+  int64_t candidates;       /* |M| after the temperature filter (Section 4.1)     */
+  int64_t approved;         /* moves kept by the afterburner (Algorithm 2)        */
+  int64_t rebalance_rounds; /* rebalancing rounds that found an overloaded block  */
+  int64_t rebalance_moves;  /* vertices moved by the rebalancer (Section 4.3)     */
+  int64_t objective;        /* (lambda-1) after the iteration                     */
+  int64_t max_block_weight; /* max_i c(V_i) after the iteration                    */
+  int64_t imbalanced;       /* 1 if max_i c(V_i) > L_max                           */
+  int64_t reserved;
+} jet_round_stats;
+
+/* Summary of jet_refine, written to HOST memory. */
+typedef struct {
+  int64_t iterations;           /* Jet iterations executed over all phases            */
+  int64_t objective;            /* (lambda-1) of the returned partition               */
+  int64_t initial_objective;    /* (lambda-1) of the input partition                  */
+  int64_t balanced;             /* 1 if the returned partition satisfies L_max        */
+  int64_t phase_iterations[8];  /* iterations per temperature (first 8 phases)        */
+} jet_refine_result;
+
+typedef struct jet_ctx jet_ctx;
+
+/*
+ * Create a context for one hypergraph: validates the arguments, checks the
+ * CSR arrays on the device (index ranges, monotone offsets, positive
+ * weights, the transpose degree counts), computes c(V), ceil(c(V)/k), L_max
+ * and the deadzone bound, classifies vertices and edges by size, and
+ * allocates the library-owned workspace (about m*ceil(k/32)*4 + 48*n bytes
+ * plus the class lists).  `stream` is a cudaStream_t (NULL = legacy default
+ * stream).  SYNCHRONIZES the stream.  Errors: JET_ERR_INVALID_ARG (k outside
+ * [2,256], negative sizes, NULL arrays with nonzero sizes, eps/d
+ * denominators <= 0, negative numerators), JET_ERR_DATA (bad CSR or
+ * weights), JET_ERR_OVERFLOW (some sum of omega over I(v) >= 2^31, c(v) >
+ * 32767, or c(V) >= 2^50), JET_ERR_OOM, JET_ERR_CUDA.  *out is NULL on error.
+ */
+int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *params, void *stream);
+
+/* Free the workspace.  Synchronizes the stream first.  NULL is ignored. */
+void jet_ctx_destroy(jet_ctx *ctx);
+
+/* One-line reason of the last error on this context (static string if ctx is NULL). */
+const char *jet_last_error(const jet_ctx *ctx);
+
+/*
+ * Pin counts (Section 2; the table that makes gains linear, Section 4.2):
+ * phi[e*k + i] = |e cap V_i| (int32, row-major m x k, fully overwritten) and
+ * block_w[i] = c(V_i) (int64[k], overwritten) for the partition part[n]
+ * (values in [0,k)).  Also rebuilds the context's connectivity bitmasks of
+ * phi.  A part value outside [0,k) is reported as JET_ERR_DATA by the next
+ * synchronizing call on this context (the affected pins are skipped).
+ */
+int jet_build_pincounts(jet_ctx *ctx, const int32_t *part, int32_t *phi, int64_t *block_w);
+
+/*
+ * Connectivity metric (Section 2): *objective_out = sum_e (lambda(e)-1)
+ * omega(e), lambda(e) = number of nonzero entries of row e of phi.
+ * objective_out is one device int64.  Reads phi densely; does not use or
+ * change the context's bitmasks.
+ */
+int jet_connectivity(jet_ctx *ctx, const int32_t *phi, int64_t *objective_out);
+
+/*
+ * One Jet iteration, the body of Algorithm 1 (Section 4.1): move candidates
+ * with temperature tau = tau_num/tau_den in [0,1) (the unlocked vertices
+ * whose best adjacent target t(v) has gain >= -tau * A(v)); the hypergraph
+ * afterburner (Algorithm 2), keeping candidates whose recomputed gain in the
+ * order (gain desc, vertex id asc) is > 0; ApplyMoves of the kept moves;
+ * locked[v] := 1 exactly for the moved vertices; then, if some block exceeds
+ * L_max, deterministic rebalancing rounds (Section 4.3) as in
+ * jet_rebalance.  part[n], phi[m*k], block_w[k], locked[n] (uint8) are
+ * updated in place and must describe one consistent state (as left by
+ * jet_build_pincounts or a previous call).  stats (device, may be NULL)
+ * receives the iteration's statistics.  Synchronizes the stream once per
+ * rebalancing round that runs.
+ * Errors: JET_ERR_INVALID_ARG for tau outside [0,1) or NULL state arrays.
+ */
+int jet_refine_round(jet_ctx *ctx, int32_t tau_num, int32_t tau_den, int32_t *part, int32_t *phi,
+                     int64_t *block_w, uint8_t *locked, jet_round_stats *stats);
+
+/*
+ * Deterministic rebalancing (Section 4.3) until no block exceeds L_max, a
+ * round moves nothing, or params.max_rebalance_rounds rounds ran.  Per
+ * round, from the state at its start: every vertex v of an overloaded block
+ * s with 2c(v) <= 3(c(V_s) - ceil(c(V)/k)) takes its best target b != s
+ * with c(V_b) + c(v) <= L_max outside the deadzone (c(V_b) >= L_max_real -
+ * d*eps*ceil(c(V)/k)), ties to the smaller block id; priority gain*c(v) for
+ * gain >= 0, gain/c(v) below, ties to the smaller vertex id; per overloaded
+ * block the minimal prefix of that order whose weight reaches the excess
+ * moves, all at once.  Locks are ignored and unchanged.  stats (device, may
+ * be NULL) receives rebalance_rounds, rebalance_moves, objective,
+ * max_block_weight and imbalanced (other fields 0).  Synchronizes once per
+ * round.
+ */
+int jet_rebalance(jet_ctx *ctx, int32_t *part, int32_t *phi, int64_t *block_w, jet_round_stats *stats);
+
+/*
+ * Algorithm 1 to convergence with a temperature schedule (Section 7.2: three
+ * temperatures 3/4, 3/8, 0 and an iteration limit of 8): builds phi and
+ * block_w from part, then for every tau in tau_pairs (HOST array of n_tau
+ * (num, den) pairs) clears the locks and iterates jet_refine_round until
+ * `limit` iterations in a row bring no strictly better balanced partition,
+ * then rolls back to the best balanced partition seen.  part (device, n)
+ * is updated in place; phi/block_w (device, caller-sized m*k and k) hold the
+ * final state.  *result (HOST) receives the summary.  Synchronizes.
+ */
+int jet_refine(jet_ctx *ctx, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *part, int32_t *phi,
+               int64_t *block_w, jet_refine_result *result);
+
+/*
+ * The candidate step of jet_refine_round alone (Section 4.1), for
+ * inspection: in_m[v] (uint8) = 1 for v in M, and for those v target[v] =
+ * t(v) and gain[v] = gain(v, t(v)) (int32); other entries are -1 / 0.  The
+ * candidates stay in the context for a following jet_afterburner call.
+ */
+int jet_candidates(jet_ctx *ctx, int32_t tau_num, int32_t tau_den, const int32_t *part, const int32_t *phi,
+                   const uint8_t *locked, int32_t *target, int32_t *gain, uint8_t *in_m);
+
+/*
+ * The afterburner of Algorithm 2 alone, on the candidates of the last
+ * jet_candidates call on this context with the same part/phi:
+ * rg[v] (int32) = recomputed gain, approved[v] (uint8) = v in M and rg > 0.
+ * Nothing is moved.
+ */
+int jet_afterburner(jet_ctx *ctx, const int32_t *part, const int32_t *phi, int32_t *rg, uint8_t *approved);
+
+/*
+ * End-to-end call on HOST buffers: copies the hypergraph (the same arrays as
+ * jet_hypergraph, in host memory; pinned memory gives the fastest copies) and
+ * part[n] to the device, runs jet_refine with the given schedule, and copies
+ * the refined partition back into part.  Allocates and frees its own device
+ * memory.  Synchronizes.  *result (host, may be NULL) gets the summary.
+ */
+int jet_refine_host(const jet_hypergraph *hg_host, const jet_params *params, const int32_t *tau_pairs,
+                    int32_t n_tau, int32_t limit, int32_t *part, jet_refine_result *result);
+
+/*
+ * Profiling.  The library's kernels fall into JET_PROF_FAMILIES families:
+ *   0 pin counts and bitmasks    1 move candidates         2 afterburner
+ *   3 approval and locks         4 apply moves             5 rebalancing targets
+ *   6 rebalancing selection      7 rebalancing control     8 objective and stats
+ *   9 other (connectivity, rollback, exports)
+ * Kernel launches are always counted per family.  While profiling is enabled
+ * (jet_profile_enable(ctx, 1)), each family's launches on the context's
+ * stream are also bracketed by CUDA events.  jet_profile_read synchronizes the
+ * stream and writes, per family (HOST arrays of JET_PROF_FAMILIES entries,
+ * any may be NULL): ms_out = summed device time in milliseconds, calls_out =
+ * timed launcher invocations, launches_out = kernels launched; reset != 0
+ * clears everything afterwards.  Profiling records events only and does not
+ * change results.
+ */
+#define JET_PROF_FAMILIES 10
+int jet_profile_enable(jet_ctx *ctx, int enable);
+int jet_profile_read(jet_ctx *ctx, double *ms_out, int64_t *calls_out, int64_t *launches_out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JET_H */

@@ -1,0 +1,502 @@
+// C ABI of libjet: argument checks, context and workspace, and the host-side
+// order of the kernels of one Jet iteration (Algorithm 1) and of the
+// temperature schedule (Section 7.2).
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "jet_internal.cuh"
+
+using namespace jet;
+
+namespace {
+
+thread_local char g_err[256] = {0};
+
+int fail(jet_ctx *c, int code, const char *fmt, ...) {
+  char *dst = c ? c->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 256, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(jet_ctx *c, cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation) return fail(c, JET_ERR_OOM, "%s: out of device memory", where);
+  return fail(c, JET_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                 \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(jet_ctx *c, T **p, size_t count) {
+  return cudaMallocAsync(reinterpret_cast<void **>(p), sizeof(T) * (count > 0 ? count : 1), c->stream);
+}
+
+void dfree(jet_ctx *c, void *p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+// floor(a / b) and ceil(a / b) for b > 0
+__int128 floor_div(__int128 a, __int128 b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__int128 ceil_div(__int128 a, __int128 b) { return -floor_div(-a, b); }
+
+const char *data_error_text(int err) {
+  if (err & kErrOffsets) return "CSR offsets are not monotone or do not span [0, P]";
+  if (err & kErrWeight) return "a vertex or edge weight is < 1";
+  if (err & kErrPinRange) return "a pin id is outside [0, n)";
+  if (err & kErrIncRange) return "an incidence (edge id) is outside [0, m)";
+  if (err & kErrTranspose) return "vptr/inc is not the transpose of eptr/pins (degree mismatch)";
+  if (err & kErrPartRange) return "a partition value is outside [0, k)";
+  return "data error";
+}
+
+// Copy the counters to the host and wait; report device-detected data errors.
+int sync_counters(jet_ctx *c) {
+  CK(cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream), "counters");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  if (c->cnt_host->err) {
+    int err = c->cnt_host->err;
+    cudaMemsetAsync(&c->cnt->err, 0, sizeof(int), c->stream);
+    return fail(c, JET_ERR_DATA, "%s", data_error_text(err));
+  }
+  return JET_OK;
+}
+
+// zero every counter before `err`
+cudaError_t reset_counters(jet_ctx *c) {
+  return cudaMemsetAsync(c->cnt, 0, offsetof(Counters, err), c->stream);
+}
+
+cudaError_t ensure_masks(jet_ctx *c, const int32_t *phi) {
+  if (c->phi_owner == phi) return cudaSuccess;
+  return launch_masks_from_phi(c, phi);
+}
+
+// ---- profiling: events around kernel families
+enum Fam { F_PIN = 0, F_CAND, F_AB, F_APPROVE, F_APPLY, F_RB_TGT, F_RB_SEL, F_RB_CTL, F_OBJ, F_OTHER };
+
+void prof_flush(jet_ctx *c) {
+  if (!c->prof_n) return;
+  cudaEventSynchronize(c->prof_ev[2 * c->prof_n - 1]);
+  for (int i = 0; i < c->prof_n; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) == cudaSuccess) c->fam_ms[c->prof_fam[i]] += ms;
+  }
+  c->prof_n = 0;
+}
+
+struct ProfScope {
+  jet_ctx *c;
+  int fam;
+  long long l0;
+  int slot = -1;
+  ProfScope(jet_ctx *c_, int f) : c(c_), fam(f), l0(c_->kernel_launches) {
+    if (c->prof_on && c->prof_ev) {
+      if (c->prof_n == jet_ctx::kProfPairs) prof_flush(c);
+      slot = c->prof_n++;
+      c->prof_fam[slot] = fam;
+      cudaEventRecord(c->prof_ev[2 * slot], c->stream);
+    }
+  }
+  ~ProfScope() {
+    c->fam_launches[fam] += c->kernel_launches - l0;
+    c->fam_calls[fam] += 1;
+    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
+  }
+};
+
+#define CKP(fam, call, where)     \
+  do {                            \
+    ProfScope _ps(c, fam);        \
+    CK(call, where);              \
+  } while (0)
+
+int check_ctx(jet_ctx *c) {
+  if (!c) return fail(nullptr, JET_ERR_INVALID_ARG, "context is NULL");
+  return JET_OK;
+}
+
+// Rebalancing rounds (Section 4.3) until balanced, nothing moved or the cap.
+int rebalance_loop(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
+  CKP(F_RB_CTL, launch_rb_check(c, block_w), "rebalance check");
+  int rc = sync_counters(c);
+  if (rc) return rc;
+  if (!c->cnt_host->rb_any || c->params.max_rebalance_rounds <= 0) return JET_OK;
+  for (;;) {
+    CKP(F_RB_CTL, launch_rb_prep(c, block_w), "rebalance prep");
+    CKP(F_RB_TGT, launch_rebalance_candidates(c, part, phi), "rebalance targets");
+    CKP(F_RB_SEL, launch_rb_select(c), "rebalance select");
+    CKP(F_APPLY, launch_apply(c, part, phi, block_w), "rebalance apply");
+    CKP(F_RB_CTL, launch_rb_post(c, block_w), "rebalance post");
+    rc = sync_counters(c);
+    if (rc) return rc;
+    if (c->cnt_host->rb_done) break;
+  }
+  return JET_OK;
+}
+
+int check_tau(jet_ctx *c, int32_t tau_num, int32_t tau_den) {
+  if (tau_den <= 0 || tau_num < 0 || tau_num >= tau_den)
+    return fail(c, JET_ERR_INVALID_ARG, "temperature %d/%d is outside [0, 1)", tau_num, tau_den);
+  return JET_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *jet_last_error(const jet_ctx *ctx) { return ctx ? ctx->err : g_err; }
+
+int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p, void *stream) {
+  if (!out) return fail(nullptr, JET_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!hg || !p) return fail(nullptr, JET_ERR_INVALID_ARG, "hypergraph or params is NULL");
+  if (hg->n < 0 || hg->m < 0 || hg->P < 0) return fail(nullptr, JET_ERR_INVALID_ARG, "negative size");
+  if (p->k < 2 || p->k > kMaxK) return fail(nullptr, JET_ERR_INVALID_ARG, "k = %d is outside [2, %d]", p->k, kMaxK);
+  if (p->eps_den <= 0 || p->eps_num < 0 || p->d_den <= 0 || p->d_num < 0 || p->max_rebalance_rounds < 0)
+    return fail(nullptr, JET_ERR_INVALID_ARG, "eps/d must be non-negative fractions with positive denominators");
+  if (!hg->eptr || !hg->vptr || (hg->P > 0 && (!hg->pins || !hg->inc)) || (hg->n > 0 && !hg->vwgt) ||
+      (hg->m > 0 && !hg->ewgt))
+    return fail(nullptr, JET_ERR_INVALID_ARG, "a hypergraph array is NULL");
+  jet_ctx *c = new (std::nothrow) jet_ctx();
+  if (!c) return fail(nullptr, JET_ERR_OOM, "host allocation failed");
+  c->n = hg->n;
+  c->m = hg->m;
+  c->P = hg->P;
+  c->eptr = hg->eptr;
+  c->vptr = hg->vptr;
+  c->pins = hg->pins;
+  c->inc = hg->inc;
+  c->vwgt = hg->vwgt;
+  c->ewgt = hg->ewgt;
+  c->params = *p;
+  c->k = p->k;
+  const int kw = (p->k + 31) / 32;
+  c->kwp = kw <= 1 ? 1 : kw <= 2 ? 2 : kw <= 4 ? 4 : 8;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  int rc = JET_OK;
+  int64_t *wdeg = nullptr;
+  int32_t *degc = nullptr;
+  unsigned long long *scal = nullptr;
+  unsigned long long hscal[4] = {0, 0, 0, 0};
+  do {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { rc = cuda_fail(c, e, "device query"); break; }
+    if ((e = dalloc(c, &c->cnt, 1)) != cudaSuccess ||
+        (e = cudaMallocHost(reinterpret_cast<void **>(&c->cnt_host), sizeof(Counters))) != cudaSuccess ||
+        (e = dalloc(c, &wdeg, c->n)) != cudaSuccess || (e = dalloc(c, &degc, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &scal, 4)) != cudaSuccess) {
+      rc = cuda_fail(c, e, "context allocation");
+      break;
+    }
+    memset(c->cnt_host, 0, sizeof(Counters));
+    if ((e = cudaMemsetAsync(c->cnt, 0, sizeof(Counters), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(degc, 0, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(scal, 0, sizeof(unsigned long long) * 4, c->stream)) != cudaSuccess) {
+      rc = cuda_fail(c, e, "context init");
+      break;
+    }
+    if ((e = launch_validate(c, wdeg, degc, scal)) != cudaSuccess) { rc = cuda_fail(c, e, "validation"); break; }
+    if ((e = cudaMemcpyAsync(hscal, scal, sizeof(hscal), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) {
+      rc = cuda_fail(c, e, "validation");
+      break;
+    }
+    if ((rc = sync_counters(c)) != JET_OK) break;
+    c->W = (int64_t)hscal[0];
+    c->max_wdeg = (int64_t)hscal[1];
+    c->cmax = (int32_t)hscal[2];
+    if (c->max_wdeg >= (1ll << 31) - 1) {
+      rc = fail(c, JET_ERR_OVERFLOW, "a sum of omega over I(v) (%lld) does not fit the int32 gains",
+                (long long)c->max_wdeg);
+      break;
+    }
+    if (c->cmax > kMaxVertexWeight) {
+      rc = fail(c, JET_ERR_OVERFLOW, "c(v) = %d exceeds %d (exact rebalancing priorities)", c->cmax, kMaxVertexWeight);
+      break;
+    }
+    if (c->W >= (1ll << 50)) { rc = fail(c, JET_ERR_OVERFLOW, "c(V) too large"); break; }
+    // balance constants (Section 2) and the deadzone bound (Section 4.3)
+    const __int128 A = ((__int128)c->W + c->k - 1) / c->k;
+    c->A = (int64_t)A;
+    c->Lmax = (int64_t)(((__int128)(p->eps_den + (int64_t)p->eps_num) * A) / p->eps_den);
+    const __int128 R = (__int128)p->d_den * ((int64_t)p->eps_den + p->eps_num) * A - (__int128)p->d_num * p->eps_num * A;
+    const __int128 D = (__int128)p->eps_den * p->d_den;
+    c->dz_min = (int64_t)ceil_div(R, D);
+    // class lists, workspace
+    if ((e = dalloc(c, &c->v_light, c->n)) != cudaSuccess || (e = dalloc(c, &c->e_tiny, 2 * (size_t)c->m)) != cudaSuccess ||
+        (e = dalloc(c, &c->mask, (size_t)c->m * c->kwp)) != cudaSuccess || (e = dalloc(c, &c->cand, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->rg, c->n)) != cudaSuccess || (e = dalloc(c, &c->mv_v, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->mv_st, c->n)) != cudaSuccess || (e = dalloc(c, &c->vcount, c->k)) != cudaSuccess ||
+        (e = dalloc(c, &c->rbb, c->k)) != cudaSuccess || (e = dalloc(c, &c->rb_cursor, c->k)) != cudaSuccess ||
+        (e = dalloc(c, &c->rb_key, c->n)) != cudaSuccess || (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->rb_ct, c->n)) != cudaSuccess || (e = dalloc(c, &c->best_part, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->locked_ws, c->n)) != cudaSuccess || (e = dalloc(c, &c->stats_scratch, 1)) != cudaSuccess ||
+        (e = cudaMallocHost(reinterpret_cast<void **>(&c->stats_host), sizeof(jet_round_stats))) != cudaSuccess) {
+      rc = cuda_fail(c, e, "workspace allocation");
+      break;
+    }
+    if ((e = cudaMemsetAsync(c->rg, 0, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->cand, 0, sizeof(uint64_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, c->stream)) != cudaSuccess) {
+      rc = cuda_fail(c, e, "workspace init");
+      break;
+    }
+    if ((e = launch_classify(c, wdeg)) != cudaSuccess) { rc = cuda_fail(c, e, "size classes"); break; }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) { rc = cuda_fail(c, e, "context setup"); break; }
+  } while (0);
+  dfree(c, wdeg);
+  dfree(c, degc);
+  dfree(c, scal);
+  if (rc != JET_OK) {
+    snprintf(g_err, sizeof(g_err), "%s", c->err);
+    jet_ctx_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return JET_OK;
+}
+
+void jet_ctx_destroy(jet_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
+                 c->rb_cursor, c->rb_key, c->rb_v, c->rb_ct, c->best_part, c->locked_ws, c->stats_scratch};
+  for (void *p : dev) dfree(c, p);
+  cudaStreamSynchronize(c->stream);
+  if (c->prof_ev) {
+    for (int i = 0; i < 2 * jet_ctx::kProfPairs; ++i) cudaEventDestroy(c->prof_ev[i]);
+    delete[] c->prof_ev;
+    delete[] c->prof_fam;
+  }
+  if (c->cnt_host) cudaFreeHost(c->cnt_host);
+  if (c->stats_host) cudaFreeHost(c->stats_host);
+  delete c;
+}
+
+int jet_build_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int64_t *block_w) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((c->n > 0 && !part) || (c->m > 0 && !phi) || !block_w)
+    return fail(c, JET_ERR_INVALID_ARG, "part, phi or block_w is NULL");
+  CKP(F_PIN, launch_pincounts(c, part, phi, block_w), "pin counts");
+  return JET_OK;
+}
+
+int jet_connectivity(jet_ctx *c, const int32_t *phi, int64_t *objective_out) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((c->m > 0 && !phi) || !objective_out) return fail(c, JET_ERR_INVALID_ARG, "phi or objective_out is NULL");
+  CKP(F_OTHER, launch_connectivity_dense(c, phi, objective_out), "connectivity");
+  return JET_OK;
+}
+
+int jet_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, const int32_t *part, const int32_t *phi,
+                   const uint8_t *locked, int32_t *target, int32_t *gain, uint8_t *in_m) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = check_tau(c, tau_num, tau_den))) return rc;
+  if (c->n > 0 && (!part || !locked || !target || !gain || !in_m)) return fail(c, JET_ERR_INVALID_ARG, "NULL array");
+  if (c->m > 0 && !phi) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
+  CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
+  CKP(F_CAND, launch_candidates(c, tau_num, tau_den, part, phi, locked), "candidates");
+  CKP(F_OTHER, launch_export_candidates(c, target, gain, in_m), "candidates export");
+  return JET_OK;
+}
+
+int jet_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi, int32_t *rg, uint8_t *approved) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (c->n > 0 && (!part || !rg || !approved)) return fail(c, JET_ERR_INVALID_ARG, "NULL array");
+  if (c->m > 0 && !phi) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
+  CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
+  CK(reset_counters(c), "counters");
+  CKP(F_AB, launch_afterburner(c, part, phi), "afterburner");
+  CKP(F_APPROVE, launch_approve(c, nullptr, rg, approved, false), "approve");
+  return JET_OK;
+}
+
+int jet_rebalance(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w, jet_round_stats *stats) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((c->n > 0 && !part) || (c->m > 0 && !phi) || !block_w)
+    return fail(c, JET_ERR_INVALID_ARG, "part, phi or block_w is NULL");
+  CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
+  CK(reset_counters(c), "counters");
+  if ((rc = rebalance_loop(c, part, phi, block_w))) return rc;
+  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_stats(c, block_w, stats ? stats : c->stats_scratch, 1), "stats");
+  return JET_OK;
+}
+
+int jet_refine_round(jet_ctx *c, int32_t tau_num, int32_t tau_den, int32_t *part, int32_t *phi, int64_t *block_w,
+                     uint8_t *locked, jet_round_stats *stats) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if ((rc = check_tau(c, tau_num, tau_den))) return rc;
+  if ((c->n > 0 && (!part || !locked)) || (c->m > 0 && !phi) || !block_w)
+    return fail(c, JET_ERR_INVALID_ARG, "part, phi, block_w or locked is NULL");
+  CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
+  CK(reset_counters(c), "counters");
+  CKP(F_CAND, launch_candidates(c, tau_num, tau_den, part, phi, locked), "candidates");
+  CKP(F_AB, launch_afterburner(c, part, phi), "afterburner");
+  CKP(F_APPROVE, launch_approve(c, locked, nullptr, nullptr, true), "approve");
+  CKP(F_APPLY, launch_apply(c, part, phi, block_w), "apply");
+  if ((rc = rebalance_loop(c, part, phi, block_w))) return rc;
+  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_stats(c, block_w, stats ? stats : c->stats_scratch, 0), "stats");
+  return JET_OK;
+}
+
+int jet_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *part, int32_t *phi,
+               int64_t *block_w, jet_refine_result *result) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (n_tau < 0 || (n_tau > 0 && !tau_pairs) || limit < 1)
+    return fail(c, JET_ERR_INVALID_ARG, "bad schedule (n_tau %d, limit %d)", n_tau, limit);
+  for (int i = 0; i < n_tau; ++i)
+    if ((rc = check_tau(c, tau_pairs[2 * i], tau_pairs[2 * i + 1]))) return rc;
+  if ((c->n > 0 && !part) || (c->m > 0 && !phi) || !block_w || !result)
+    return fail(c, JET_ERR_INVALID_ARG, "part, phi, block_w or result is NULL");
+  memset(result, 0, sizeof(*result));
+  jet_round_stats *st = c->stats_host;
+  auto read_stats = [&]() -> int {
+    CK(cudaMemcpyAsync(st, c->stats_scratch, sizeof(jet_round_stats), cudaMemcpyDeviceToHost, c->stream), "stats");
+    return sync_counters(c);
+  };
+  CKP(F_PIN, launch_pincounts(c, part, phi, block_w), "pin counts");
+  CK(reset_counters(c), "counters");
+  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_stats(c, block_w, c->stats_scratch, 1), "stats");
+  if ((rc = read_stats())) return rc;
+  result->initial_objective = st->objective;
+  bool have_best = !st->imbalanced;
+  int64_t best_obj = st->objective;
+  if (have_best && c->n > 0)
+    CK(cudaMemcpyAsync(c->best_part, part, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+  for (int ti = 0; ti < n_tau; ++ti) {
+    if (c->n > 0) CK(cudaMemsetAsync(c->locked_ws, 0, c->n, c->stream), "locks");
+    int it = 0;
+    int64_t in_phase = 0;
+    while (it < limit) {
+      if ((rc = jet_refine_round(c, tau_pairs[2 * ti], tau_pairs[2 * ti + 1], part, phi, block_w, c->locked_ws,
+                                 c->stats_scratch)))
+        return rc;
+      if ((rc = read_stats())) return rc;
+      result->iterations += 1;
+      in_phase += 1;
+      it += 1;
+      if (!st->imbalanced && (!have_best || st->objective < best_obj)) {
+        have_best = true;
+        best_obj = st->objective;
+        if (c->n > 0)
+          CK(cudaMemcpyAsync(c->best_part, part, sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, c->stream),
+             "snapshot");
+        it = 0;
+      }
+    }
+    if (ti < 8) result->phase_iterations[ti] = in_phase;
+    if (have_best) {  // rollback to the best balanced partition
+      CKP(F_OTHER, launch_rollback_moves(c, part, c->best_part), "rollback");
+      CKP(F_APPLY, launch_apply(c, part, phi, block_w), "rollback apply");
+    }
+  }
+  CK(reset_counters(c), "counters");
+  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_stats(c, block_w, c->stats_scratch, 1), "stats");
+  if ((rc = read_stats())) return rc;
+  result->objective = st->objective;
+  result->balanced = !st->imbalanced;
+  return JET_OK;
+}
+
+int jet_profile_enable(jet_ctx *c, int enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (enable && !c->prof_ev) {
+    c->prof_ev = new (std::nothrow) cudaEvent_t[2 * jet_ctx::kProfPairs];
+    c->prof_fam = new (std::nothrow) int[jet_ctx::kProfPairs];
+    if (!c->prof_ev || !c->prof_fam) return fail(c, JET_ERR_OOM, "profiler allocation");
+    for (int i = 0; i < 2 * jet_ctx::kProfPairs; ++i) CK(cudaEventCreate(&c->prof_ev[i]), "profiler events");
+  }
+  c->prof_on = enable ? 1 : 0;
+  return JET_OK;
+}
+
+int jet_profile_read(jet_ctx *c, double *ms_out, int64_t *calls_out, int64_t *launches_out, int reset) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  if (c->prof_ev) prof_flush(c);
+  for (int f = 0; f < JET_PROF_FAMILIES; ++f) {
+    if (ms_out) ms_out[f] = c->fam_ms[f];
+    if (calls_out) calls_out[f] = c->fam_calls[f];
+    if (launches_out) launches_out[f] = c->fam_launches[f];
+    if (reset) {
+      c->fam_ms[f] = 0;
+      c->fam_calls[f] = 0;
+      c->fam_launches[f] = 0;
+    }
+  }
+  return JET_OK;
+}
+
+int jet_refine_host(const jet_hypergraph *hh, const jet_params *p, const int32_t *tau_pairs, int32_t n_tau,
+                    int32_t limit, int32_t *part, jet_refine_result *result) {
+  if (!hh || !p || !part) return fail(nullptr, JET_ERR_INVALID_ARG, "NULL argument");
+  if (hh->n < 0 || hh->m < 0 || hh->P < 0 || p->k < 2 || p->k > kMaxK)
+    return fail(nullptr, JET_ERR_INVALID_ARG, "bad sizes or k");
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(nullptr, JET_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+  const size_t n = (size_t)hh->n, m = (size_t)hh->m, P = (size_t)hh->P, k = (size_t)p->k;
+  int64_t *eptr = nullptr, *vptr = nullptr, *bw = nullptr;
+  int32_t *pins = nullptr, *inc = nullptr, *vw = nullptr, *ew = nullptr, *pt = nullptr, *phi = nullptr;
+  void **bufs[] = {(void **)&eptr, (void **)&vptr, (void **)&bw, (void **)&pins, (void **)&inc,
+                   (void **)&vw, (void **)&ew, (void **)&pt, (void **)&phi};
+  size_t sizes[] = {8 * (m + 1), 8 * (n + 1), 8 * k, 4 * (P ? P : 1), 4 * (P ? P : 1),
+                    4 * (n ? n : 1), 4 * (m ? m : 1), 4 * (n ? n : 1), 4 * (m * k ? m * k : 1)};
+  int rc = JET_OK;
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaMallocAsync(bufs[i], sizes[i], s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(eptr, hh->eptr, 8 * (m + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(vptr, hh->vptr, 8 * (n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && P) e = cudaMemcpyAsync(pins, hh->pins, 4 * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && P) e = cudaMemcpyAsync(inc, hh->inc, 4 * P, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(vw, hh->vwgt, 4 * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && m) e = cudaMemcpyAsync(ew, hh->ewgt, 4 * m, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n) e = cudaMemcpyAsync(pt, part, 4 * n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) rc = fail(nullptr, e == cudaErrorMemoryAllocation ? JET_ERR_OOM : JET_ERR_CUDA, "upload: %s",
+                                  cudaGetErrorString(e));
+  jet_ctx *c = nullptr;
+  if (rc == JET_OK) {
+    jet_hypergraph dh{hh->n, hh->m, hh->P, eptr, pins, vptr, inc, vw, ew};
+    rc = jet_ctx_create(&c, &dh, p, s);
+  }
+  jet_refine_result local;
+  if (rc == JET_OK) {
+    rc = jet_refine(c, tau_pairs, n_tau, limit, pt, phi, bw, result ? result : &local);
+    if (rc != JET_OK) snprintf(g_err, sizeof(g_err), "%s", c->err);
+  }
+  if (rc == JET_OK && n) {
+    e = cudaMemcpyAsync(part, pt, 4 * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = fail(nullptr, JET_ERR_CUDA, "download: %s", cudaGetErrorString(e));
+  }
+  if (c) jet_ctx_destroy(c);
+  for (int i = 0; i < 9; ++i)
+    if (*bufs[i]) cudaFreeAsync(*bufs[i], s);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Internal declarations of libjet (deterministic Jet refinement on sm_103a).
+//
+// Device data layout (all int32 unless noted):
+//   caller-owned: eptr/vptr (int64 CSR offsets), pins, inc, vwgt, ewgt,
+//                 part[n], phi[m*k] (row-major by edge), block_w[k] (int64),
+//                 locked[n] (uint8)
+//   context-owned (workspace):
+//     mask[m*KWP]    uint32 bitmask of Lambda(e) = {i : phi_e[i] > 0}, KWP
+//                    words per edge (KWP = ceil(k/32) rounded up to 1,2,4,8
+//                    so a row is one aligned vector load)
+//     cand[n]        uint64 move-candidate record (0 = not in M), see below
+//     rg[n]          recomputed gain of Algorithm 2 (zeroed after use)
+//     mv_v/mv_st[n]  move list: vertex, (source | target << 16)
+//     vcount[k]      vertices per block (segment sizes for rebalancing)
+//     rb_*           rebalancing records and per-block state
+//     class lists    vertex / edge ids by size class (built once)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jet.h"
+
+namespace jet {
+
+constexpr int kMaxK = 256;
+constexpr int kLightPlanes = 6;      // thread-per-vertex gain path: weighted degree < 2^6
+constexpr int kTinyEdge = 8;         // thread-per-edge afterburner: |e| <= 8
+constexpr int kWarpEdge = 2048;      // warp-per-edge afterburner: 8 < |e| <= 2048
+constexpr int kWarpEdgeSlots = 32;   // a warp-class edge with more candidates is deferred
+constexpr int kPrioShift = 30;       // exact rebalancing priority encoding (needs c(v) <= 2^15)
+constexpr int kMaxVertexWeight = 32767;
+
+// Candidate record: bits 63..32 = INT32_MAX - gain (so smaller = earlier in
+// the order "gain desc"), bits 23..16 = t(v), bits 15..8 = Pi(v), bit 0 = 1.
+// The afterburner order key of v is (record & ~0xffffffff) | v.
+__host__ __device__ inline uint64_t pack_cand(int32_t g, int s, int t) {
+  uint32_t hi = (uint32_t)((int64_t)INT32_MAX - (int64_t)g);
+  return ((uint64_t)hi << 32) | ((uint64_t)(uint32_t)t << 16) | ((uint64_t)(uint32_t)s << 8) | 1ull;
+}
+__host__ __device__ inline int cand_s(uint64_t r) { return (int)((r >> 8) & 0xff); }
+__host__ __device__ inline int cand_t(uint64_t r) { return (int)((r >> 16) & 0xff); }
+__host__ __device__ inline int32_t cand_gain(uint64_t r) { return (int32_t)((int64_t)INT32_MAX - (int64_t)(r >> 32)); }
+__host__ __device__ inline uint64_t cand_key(uint64_t r, int32_t v) { return (r & 0xffffffff00000000ull) | (uint32_t)v; }
+
+// Device-side counters of one call (one cache line each group).
+struct Counters {
+  unsigned long long n_moves;     // entries in the move list
+  unsigned long long n_cand;      // |M|
+  unsigned long long approved;    // afterburner-approved moves
+  unsigned long long n_deferred;  // warp-class edges handed to the block path
+  long long objective;            // (lambda-1), accumulated
+  long long rb_rounds;
+  long long rb_moves;
+  int rb_done;                    // rebalancing loop may stop
+  int rb_any;                     // an overloaded block exists
+  int err;                        // bit flags of data errors found on the device
+  int pad[7];
+};
+
+enum : int { kErrPartRange = 1, kErrPinRange = 2, kErrIncRange = 4, kErrOffsets = 8, kErrWeight = 16,
+             kErrTranspose = 32 };
+
+// Per-block state of one rebalancing round (Section 4.3).
+struct RbBlock {
+  long long bw;      // c(V_b) at the start of the round
+  long long cap;     // max c(v) that may still enter b (-1: overloaded or in the deadzone)
+  long long excess;  // c(V_b) - L_max if overloaded
+  int off;           // segment offset of b's rebalancing records
+  int over;          // 1 if c(V_b) > L_max
+};
+
+}  // namespace jet
+
+struct jet_ctx {
+  // problem (caller-owned device arrays)
+  int32_t n = 0, m = 0;
+  int64_t P = 0;
+  const int64_t *eptr = nullptr, *vptr = nullptr;
+  const int32_t *pins = nullptr, *inc = nullptr, *vwgt = nullptr, *ewgt = nullptr;
+  jet_params params{};
+  int32_t k = 0, kwp = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+
+  // balance constants (Section 2, Section 4.3)
+  int64_t W = 0, A = 0, Lmax = 0, dz_min = 0;
+  int64_t max_wdeg = 0;
+  int32_t cmax = 0;
+
+  // size classes
+  int32_t *v_light = nullptr, *v_heavy = nullptr;
+  int32_t n_light = 0, n_heavy = 0;
+  int32_t *e_tiny = nullptr, *e_mid = nullptr, *e_big = nullptr;  // e_big has room for deferred edges after n_big
+  int32_t n_tiny = 0, n_mid = 0, n_big = 0;
+
+  // workspace
+  uint32_t *mask = nullptr;
+  uint64_t *cand = nullptr;
+  int32_t *rg = nullptr;
+  int32_t *mv_v = nullptr;
+  uint32_t *mv_st = nullptr;
+  int32_t *vcount = nullptr;
+  jet::Counters *cnt = nullptr;
+  jet::Counters *cnt_host = nullptr;  // pinned mirror
+  jet::RbBlock *rbb = nullptr;
+  int32_t *rb_cursor = nullptr;
+  uint64_t *rb_key = nullptr;
+  int32_t *rb_v = nullptr;
+  int32_t *rb_ct = nullptr;           // c(v) << 8 | target
+  int32_t *best_part = nullptr;       // best balanced partition of jet_refine
+  uint8_t *locked_ws = nullptr;       // locks of jet_refine
+  jet_round_stats *stats_scratch = nullptr;
+  jet_round_stats *stats_host = nullptr;  // pinned
+
+  const int32_t *phi_owner = nullptr;  // phi whose bitmasks `mask` holds
+  char err[256] = {0};
+
+  // profiling: kernel launches (always counted) and event pairs per family
+  long long kernel_launches = 0;
+  long long fam_launches[JET_PROF_FAMILIES] = {0};
+  long long fam_calls[JET_PROF_FAMILIES] = {0};
+  double fam_ms[JET_PROF_FAMILIES] = {0};
+  int prof_on = 0;
+  static constexpr int kProfPairs = 2048;
+  cudaEvent_t *prof_ev = nullptr;  // 2 * kProfPairs events
+  int *prof_fam = nullptr;
+  int prof_n = 0;                  // pairs recorded and not yet read
+};
+
+namespace jet {
+
+// ---- launchers (one per kernel family); all enqueue on ctx->stream ----
+// state kernels (k_state.cu)
+cudaError_t launch_validate(jet_ctx *c, int64_t *wdeg_tmp, int32_t *degcount_tmp, unsigned long long *scal);
+cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg);
+cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int64_t *block_w);
+cudaError_t launch_masks_from_phi(jet_ctx *c, const int32_t *phi);
+cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *out);
+cudaError_t launch_objective_masks(jet_ctx *c);
+// candidates (k_cand.cu)
+cudaError_t launch_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, const int32_t *part, const int32_t *phi,
+                              const uint8_t *locked);
+cudaError_t launch_rebalance_candidates(jet_ctx *c, const int32_t *part, const int32_t *phi);
+// afterburner (k_ab.cu)
+cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi);
+cudaError_t launch_approve(jet_ctx *c, uint8_t *locked, int32_t *rg_out, uint8_t *approved_out, bool build_moves);
+cudaError_t launch_export_candidates(jet_ctx *c, int32_t *target, int32_t *gain, uint8_t *in_m);
+// moves, rebalancing, loop control (k_moves.cu)
+cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w);
+cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w);
+cudaError_t launch_rb_prep(jet_ctx *c, const int64_t *block_w);
+cudaError_t launch_rb_select(jet_ctx *c);
+cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w);
+cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *stats, int rebalance_only);
+cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best);
+
+inline int grid_for(int64_t items, int per_block, int num_sms, int blocks_per_sm = 8) {
+  int64_t g = (items + per_block - 1) / per_block;
+  int64_t cap = (int64_t)num_sms * blocks_per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace jet

@@ -1,0 +1,415 @@
+// State kernels: input validation, size classes, pin counts phi_e[i] with
+// their connectivity bitmasks, block weights, and the connectivity metric
+// (lambda-1) of Section 2.
+#include <vector>
+
+#include "jet_internal.cuh"
+
+namespace jet {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void add_i64(long long *p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+
+// Sum of a long long over the block, returned on thread 0.
+__device__ long long block_sum_ll(long long x) {
+  __shared__ long long s_part[32];
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s_part[w] = x;
+  __syncthreads();
+  long long tot = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += s_part[i];
+  __syncthreads();
+  return tot;
+}
+
+// ---------------------------------------------------------------- validation
+// Phase 1: offsets monotone and in range, weights positive and bounded.
+__global__ void k_validate_offsets(const int64_t *eptr, const int64_t *vptr, const int32_t *vwgt,
+                                   const int32_t *ewgt, int32_t n, int32_t m, int64_t P, Counters *cnt) {
+  int err = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)m + n + 2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i <= m) {  // eptr[i]
+      int64_t a = eptr[i];
+      if (a < 0 || a > P) err |= kErrOffsets;
+      if (i == 0 && a != 0) err |= kErrOffsets;
+      if (i == m && a != P) err |= kErrOffsets;
+      if (i < m && eptr[i + 1] < a) err |= kErrOffsets;
+      if (i < m && ewgt[i] < 1) err |= kErrWeight;
+    } else {
+      int64_t v = i - m - 1;  // vptr[v], v in [0, n]
+      int64_t a = vptr[v];
+      if (a < 0 || a > P) err |= kErrOffsets;
+      if (v == 0 && a != 0) err |= kErrOffsets;
+      if (v == n && a != P) err |= kErrOffsets;
+      if (v < n && vptr[v + 1] < a) err |= kErrOffsets;
+      if (v < n && vwgt[v] < 1) err |= kErrWeight;
+    }
+  }
+  if (err) atomicOr(&cnt->err, err);
+}
+
+// Phase 2: pin and incidence ids in range; occurrences of every vertex among the pins.
+__global__ void k_validate_ids(const int32_t *pins, const int32_t *inc, int32_t n, int32_t m, int64_t P,
+                               int32_t *degcount, Counters *cnt) {
+  int err = 0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = pins[p];
+    if (v < 0 || v >= n) err |= kErrPinRange;
+    else atomicAdd(&degcount[v], 1);
+    int32_t e = inc[p];
+    if (e < 0 || e >= m) err |= kErrIncRange;
+  }
+  if (err) atomicOr(&cnt->err, err);
+}
+
+// Phase 3: degree of the transpose, weighted degree sum of omega over I(v), c(V), max c(v).
+// scal[0] = c(V), scal[1] = max weighted degree, scal[2] = max c(v).
+__global__ void k_validate_degrees(const int64_t *vptr, const int32_t *inc, const int32_t *vwgt,
+                                   const int32_t *ewgt, int32_t n, const int32_t *degcount, int64_t *wdeg,
+                                   unsigned long long *scal, Counters *cnt) {
+  int err = 0;
+  long long wsum = 0;
+  unsigned long long wmax = 0, cm = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j0 = vptr[v], j1 = vptr[v + 1];
+    if (j1 - j0 != degcount[v]) err |= kErrTranspose;
+    long long d = 0;
+    for (int64_t j = j0; j < j1; ++j) d += ewgt[inc[j]];
+    wdeg[v] = d;
+    wmax = d > (long long)wmax ? (unsigned long long)d : wmax;
+    int32_t c = vwgt[v];
+    wsum += c;
+    cm = (unsigned long long)c > cm ? (unsigned long long)c : cm;
+  }
+  long long tot = block_sum_ll(wsum);
+  if (threadIdx.x == 0) atomicAdd(&scal[0], (unsigned long long)tot);
+  atomicMax(&scal[1], wmax);
+  atomicMax(&scal[2], cm);
+  if (err) atomicOr(&cnt->err, err);
+}
+
+// ---------------------------------------------------------------- classes
+// Stable three-way partition of ids [0, count) by class code (0, 1, 2).
+__global__ void k_class_count(const uint8_t *code, int32_t count, int32_t *blk_counts) {
+  __shared__ int s_c[3];
+  if (threadIdx.x < 3) s_c[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int c = i < count ? code[i] : 3;
+  for (int cl = 0; cl < 3; ++cl) {
+    unsigned b = __ballot_sync(kFull, c == cl);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&s_c[cl], __popc(b));
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) blk_counts[blockIdx.x * 3 + threadIdx.x] = s_c[threadIdx.x];
+}
+
+__global__ void k_class_scatter(const uint8_t *code, int32_t count, const int32_t *blk_off, int32_t *out) {
+  __shared__ int s_w[32][3];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int c = i < count ? code[i] : 3;
+  unsigned rank = 0;
+  for (int cl = 0; cl < 3; ++cl) {
+    unsigned b = __ballot_sync(kFull, c == cl);
+    if (lane == 0) s_w[w][cl] = __popc(b);
+    if (c == cl) rank = __popc(b & ((1u << lane) - 1));
+  }
+  __syncthreads();
+  if (c < 3) {
+    int base = blk_off[blockIdx.x * 3 + c];
+    for (int ww = 0; ww < w; ++ww) base += s_w[ww][c];
+    out[base + rank] = (int32_t)i;
+  }
+}
+
+__global__ void k_vertex_codes(const int64_t *wdeg, int32_t n, uint8_t *code) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    code[v] = wdeg[v] < (1ll << kLightPlanes) ? 0 : 1;
+}
+
+__global__ void k_edge_codes(const int64_t *eptr, int32_t m, uint8_t *code) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t sz = eptr[e + 1] - eptr[e];
+    code[e] = sz <= kTinyEdge ? 0 : (sz <= kWarpEdge ? 1 : 2);
+  }
+}
+
+// ---------------------------------------------------------------- pin counts
+// Warp per edge: histogram of the pins' blocks in shared memory, then one
+// coalesced store of the phi row and one ballot per mask word.
+__global__ void __launch_bounds__(256) k_pincounts(const int64_t *eptr, const int32_t *pins, const int32_t *part,
+                                                   int32_t m, int32_t k, int32_t kwp, int32_t *phi, uint32_t *mask,
+                                                   Counters *cnt) {
+  extern __shared__ int s_hist[];
+  const int lane = threadIdx.x & 31;
+  int *h = s_hist + (threadIdx.x >> 5) * k;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int err = 0;
+  for (int64_t e = gw; e < m; e += nw) {
+    for (int b = lane; b < k; b += 32) h[b] = 0;
+    __syncwarp();
+    const int64_t p1 = eptr[e + 1];
+    for (int64_t p = eptr[e] + lane; p < p1; p += 32) {
+      int b = part[pins[p]];
+      if ((unsigned)b < (unsigned)k) atomicAdd(&h[b], 1);
+      else err |= kErrPartRange;
+    }
+    __syncwarp();
+    int32_t *row = phi + e * k;
+    for (int q = 0; q < kwp; ++q) {
+      int b = q * 32 + lane;
+      int val = b < k ? h[b] : 0;
+      if (b < k) row[b] = val;
+      unsigned bits = __ballot_sync(kFull, val > 0);
+      if (lane == 0) mask[e * kwp + q] = bits;
+    }
+    __syncwarp();
+  }
+  if (err) atomicOr(&cnt->err, err);
+}
+
+// c(V_i) and |V_i|, aggregated per block in shared memory.
+__global__ void k_block_weights(const int32_t *part, const int32_t *vwgt, int32_t n, int32_t k, int64_t *bw,
+                                int32_t *vcount, Counters *cnt) {
+  __shared__ long long s_bw[kMaxK];
+  __shared__ int s_cnt[kMaxK];
+  for (int b = threadIdx.x; b < k; b += blockDim.x) { s_bw[b] = 0; s_cnt[b] = 0; }
+  __syncthreads();
+  int err = 0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int b = part[v];
+    if ((unsigned)b < (unsigned)k) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(&s_bw[b]), (unsigned long long)vwgt[v]);
+      atomicAdd(&s_cnt[b], 1);
+    } else {
+      err |= kErrPartRange;
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < k; b += blockDim.x) {
+    if (s_bw[b]) add_i64(reinterpret_cast<long long *>(&bw[b]), s_bw[b]);
+    if (s_cnt[b]) atomicAdd(&vcount[b], s_cnt[b]);
+  }
+  if (err) atomicOr(&cnt->err, err);
+}
+
+// Bitmasks of Lambda(e) from a dense phi (warp per edge).
+__global__ void __launch_bounds__(256) k_masks_from_phi(const int32_t *phi, int32_t m, int32_t k, int32_t kwp,
+                                                        uint32_t *mask) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = gw; e < m; e += nw) {
+    const int32_t *row = phi + e * k;
+    for (int q = 0; q < kwp; ++q) {
+      int b = q * 32 + lane;
+      unsigned bits = __ballot_sync(kFull, b < k && row[b] > 0);
+      if (lane == 0) mask[e * kwp + q] = bits;
+    }
+  }
+}
+
+// (lambda-1) from a dense phi: warp per edge counts the nonzero entries of its row.
+__global__ void __launch_bounds__(256) k_connectivity_dense(const int32_t *phi, const int32_t *ewgt, int32_t m,
+                                                            int32_t k, long long *out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  long long acc = 0;
+  for (int64_t e = gw; e < m; e += nw) {
+    const int32_t *row = phi + e * k;
+    int lam = 0;
+    for (int b0 = 0; b0 < k; b0 += 32) lam += __popc(__ballot_sync(kFull, b0 + lane < k && row[b0 + lane] > 0));
+    if (lane == 0 && lam > 0) acc += (long long)(lam - 1) * ewgt[e];
+  }
+  long long tot = block_sum_ll(acc);
+  if (threadIdx.x == 0 && tot) add_i64(out, tot);
+}
+
+// (lambda-1) from the bitmasks: thread per edge.
+__global__ void __launch_bounds__(256) k_objective_masks(const uint32_t *mask, const int32_t *ewgt, int32_t m,
+                                                         int32_t kwp, Counters *cnt) {
+  long long acc = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    int lam = 0;
+    for (int q = 0; q < kwp; ++q) lam += __popc(mask[e * kwp + q]);
+    if (lam > 0) acc += (long long)(lam - 1) * ewgt[e];
+  }
+  long long tot = block_sum_ll(acc);
+  if (threadIdx.x == 0 && tot) add_i64(&cnt->objective, tot);
+}
+
+}  // namespace
+
+cudaError_t launch_validate(jet_ctx *c, int64_t *wdeg_tmp, int32_t *degcount_tmp, unsigned long long *scal) {
+  // phases 1..3; the caller synchronizes and checks cnt->err between phases
+  cudaStream_t s = c->stream;
+  int g = grid_for((int64_t)c->m + c->n + 2, 256, c->num_sms);
+  k_validate_offsets<<<g, 256, 0, s>>>(c->eptr, c->vptr, c->vwgt, c->ewgt, c->n, c->m, c->P, c->cnt);
+  ++c->kernel_launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  if (c->cnt_host->err) return cudaSuccess;  // offsets unusable: stop before indexing with them
+  if (c->P > 0) {
+    k_validate_ids<<<grid_for(c->P, 256, c->num_sms), 256, 0, s>>>(c->pins, c->inc, c->n, c->m, c->P, degcount_tmp,
+                                                                    c->cnt);
+    ++c->kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  e = cudaMemcpyAsync(c->cnt_host, c->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  if (c->cnt_host->err) return cudaSuccess;
+  if (c->n > 0) {
+    k_validate_degrees<<<grid_for(c->n, 256, c->num_sms), 256, 0, s>>>(c->vptr, c->inc, c->vwgt, c->ewgt, c->n,
+                                                                        degcount_tmp, wdeg_tmp, scal, c->cnt);
+    ++c->kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Builds the class lists into one id array per kind (vertex: light, heavy;
+// edge: tiny, mid, big).  Synchronizes.
+static cudaError_t stable_partition(jet_ctx *c, const uint8_t *code, int32_t count, int32_t *out, int32_t totals[3]) {
+  totals[0] = totals[1] = totals[2] = 0;
+  if (count == 0) return cudaSuccess;
+  const int bs = 1024;
+  const int nb = (int)((count + bs - 1) / bs);
+  int32_t *d_cnt = nullptr, *d_off = nullptr;
+  cudaError_t e = cudaMallocAsync(&d_cnt, sizeof(int32_t) * 3 * nb, c->stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMallocAsync(&d_off, sizeof(int32_t) * 3 * nb, c->stream);
+  if (e != cudaSuccess) { cudaFreeAsync(d_cnt, c->stream); return e; }
+  std::vector<int32_t> h(3 * (size_t)nb);
+  k_class_count<<<nb, bs, 0, c->stream>>>(code, count, d_cnt);
+  ++c->kernel_launches;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_cnt, sizeof(int32_t) * 3 * nb, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) {
+    int64_t tot[3] = {0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+      for (int cl = 0; cl < 3; ++cl) tot[cl] += h[3 * b + cl];
+    int64_t run[3] = {0, tot[0], tot[0] + tot[1]};
+    for (int b = 0; b < nb; ++b)
+      for (int cl = 0; cl < 3; ++cl) {
+        int32_t x = h[3 * b + cl];
+        h[3 * b + cl] = (int32_t)run[cl];
+        run[cl] += x;
+      }
+    for (int cl = 0; cl < 3; ++cl) totals[cl] = (int32_t)tot[cl];
+    e = cudaMemcpyAsync(d_off, h.data(), sizeof(int32_t) * 3 * nb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+      k_class_scatter<<<nb, bs, 0, c->stream>>>(code, count, d_off, out);
+      ++c->kernel_launches;
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  cudaFreeAsync(d_cnt, c->stream);
+  cudaFreeAsync(d_off, c->stream);
+  return e;
+}
+
+cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
+  // vertex lists live in one array: [light | heavy]; edge lists in one array
+  // of m + (mid count) entries: [tiny | mid | big | room for deferred mid edges]
+  int64_t mx = c->n > c->m ? c->n : c->m;
+  uint8_t *code = nullptr;
+  cudaError_t e = cudaMallocAsync(&code, mx > 0 ? mx : 1, c->stream);
+  if (e != cudaSuccess) return e;
+  int32_t t[3];
+  if (c->n > 0) {
+    k_vertex_codes<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(wdeg, c->n, code);
+    ++c->kernel_launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = stable_partition(c, code, c->n, c->v_light, t);
+  if (e == cudaSuccess) {
+    c->n_light = t[0];
+    c->n_heavy = t[1];
+    c->v_heavy = c->v_light + t[0];
+    if (c->m > 0) {
+      k_edge_codes<<<grid_for(c->m, 256, c->num_sms), 256, 0, c->stream>>>(c->eptr, c->m, code);
+      ++c->kernel_launches;
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = stable_partition(c, code, c->m, c->e_tiny, t);
+  if (e == cudaSuccess) {
+    c->n_tiny = t[0];
+    c->n_mid = t[1];
+    c->n_big = t[2];
+    c->e_mid = c->e_tiny + t[0];
+    c->e_big = c->e_mid + t[1];
+  }
+  cudaFreeAsync(code, c->stream);
+  return e;
+}
+
+cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int64_t *block_w) {
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemsetAsync(block_w, 0, sizeof(int64_t) * c->k, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, s);
+  if (e != cudaSuccess) return e;
+  if (c->m > 0) {
+    const int threads = 256;
+    size_t smem = (size_t)(threads / 32) * c->k * sizeof(int);
+    k_pincounts<<<grid_for((int64_t)c->m * 32, threads, c->num_sms), threads, smem, s>>>(
+        c->eptr, c->pins, part, c->m, c->k, c->kwp, phi, c->mask, c->cnt);
+    ++c->kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (c->n > 0) {
+    k_block_weights<<<grid_for(c->n, 256, c->num_sms, 2), 256, 0, s>>>(part, c->vwgt, c->n, c->k, block_w,
+                                                                        c->vcount, c->cnt);
+    ++c->kernel_launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  c->phi_owner = phi;
+  return cudaSuccess;
+}
+
+cudaError_t launch_masks_from_phi(jet_ctx *c, const int32_t *phi) {
+  if (c->m > 0) {
+    k_masks_from_phi<<<grid_for((int64_t)c->m * 32, 256, c->num_sms), 256, 0, c->stream>>>(phi, c->m, c->k, c->kwp,
+                                                                                            c->mask);
+    ++c->kernel_launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  c->phi_owner = phi;
+  return cudaSuccess;
+}
+
+cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *out) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), c->stream);
+  if (e != cudaSuccess || c->m == 0) return e;
+  k_connectivity_dense<<<grid_for((int64_t)c->m * 32, 256, c->num_sms), 256, 0, c->stream>>>(
+      phi, c->ewgt, c->m, c->k, reinterpret_cast<long long *>(out));
+  ++c->kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective_masks(jet_ctx *c) {
+  cudaError_t e = cudaMemsetAsync(&c->cnt->objective, 0, sizeof(long long), c->stream);
+  if (e != cudaSuccess || c->m == 0) return e;
+  k_objective_masks<<<grid_for(c->m, 256, c->num_sms), 256, 0, c->stream>>>(c->mask, c->ewgt, c->m, c->kwp, c->cnt);
+  ++c->kernel_launches;
+  return cudaGetLastError();
+}
+
+}  // namespace jet

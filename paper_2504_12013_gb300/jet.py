@@ -1,0 +1,299 @@
+"""Python binding of libjet (``include/jet.h``): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes
+torch tensors (device memory) where the C function takes device pointers.
+All computation happens in the CUDA library; there is no CPU fallback.  If
+``lib/libjet.so`` is missing, every call raises ``RuntimeError``: build it
+with ``python -c "import __graft_entry__ as g; g.build()"``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libjet.so")
+
+JET_OK = 0
+ERRORS = {-1: "JET_ERR_INVALID_ARG", -2: "JET_ERR_OOM", -3: "JET_ERR_CUDA", -4: "JET_ERR_OVERFLOW", -5: "JET_ERR_DATA"}
+
+# every symbol include/jet.h declares
+EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pincounts", "jet_connectivity",
+           "jet_refine_round", "jet_rebalance", "jet_refine", "jet_candidates", "jet_afterburner",
+           "jet_refine_host", "jet_profile_enable", "jet_profile_read")
+
+PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
+                 "rebalance_select", "rebalance_control", "objective", "other")
+
+_P = ctypes.c_void_p
+
+
+class JetHypergraph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("P", ctypes.c_int64),
+                ("eptr", _P), ("pins", _P), ("vptr", _P), ("inc", _P), ("vwgt", _P), ("ewgt", _P)]
+
+
+class JetParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("eps_num", ctypes.c_int32), ("eps_den", ctypes.c_int32),
+                ("d_num", ctypes.c_int32), ("d_den", ctypes.c_int32), ("max_rebalance_rounds", ctypes.c_int32)]
+
+
+STATS_FIELDS = ("candidates", "approved", "rebalance_rounds", "rebalance_moves", "objective", "max_block_weight",
+                "imbalanced", "reserved")
+
+
+class JetRoundStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in STATS_FIELDS]
+
+
+class JetRefineResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("objective", ctypes.c_int64),
+                ("initial_objective", ctypes.c_int64), ("balanced", ctypes.c_int64),
+                ("phase_iterations", ctypes.c_int64 * 8)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "objective": self.objective,
+                "initial_objective": self.initial_objective, "balanced": self.balanced,
+                "phase_iterations": list(self.phase_iterations)}
+
+
+class JetError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library():
+    """Load libjet.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: the CUDA library has not been built "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            lib = ctypes.CDLL(LIB_PATH)
+            i32, i64, pp = ctypes.c_int32, ctypes.c_int64, ctypes.POINTER
+            lib.jet_ctx_create.argtypes = [pp(_P), pp(JetHypergraph), pp(JetParams), _P]
+            lib.jet_ctx_destroy.argtypes = [_P]
+            lib.jet_ctx_destroy.restype = None
+            lib.jet_last_error.argtypes = [_P]
+            lib.jet_last_error.restype = ctypes.c_char_p
+            lib.jet_build_pincounts.argtypes = [_P, _P, _P, _P]
+            lib.jet_connectivity.argtypes = [_P, _P, _P]
+            lib.jet_refine_round.argtypes = [_P, i32, i32, _P, _P, _P, _P, _P]
+            lib.jet_rebalance.argtypes = [_P, _P, _P, _P, _P]
+            lib.jet_refine.argtypes = [_P, pp(i32), i32, i32, _P, _P, _P, pp(JetRefineResult)]
+            lib.jet_candidates.argtypes = [_P, i32, i32, _P, _P, _P, _P, _P, _P]
+            lib.jet_afterburner.argtypes = [_P, _P, _P, _P, _P]
+            lib.jet_refine_host.argtypes = [pp(JetHypergraph), pp(JetParams), pp(i32), i32, i32, _P,
+                                            pp(JetRefineResult)]
+            lib.jet_profile_enable.argtypes = [_P, ctypes.c_int]
+            lib.jet_profile_read.argtypes = [_P, pp(ctypes.c_double), pp(i64), pp(i64), ctypes.c_int]
+            for f in EXPORTS:
+                if f not in ("jet_ctx_destroy", "jet_last_error"):
+                    getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _check(rc, ctx=None):
+    if rc != JET_OK:
+        raise JetError(rc, jet_last_error(ctx))
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class DeviceHypergraph:
+    """A host ``synth.Hypergraph`` uploaded to torch device tensors."""
+
+    def __init__(self, hg, device="cuda"):
+        import torch
+        self.n, self.m, self.P = hg.n, hg.m, hg.P
+        self.host = hg
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.eptr, self.pins, self.vptr, self.inc = t(hg.eptr), t(hg.pins), t(hg.vptr), t(hg.inc)
+        self.vwgt, self.ewgt = t(hg.vwgt), t(hg.ewgt)
+
+    def c(self) -> JetHypergraph:
+        import torch
+        return JetHypergraph(self.n, self.m, self.P, _ptr(self.eptr, torch.int64), _ptr(self.pins, torch.int32),
+                             _ptr(self.vptr, torch.int64), _ptr(self.inc, torch.int32),
+                             _ptr(self.vwgt, torch.int32), _ptr(self.ewgt, torch.int32))
+
+
+def params(k, eps=(3, 100), d=(1, 10), max_rebalance_rounds=32) -> JetParams:
+    return JetParams(k, eps[0], eps[1], d[0], d[1], max_rebalance_rounds)
+
+
+class Ctx:
+    """Owning handle of a jet_ctx; keeps the hypergraph tensors alive."""
+
+    def __init__(self, handle, hg, params_):
+        self.handle = handle
+        self.hg = hg
+        self.params = params_
+
+    @property
+    def k(self):
+        return self.params.k
+
+    def close(self):
+        if self.handle:
+            load_library().jet_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- C ABI names
+
+def jet_last_error(ctx=None) -> str:
+    h = ctx.handle if isinstance(ctx, Ctx) else ctx
+    return load_library().jet_last_error(h).decode()
+
+
+def jet_ctx_create(hg: DeviceHypergraph, p: JetParams, stream=None) -> Ctx:
+    lib = load_library()
+    out = _P()
+    chg = hg.c()
+    rc = lib.jet_ctx_create(ctypes.byref(out), ctypes.byref(chg), ctypes.byref(p), _stream_ptr(stream))
+    _check(rc)
+    return Ctx(out, hg, p)
+
+
+def jet_ctx_destroy(ctx: Ctx):
+    ctx.close()
+
+
+def jet_build_pincounts(ctx: Ctx, part, phi, block_w):
+    import torch
+    _check(load_library().jet_build_pincounts(ctx.handle, _ptr(part, torch.int32, "part"),
+                                              _ptr(phi, torch.int32, "phi"), _ptr(block_w, torch.int64, "block_w")),
+           ctx)
+
+
+def jet_connectivity(ctx: Ctx, phi, objective_out):
+    import torch
+    _check(load_library().jet_connectivity(ctx.handle, _ptr(phi, torch.int32, "phi"),
+                                           _ptr(objective_out, torch.int64, "objective_out")), ctx)
+
+
+def jet_refine_round(ctx: Ctx, tau, part, phi, block_w, locked, stats=None):
+    import torch
+    _check(load_library().jet_refine_round(ctx.handle, int(tau[0]), int(tau[1]), _ptr(part, torch.int32, "part"),
+                                           _ptr(phi, torch.int32, "phi"), _ptr(block_w, torch.int64, "block_w"),
+                                           _ptr(locked, torch.uint8, "locked"), _ptr(stats, torch.int64, "stats")),
+           ctx)
+
+
+def jet_rebalance(ctx: Ctx, part, phi, block_w, stats=None):
+    import torch
+    _check(load_library().jet_rebalance(ctx.handle, _ptr(part, torch.int32, "part"), _ptr(phi, torch.int32, "phi"),
+                                        _ptr(block_w, torch.int64, "block_w"), _ptr(stats, torch.int64, "stats")),
+           ctx)
+
+
+def jet_refine(ctx: Ctx, schedule, limit, part, phi, block_w) -> dict:
+    import torch
+    pairs = (ctypes.c_int32 * (2 * len(schedule)))(*[int(x) for t in schedule for x in t])
+    res = JetRefineResult()
+    _check(load_library().jet_refine(ctx.handle, pairs, len(schedule), int(limit), _ptr(part, torch.int32, "part"),
+                                     _ptr(phi, torch.int32, "phi"), _ptr(block_w, torch.int64, "block_w"),
+                                     ctypes.byref(res)), ctx)
+    return res.as_dict()
+
+
+def jet_candidates(ctx: Ctx, tau, part, phi, locked, target, gain, in_m):
+    import torch
+    _check(load_library().jet_candidates(ctx.handle, int(tau[0]), int(tau[1]), _ptr(part, torch.int32, "part"),
+                                         _ptr(phi, torch.int32, "phi"), _ptr(locked, torch.uint8, "locked"),
+                                         _ptr(target, torch.int32, "target"), _ptr(gain, torch.int32, "gain"),
+                                         _ptr(in_m, torch.uint8, "in_m")), ctx)
+
+
+def jet_afterburner(ctx: Ctx, part, phi, rg, approved):
+    import torch
+    _check(load_library().jet_afterburner(ctx.handle, _ptr(part, torch.int32, "part"), _ptr(phi, torch.int32, "phi"),
+                                          _ptr(rg, torch.int32, "rg"), _ptr(approved, torch.uint8, "approved")), ctx)
+
+
+def jet_refine_host(hg, p: JetParams, schedule, limit, part: np.ndarray) -> dict:
+    """Host buffers in and out: ``hg`` is a ``synth.Hypergraph`` (numpy), ``part`` int32[n] is refined in place."""
+    assert part.dtype == np.int32 and part.flags.c_contiguous
+    arrs = [np.ascontiguousarray(a) for a in (hg.eptr, hg.pins, hg.vptr, hg.inc, hg.vwgt, hg.ewgt)]
+    ch = JetHypergraph(hg.n, hg.m, hg.P, *[a.ctypes.data for a in arrs])
+    pairs = (ctypes.c_int32 * (2 * len(schedule)))(*[int(x) for t in schedule for x in t])
+    res = JetRefineResult()
+    rc = load_library().jet_refine_host(ctypes.byref(ch), ctypes.byref(p), pairs, len(schedule), int(limit),
+                                        part.ctypes.data, ctypes.byref(res))
+    _check(rc)
+    return res.as_dict()
+
+
+def jet_profile_enable(ctx: Ctx, enable: bool = True):
+    _check(load_library().jet_profile_enable(ctx.handle, 1 if enable else 0), ctx)
+
+
+def jet_profile_read(ctx: Ctx, reset: bool = True) -> dict:
+    """Per kernel family: device ms (while enabled), timed calls, kernel launches."""
+    n = len(PROF_FAMILIES)
+    ms = (ctypes.c_double * n)()
+    calls = (ctypes.c_int64 * n)()
+    launches = (ctypes.c_int64 * n)()
+    _check(load_library().jet_profile_read(ctx.handle, ms, calls, launches, 1 if reset else 0), ctx)
+    return {f: {"ms": ms[i], "calls": calls[i], "launches": launches[i]} for i, f in enumerate(PROF_FAMILIES)}
+
+
+# ---------------------------------------------------------------- state helper
+
+class JetState:
+    """Device state of one refinement: Pi, phi, c(V_i), locks and a stats slot."""
+
+    def __init__(self, ctx: Ctx, part):
+        import torch
+        dev = ctx.hg.eptr.device
+        self.ctx = ctx
+        self.part = torch.as_tensor(part, dtype=torch.int32).to(dev).contiguous()
+        self.phi = torch.empty(max(ctx.hg.m * ctx.k, 1), dtype=torch.int32, device=dev)
+        self.block_w = torch.empty(ctx.k, dtype=torch.int64, device=dev)
+        self.locked = torch.zeros(max(ctx.hg.n, 1), dtype=torch.uint8, device=dev)
+        self.stats = torch.zeros(8, dtype=torch.int64, device=dev)
+        jet_build_pincounts(ctx, self.part, self.phi, self.block_w)
+
+    def round(self, tau):
+        jet_refine_round(self.ctx, tau, self.part, self.phi, self.block_w, self.locked, self.stats)
+
+    def stats_dict(self):
+        return dict(zip(STATS_FIELDS[:7], [int(x) for x in self.stats.cpu().tolist()[:7]]))
