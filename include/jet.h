@@ -230,6 +230,30 @@ int jet_refine_host(const jet_hypergraph *hg_host, const jet_params *params, con
 int jet_profile_enable(jet_ctx *ctx, int enable);
 int jet_profile_read(jet_ctx *ctx, double *ms_out, int64_t *calls_out, int64_t *launches_out, int reset);
 
+/*
+ * Block weights without any device allocation (the paper has no counterpart;
+ * this is a deployment variant of the block-weight pass of
+ * jet_build_pincounts).  For callers that must not allocate device memory:
+ * applications that give the whole device to their own pool, and loops where
+ * a cudaMalloc/cudaFree would stall the device too long.  No context is
+ * needed.
+ *   part[n] (device, values in [0,k)), vwgt[n] (device, c(v)) in;
+ *   block_w[k] (device int64, overwritten) = c(V_i);
+ *   block_count[k] (device int32, may be NULL) = |V_i|;
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * Scratch: a file-scope device array of 1.25 KiB per GPU, resident until
+ * process exit, limits k to [2, 256] (JET_ERR_INVALID_ARG otherwise).  The
+ * first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  Every call clears the array first; calls that
+ * overlap on the GPU share it and race.  Allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call).  Synchronizes the stream to read the
+ * data-error flag: a value of part outside [0,k) returns JET_ERR_DATA.
+ * Errors are reported by jet_last_error(NULL).
+ */
+int jet_block_weights_noalloc(const int32_t *part, const int32_t *vwgt, int32_t n, int32_t k, int64_t *block_w,
+                              int32_t *block_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -151,6 +151,13 @@ int check_tau(jet_ctx *c, int32_t tau_num, int32_t tau_den) {
 
 }  // namespace
 
+void jet::set_global_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
 extern "C" {
 
 const char *jet_last_error(const jet_ctx *ctx) { return ctx ? ctx->err : g_err; }

@@ -155,6 +155,9 @@ cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w);
 cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *stats, int rebalance_only);
 cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best);
 
+// Sets the message returned by jet_last_error(NULL) (for entry points without a context).
+void set_global_error(const char *fmt, ...);
+
 inline int grid_for(int64_t items, int per_block, int num_sms, int blocks_per_sm = 8) {
   int64_t g = (items + per_block - 1) / per_block;
   int64_t cap = (int64_t)num_sms * blocks_per_sm;

@@ -23,7 +23,7 @@ ERRORS = {-1: "JET_ERR_INVALID_ARG", -2: "JET_ERR_OOM", -3: "JET_ERR_CUDA", -4: 
 # every symbol include/jet.h declares
 EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pincounts", "jet_connectivity",
            "jet_refine_round", "jet_rebalance", "jet_refine", "jet_candidates", "jet_afterburner",
-           "jet_refine_host", "jet_profile_enable", "jet_profile_read")
+           "jet_refine_host", "jet_profile_enable", "jet_profile_read", "jet_block_weights_noalloc")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -96,6 +96,7 @@ def load_library():
                                             pp(JetRefineResult)]
             lib.jet_profile_enable.argtypes = [_P, ctypes.c_int]
             lib.jet_profile_read.argtypes = [_P, pp(ctypes.c_double), pp(i64), pp(i64), ctypes.c_int]
+            lib.jet_block_weights_noalloc.argtypes = [_P, _P, i32, i32, _P, _P, _P]
             for f in EXPORTS:
                 if f not in ("jet_ctx_destroy", "jet_last_error"):
                     getattr(lib, f).restype = ctypes.c_int
@@ -274,6 +275,16 @@ def jet_profile_read(ctx: Ctx, reset: bool = True) -> dict:
     launches = (ctypes.c_int64 * n)()
     _check(load_library().jet_profile_read(ctx.handle, ms, calls, launches, 1 if reset else 0), ctx)
     return {f: {"ms": ms[i], "calls": calls[i], "launches": launches[i]} for i, f in enumerate(PROF_FAMILIES)}
+
+
+def jet_block_weights_noalloc(part, vwgt, k, block_w, block_count=None, stream=None):
+    """c(V_i) (and |V_i|) with no device allocation; scratch is a static device array (k <= 256)."""
+    import torch
+    n = part.numel()
+    _check(load_library().jet_block_weights_noalloc(_ptr(part, torch.int32, "part"), _ptr(vwgt, torch.int32, "vwgt"),
+                                                    n, int(k), _ptr(block_w, torch.int64, "block_w"),
+                                                    _ptr(block_count, torch.int32, "block_count"),
+                                                    _stream_ptr(stream)))
 
 
 # ---------------------------------------------------------------- state helper
