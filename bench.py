@@ -115,8 +115,7 @@ def kernel_bytes(hg, k, deg, st_before, round_stats):
     b = 8 * (n + 1) + 4 * n + n + 4 * int(unlocked.sum())  # vptr, vertex list, locks, own block
     b += 4 * Pu                                              # incidences of unlocked vertices
     b += min(4 * Pu, 4 * m)                                  # omega(e) gathers
-    b += min(4 * kw * Pu, 4 * kw * m)                        # Lambda(e) bitmask gathers
-    b += min(4 * Pu, 4 * m * k)                              # phi_e[s] gathers
+    b += min(8 * kw * Pu, 8 * kw * m)                        # bitmask rows (phi >= 1, phi >= 2) gathers
     b += 8 * n                                               # candidate records written
     return b
 
@@ -318,7 +317,10 @@ def main():
                      "frac": (achieved / hbm) if achieved else None, "traffic": None,
                      "peak_source": peak_src,
                      "dominant_family": dom, "family_share": {f: round(v / total_fam, 4) for f, v in fam_ms.items()}
-                     if total_fam > 0 else {}},
+                     if total_fam > 0 else {},
+                     "family_ms_per_step": {f: round(v / args.steps, 4) for f, v in fam_ms.items()},
+                     "candidates_ms_per_step": cand_ms / args.steps,
+                     "model_bytes_per_step": r["model_bytes"] / args.steps},
         "clocks": r["clocks"],
         "gpu_launches": launches,
         "e2e": e2e,

@@ -133,7 +133,7 @@ int rebalance_loop(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   for (;;) {
     CKP(F_RB_CTL, launch_rb_prep(c, block_w), "rebalance prep");
     CKP(F_RB_TGT, launch_rebalance_candidates(c, part, phi), "rebalance targets");
-    CKP(F_RB_SEL, launch_rb_select(c), "rebalance select");
+    CKP(F_RB_SEL, launch_rb_select(c, part), "rebalance select");
     CKP(F_APPLY, launch_apply(c, part, phi, block_w), "rebalance apply");
     CKP(F_RB_CTL, launch_rb_post(c, block_w), "rebalance post");
     rc = sync_counters(c);
@@ -239,13 +239,32 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     const __int128 R = (__int128)p->d_den * ((int64_t)p->eps_den + p->eps_num) * A - (__int128)p->d_num * p->eps_num * A;
     const __int128 D = (__int128)p->eps_den * p->d_den;
     c->dz_min = (int64_t)ceil_div(R, D);
+    {  // exact 32-bit rebalancing priorities when lcm(1..cmax) keeps them small
+      __int128 L = 1;
+      for (int x = 2; x <= c->cmax && L < ((__int128)1 << 40); ++x) {
+        __int128 a = L, b = x;
+        while (b) { __int128 t = a % b; a = b; b = t; }
+        L = L / a * x;
+      }
+      const __int128 span = (__int128)c->max_wdeg * (c->cmax + L);
+      c->rb_compact = (L < ((__int128)1 << 40) && span < ((__int128)1 << 32)) ? 1 : 0;
+      c->rb_L = c->rb_compact ? (int64_t)L : 1;
+      c->rb_Pmax = (int64_t)c->max_wdeg * c->cmax;
+      int hb = 0;
+      while (hb < 64 && (((__int128)1 << hb) <= span)) ++hb;  // bit length of the largest priority part
+      c->rb_hbits = c->rb_compact ? hb : 64;
+      int vb = 1;
+      while (vb < 31 && (1ll << vb) < (long long)c->n) ++vb;  // vertex ids need vb bits
+      c->rb_vbits = vb;
+    }
     // class lists, workspace
-    if ((e = dalloc(c, &c->v_light, c->n)) != cudaSuccess || (e = dalloc(c, &c->e_tiny, 2 * (size_t)c->m)) != cudaSuccess ||
-        (e = dalloc(c, &c->mask, (size_t)c->m * c->kwp)) != cudaSuccess || (e = dalloc(c, &c->cand, c->n)) != cudaSuccess ||
+    if ((e = dalloc(c, &c->v_light, c->n)) != cudaSuccess || (e = dalloc(c, &c->e_tiny, (size_t)c->m)) != cudaSuccess ||
+        (e = dalloc(c, &c->mask, (size_t)c->m * 2 * c->kwp)) != cudaSuccess || (e = dalloc(c, &c->cand, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->rg, c->n)) != cudaSuccess || (e = dalloc(c, &c->mv_v, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->mv_st, c->n)) != cudaSuccess || (e = dalloc(c, &c->vcount, c->k)) != cudaSuccess ||
-        (e = dalloc(c, &c->rbb, c->k)) != cudaSuccess || (e = dalloc(c, &c->rb_cursor, c->k)) != cudaSuccess ||
-        (e = dalloc(c, &c->rb_key, c->n)) != cudaSuccess || (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->rbb, c->k)) != cudaSuccess || (e = dalloc(c, &c->rb_hi, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->rb_hist, (size_t)c->k * kRbBins)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_ct, c->n)) != cudaSuccess || (e = dalloc(c, &c->best_part, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->locked_ws, c->n)) != cudaSuccess || (e = dalloc(c, &c->stats_scratch, 1)) != cudaSuccess ||
         (e = cudaMallocHost(reinterpret_cast<void **>(&c->stats_host), sizeof(jet_round_stats))) != cudaSuccess) {
@@ -254,7 +273,8 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     }
     if ((e = cudaMemsetAsync(c->rg, 0, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->cand, 0, sizeof(uint64_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, c->stream)) != cudaSuccess) {
+        (e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->rb_hist, 0, sizeof(unsigned long long) * c->k * kRbBins, c->stream)) != cudaSuccess) {
       rc = cuda_fail(c, e, "workspace init");
       break;
     }
@@ -277,7 +297,7 @@ void jet_ctx_destroy(jet_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
-                 c->rb_cursor, c->rb_key, c->rb_v, c->rb_ct, c->best_part, c->locked_ws, c->stats_scratch};
+                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->stats_scratch};
   for (void *p : dev) dfree(c, p);
   cudaStreamSynchronize(c->stream);
   if (c->prof_ev) {

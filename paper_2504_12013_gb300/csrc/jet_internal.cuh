@@ -5,9 +5,9 @@
 //                 part[n], phi[m*k] (row-major by edge), block_w[k] (int64),
 //                 locked[n] (uint8)
 //   context-owned (workspace):
-//     mask[m*KWP]    uint32 bitmask of Lambda(e) = {i : phi_e[i] > 0}, KWP
-//                    words per edge (KWP = ceil(k/32) rounded up to 1,2,4,8
-//                    so a row is one aligned vector load)
+//     mask[m*2*KWP]  per edge KWP uint32 words of Lambda(e) = {i : phi_e[i] > 0}
+//                    then KWP words of {i : phi_e[i] > 1} (KWP = ceil(k/32)
+//                    rounded up to 1,2,4,8, so a row is aligned vector loads)
 //     cand[n]        uint64 move-candidate record (0 = not in M), see below
 //     rg[n]          recomputed gain of Algorithm 2 (zeroed after use)
 //     mv_v/mv_st[n]  move list: vertex, (source | target << 16)
@@ -52,10 +52,11 @@ struct Counters {
   long long objective;            // (lambda-1), accumulated
   long long rb_rounds;
   long long rb_moves;
+  unsigned long long n_rec;       // rebalancing records of the current round
   int rb_done;                    // rebalancing loop may stop
   int rb_any;                     // an overloaded block exists
   int err;                        // bit flags of data errors found on the device
-  int pad[7];
+  int pad[5];
 };
 
 enum : int { kErrPartRange = 1, kErrPinRange = 2, kErrIncRange = 4, kErrOffsets = 8, kErrWeight = 16,
@@ -63,12 +64,18 @@ enum : int { kErrPartRange = 1, kErrPinRange = 2, kErrIncRange = 4, kErrOffsets 
 
 // Per-block state of one rebalancing round (Section 4.3).
 struct RbBlock {
-  long long bw;      // c(V_b) at the start of the round
-  long long cap;     // max c(v) that may still enter b (-1: overloaded or in the deadzone)
-  long long excess;  // c(V_b) - L_max if overloaded
-  int off;           // segment offset of b's rebalancing records
-  int over;          // 1 if c(V_b) > L_max
+  long long bw;                  // c(V_b) at the start of the round
+  long long cap;                 // max c(v) that may still enter b (-1: overloaded or in the deadzone)
+  long long excess;              // c(V_b) - L_max if overloaded
+  long long before;              // selection: weight of b's records below the fixed key prefix
+  unsigned long long pre_hi;     // selection: fixed prefix of the threshold key (high word)
+  unsigned long long pre_lo;     //   ... (low word)
+  int over;                      // 1 if c(V_b) > L_max
+  int all;                       // selection: every record of b moves
 };
+
+constexpr int kRbDigitBits = 11;  // radix-select digit width
+constexpr int kRbBins = 1 << kRbDigitBits;
 
 }  // namespace jet
 
@@ -87,11 +94,15 @@ struct jet_ctx {
   int64_t W = 0, A = 0, Lmax = 0, dz_min = 0;
   int64_t max_wdeg = 0;
   int32_t cmax = 0;
+  // compact rebalancing keys: priority gain*c (gain >= 0) or gain*(L/c) (gain < 0), L = lcm(1..cmax),
+  // stored as (Pmax - P) << 32 | v when max_wdeg*(cmax + L) < 2^32
+  int rb_compact = 0;
+  int64_t rb_L = 1, rb_Pmax = 0;
 
   // size classes
   int32_t *v_light = nullptr, *v_heavy = nullptr;
   int32_t n_light = 0, n_heavy = 0;
-  int32_t *e_tiny = nullptr, *e_mid = nullptr, *e_big = nullptr;  // e_big has room for deferred edges after n_big
+  int32_t *e_tiny = nullptr, *e_mid = nullptr, *e_big = nullptr;  // one array of m ids: [tiny | mid | big]
   int32_t n_tiny = 0, n_mid = 0, n_big = 0;
 
   // workspace
@@ -104,10 +115,11 @@ struct jet_ctx {
   jet::Counters *cnt = nullptr;
   jet::Counters *cnt_host = nullptr;  // pinned mirror
   jet::RbBlock *rbb = nullptr;
-  int32_t *rb_cursor = nullptr;
-  uint64_t *rb_key = nullptr;
-  int32_t *rb_v = nullptr;
-  int32_t *rb_ct = nullptr;           // c(v) << 8 | target
+  uint64_t *rb_hi = nullptr;          // per record: priority part of the rebalancing key
+  int32_t *rb_v = nullptr;            // per record: vertex
+  int32_t *rb_ct = nullptr;           // per record: c(v) << 16 | block << 8 | target
+  unsigned long long *rb_hist = nullptr;  // k x kRbBins weighted digit histograms (zero between uses)
+  int rb_hbits = 0, rb_vbits = 1;     // key = rb_hi << rb_vbits | v, rb_hbits + rb_vbits significant bits
   int32_t *best_part = nullptr;       // best balanced partition of jet_refine
   uint8_t *locked_ws = nullptr;       // locks of jet_refine
   jet_round_stats *stats_scratch = nullptr;
@@ -150,10 +162,35 @@ cudaError_t launch_export_candidates(jet_ctx *c, int32_t *target, int32_t *gain,
 cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w);
 cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w);
 cudaError_t launch_rb_prep(jet_ctx *c, const int64_t *block_w);
-cudaError_t launch_rb_select(jet_ctx *c);
+cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part);
 cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w);
 cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *stats, int rebalance_only);
 cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best);
+
+// Block-wide append to a global list: every thread of the block calls it (same
+// iteration); each thread with `sel` gets a distinct slot.  One atomicAdd per
+// block instead of one per warp keeps the list counter from serializing.
+// s_wc: blockDim.x/32 unsigned, s_base: one unsigned long long, both shared.
+__device__ __forceinline__ unsigned long long block_append(bool sel, unsigned long long *counter, unsigned *s_wc,
+                                                           unsigned long long *s_base) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned bal = __ballot_sync(0xffffffffu, sel);
+  if (lane == 0) s_wc[wid] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int i = 0; i < nw; ++i) {
+      const unsigned x = s_wc[i];
+      s_wc[i] = tot;
+      tot += x;
+    }
+    *s_base = tot ? atomicAdd(counter, (unsigned long long)tot) : 0ull;
+  }
+  __syncthreads();
+  const unsigned long long pos = *s_base + s_wc[wid] + __popc(bal & ((1u << lane) - 1));
+  __syncthreads();
+  return pos;
+}
 
 // Sets the message returned by jet_last_error(NULL) (for entry points without a context).
 void set_global_error(const char *fmt, ...);

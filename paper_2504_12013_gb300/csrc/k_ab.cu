@@ -17,12 +17,14 @@
 // most one pays -omega(e) (the first arrival), and both need
 // phi_e[b] = |D_b| and max(D_b) < min(R_b) in the order.  This is the same
 // result as the replay, computed with counts and a max/min per block.
+// phi_e[b] = |D_b| holds exactly when no pin of e outside M lies in b, which
+// the kernels test with a bitmask of the blocks of e's non-candidate pins
+// (gathered from the partition), so the afterburner reads no phi entry.
 //
 // Size classes: |e| <= 8 one thread per edge (pairwise tests in registers);
-// 8 < |e| <= 2048 one warp per edge, candidates gathered in shared memory,
-// pairwise tests over at most 32 candidates; larger edges and warp-class
-// edges with more than 32 candidates: one block per edge with per-block
-// counters / max / min in shared memory.
+// 8 < |e| <= 2048 one warp per edge and > 2048 one thread block per edge,
+// both with a per-block max / min table and a non-candidate bitmask in
+// shared memory.
 #include "jet_internal.cuh"
 
 namespace jet {
@@ -32,39 +34,14 @@ constexpr unsigned kFull = 0xffffffffu;
 
 struct AbArgs {
   const int64_t *eptr;
-  const int32_t *pins, *ewgt, *phi;
+  const int32_t *pins, *ewgt, *part;
   const uint64_t *cand;
   int32_t *rg;
   int32_t k;
   const int32_t *elist;
   int32_t nlist;
-  int32_t *deferred;  // append area for warp-class edges with > 32 candidates
-  int32_t n_big;
   Counters *cnt;
 };
-
-// Contribution of candidate i (key K, source s, target t) of edge e given the
-// other candidates' (key, s|t<<8) through `get(j)`, j < cnt.
-template <class Get>
-__device__ __forceinline__ int pin_delta(const AbArgs &a, int64_t e, int w, uint64_t K, int s, int t, int cnt,
-                                         Get get) {
-  bool last_dep = true, no_arr_before = true, first_arr = true, no_dep_after = true;
-  int n_src_s = 0, n_src_t = 0;
-  for (int j = 0; j < cnt; ++j) {
-    uint64_t Kj;
-    uint32_t stj;
-    get(j, Kj, stj);
-    const int sj = stj & 255, tj = stj >> 8;
-    if (sj == s) { ++n_src_s; if (Kj > K) last_dep = false; }
-    if (tj == s && Kj < K) no_arr_before = false;
-    if (tj == t && Kj < K) first_arr = false;
-    if (sj == t) { ++n_src_t; if (Kj > K) no_dep_after = false; }
-  }
-  int delta = 0;
-  if (last_dep && no_arr_before && a.phi[e * a.k + s] == n_src_s) delta += w;
-  if (first_arr && no_dep_after && a.phi[e * a.k + t] == n_src_t) delta -= w;
-  return delta;
-}
 
 __global__ void __launch_bounds__(256) k_ab_tiny(AbArgs a) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nlist; i += gridDim.x * blockDim.x) {
@@ -72,44 +49,56 @@ __global__ void __launch_bounds__(256) k_ab_tiny(AbArgs a) {
     const int64_t p0 = a.eptr[e];
     const int sz = (int)(a.eptr[e + 1] - p0);
     uint64_t key[kTinyEdge];
-    uint32_t st[kTinyEdge];
+    uint32_t st[kTinyEdge];  // s | t << 8 | 1 << 16 for a candidate; block | 1 << 17 for another pin
+    int vid[kTinyEdge];
     int nin = 0;
 #pragma unroll
     for (int q = 0; q < kTinyEdge; ++q) {
       key[q] = 0;
       st[q] = 0;
+      vid[q] = 0;
       if (q < sz) {
         const int v = a.pins[p0 + q];
         const uint64_t r = a.cand[v];
+        vid[q] = v;
         if (r) {
           ++nin;
           key[q] = cand_key(r, v);
-          st[q] = (uint32_t)cand_s(r) | ((uint32_t)cand_t(r) << 8) | 0x10000u;  // bit 16: in M
+          st[q] = (uint32_t)cand_s(r) | ((uint32_t)cand_t(r) << 8) | 0x10000u;
+        } else {
+          st[q] = 0x20000u;
         }
       }
     }
     if (nin == 0) continue;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q)
+      if (st[q] & 0x20000u) st[q] |= (uint32_t)(a.part[vid[q]] & 255);  // block of a non-candidate pin
     const int w = a.ewgt[e];
 #pragma unroll
     for (int q = 0; q < kTinyEdge; ++q) {
       if (!(st[q] & 0x10000u)) continue;
       const int s = st[q] & 255, t = (st[q] >> 8) & 255;
       const uint64_t K = key[q];
-      bool last_dep = true, no_arr_before = true, first_arr = true, no_dep_after = true;
-      int n_src_s = 0, n_src_t = 0;
+      bool last_dep = true, no_arr_before = true, first_arr = true, no_dep_after = true, nm_s = false, nm_t = false;
 #pragma unroll
       for (int r = 0; r < kTinyEdge; ++r) {
+        if (st[r] & 0x20000u) {
+          const int br = st[r] & 255;
+          nm_s |= br == s;
+          nm_t |= br == t;
+        }
         if (!(st[r] & 0x10000u)) continue;
         const int sr = st[r] & 255, tr = (st[r] >> 8) & 255;
         const uint64_t Kr = key[r];
-        if (sr == s) { ++n_src_s; if (Kr > K) last_dep = false; }
+        if (sr == s && Kr > K) last_dep = false;
         if (tr == s && Kr < K) no_arr_before = false;
         if (tr == t && Kr < K) first_arr = false;
-        if (sr == t) { ++n_src_t; if (Kr > K) no_dep_after = false; }
+        if (sr == t && Kr > K) no_dep_after = false;
       }
       int delta = 0;
-      if (last_dep && no_arr_before && a.phi[(int64_t)e * a.k + s] == n_src_s) delta += w;
-      if (first_arr && no_dep_after && a.phi[(int64_t)e * a.k + t] == n_src_t) delta -= w;
+      if (last_dep && no_arr_before && !nm_s) delta += w;
+      if (first_arr && no_dep_after && !nm_t) delta -= w;
       if (delta) atomicAdd(&a.rg[(int)(K & 0xffffffffu)], delta);
     }
   }
@@ -117,71 +106,76 @@ __global__ void __launch_bounds__(256) k_ab_tiny(AbArgs a) {
 
 constexpr int kAbWarps = 8;
 
+// Warp per edge (8 < |e| <= 2048): the per-block form of the replay in
+// shared memory, one table per warp: max key of the departures and min key
+// of the arrivals of every block, and the blocks holding a non-candidate pin.
+// A key is never 0 (its high word is INT32_MAX - gain >= 1), so max = 0 means
+// "no departure" and min = ~0 "no arrival".
 __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
-  __shared__ uint64_t s_key[kAbWarps][kWarpEdgeSlots];
-  __shared__ uint32_t s_st[kAbWarps][kWarpEdgeSlots];
+  extern __shared__ unsigned long long s_tab[];  // per warp: maxd[k], mina[k]
+  __shared__ uint32_t s_nm[kAbWarps][kMaxK / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long *maxd = s_tab + (size_t)w * 2 * a.k;
+  unsigned long long *mina = maxd + a.k;
+  uint32_t *nm = s_nm[w];
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int i = gw; i < a.nlist; i += nw) {
     const int e = a.elist[i];
     const int64_t p0 = a.eptr[e], p1 = a.eptr[e + 1];
-    int cnt = 0;
-    bool overflow = false;
-    for (int64_t base = p0; base < p1; base += 32) {
-      const int64_t p = base + lane;
-      uint64_t r = 0;
-      int v = 0;
-      if (p < p1) {
-        v = a.pins[p];
-        r = a.cand[v];
-      }
-      const unsigned bal = __ballot_sync(kFull, r != 0);
-      const int pos = cnt + __popc(bal & ((1u << lane) - 1));
-      if (r != 0 && pos < kWarpEdgeSlots) {
-        s_key[w][pos] = cand_key(r, v);
-        s_st[w][pos] = (uint32_t)cand_s(r) | ((uint32_t)cand_t(r) << 8);
-      }
-      cnt += __popc(bal);
-      if (cnt > kWarpEdgeSlots) { overflow = true; break; }
+    for (int b = lane; b < a.k; b += 32) {
+      maxd[b] = 0ull;
+      mina[b] = ~0ull;
     }
+    if (lane < kMaxK / 32) nm[lane] = 0;
     __syncwarp();
-    if (overflow) {
-      if (lane == 0) {
-        const unsigned long long slot = atomicAdd(&a.cnt->n_deferred, 1ull);
-        a.deferred[slot] = e;
+    bool any = false;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const int v = a.pins[p];
+      const uint64_t r = a.cand[v];
+      if (r) {
+        any = true;
+        const uint64_t K = cand_key(r, v);
+        atomicMax(&maxd[cand_s(r)], (unsigned long long)K);
+        atomicMin(&mina[cand_t(r)], (unsigned long long)K);
+      } else {
+        const int b = a.part[v] & 255;
+        atomicOr(&nm[b >> 5], 1u << (b & 31));
       }
-      __syncwarp();
-      continue;
     }
-    if (lane < cnt) {
-      const uint64_t K = s_key[w][lane];
-      const int s = s_st[w][lane] & 255, t = s_st[w][lane] >> 8;
-      const int delta = pin_delta(a, e, a.ewgt[e], K, s, t, cnt, [&](int j, uint64_t &Kj, uint32_t &stj) {
-        Kj = s_key[w][j];
-        stj = s_st[w][j];
-      });
-      if (delta) atomicAdd(&a.rg[(int)(K & 0xffffffffu)], delta);
+    any = __any_sync(kFull, any);
+    __syncwarp();
+    if (any) {
+      const int wt = a.ewgt[e];
+      for (int b = lane; b < a.k; b += 32) {
+        const unsigned long long md = maxd[b], ma = mina[b];
+        const bool has_d = md != 0ull, has_a = ma != ~0ull;
+        if (!has_d && !has_a) continue;
+        if ((nm[b >> 5] >> (b & 31)) & 1u) continue;  // a pin of e in b stays
+        if (has_d && has_a && !(md < ma)) continue;
+        if (has_d) atomicAdd(&a.rg[(int)(md & 0xffffffffu)], wt);
+        if (has_a) atomicAdd(&a.rg[(int)(ma & 0xffffffffu)], -wt);
+      }
     }
     __syncwarp();
   }
 }
 
-// Block per edge: the big class (a.elist[0..n_big)) and the deferred
-// warp-class edges (a.deferred[0..n_deferred)).
+// Block per edge: the big class (|e| > 2048).
 __global__ void __launch_bounds__(512) k_ab_block(AbArgs a) {
   extern __shared__ unsigned long long s_mem[];
   unsigned long long *s_maxd = s_mem;            // k: max key among departures
   unsigned long long *s_mina = s_mem + a.k;      // k: min key among arrivals
   int *s_cntd = reinterpret_cast<int *>(s_mem + 2 * a.k);  // k: number of departures
-  const int total = a.n_big + (int)a.cnt->n_deferred;
-  for (int i = blockIdx.x; i < total; i += gridDim.x) {
-    const int e = i < a.n_big ? a.elist[i] : a.deferred[i - a.n_big];
+  __shared__ uint32_t s_nm[kMaxK / 32];          // blocks holding a non-candidate pin
+  for (int i = blockIdx.x; i < a.nlist; i += gridDim.x) {
+    const int e = a.elist[i];
     for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
       s_maxd[b] = 0ull;
       s_mina[b] = ~0ull;
       s_cntd[b] = 0;
     }
+    if (threadIdx.x < kMaxK / 32) s_nm[threadIdx.x] = 0;
     __syncthreads();
     const int64_t p1 = a.eptr[e + 1];
     for (int64_t p = a.eptr[e] + threadIdx.x; p < p1; p += blockDim.x) {
@@ -193,6 +187,10 @@ __global__ void __launch_bounds__(512) k_ab_block(AbArgs a) {
         atomicAdd(&s_cntd[s], 1);
         atomicMax(&s_maxd[s], (unsigned long long)K);
         atomicMin(&s_mina[t], (unsigned long long)K);
+      } else {
+        const int b = a.part[v] & 255;
+        const uint32_t bit = 1u << (b & 31);
+        if (!(s_nm[b >> 5] & bit)) atomicOr(&s_nm[b >> 5], bit);
       }
     }
     __syncthreads();
@@ -201,7 +199,7 @@ __global__ void __launch_bounds__(512) k_ab_block(AbArgs a) {
       const int nd = s_cntd[b];
       const bool has_a = s_mina[b] != ~0ull;
       if (nd == 0 && !has_a) continue;
-      if (a.phi[(int64_t)e * a.k + b] != nd) continue;  // a pin of e in b stays
+      if ((s_nm[b >> 5] >> (b & 31)) & 1u) continue;  // a pin of e in b stays
       if (nd > 0 && has_a && !(s_maxd[b] < s_mina[b])) continue;
       if (nd > 0) atomicAdd(&a.rg[(int)(s_maxd[b] & 0xffffffffu)], w);
       if (has_a) atomicAdd(&a.rg[(int)(s_mina[b] & 0xffffffffu)], -w);
@@ -225,8 +223,16 @@ struct ApArgs {
   Counters *cnt;
 };
 
+// Counters and move-list slots are aggregated per thread block (one atomic
+// per block and iteration) rather than per warp, which would serialize on
+// the few counter addresses.
 __global__ void __launch_bounds__(256) k_approve(ApArgs a) {
-  const int lane = threadIdx.x & 31;
+  constexpr int kWarps = 256 / 32;
+  __shared__ unsigned s_wc[kWarps];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned long long s_cand[kWarps];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long ncand = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     const bool valid = v < a.n;
@@ -240,22 +246,36 @@ __global__ void __launch_bounds__(256) k_approve(ApArgs a) {
       if (a.rg_out) a.rg_out[v] = g;
       if (a.approved_out) a.approved_out[v] = ap ? 1 : 0;
     }
-    const unsigned bin = __ballot_sync(kFull, in);
-    const unsigned bap = __ballot_sync(kFull, ap);
-    if (lane == 0 && bin) atomicAdd(&a.cnt->n_cand, (unsigned long long)__popc(bin));
+    ncand += __popc(__ballot_sync(kFull, in));
     if (a.build_moves) {
-      unsigned long long pos0 = 0;
-      if (lane == 0 && bap) {
-        pos0 = atomicAdd(&a.cnt->n_moves, (unsigned long long)__popc(bap));
-        atomicAdd(&a.cnt->approved, (unsigned long long)__popc(bap));
+      const unsigned bap = __ballot_sync(kFull, ap);
+      if (lane == 0) s_wc[wid] = __popc(bap);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int i = 0; i < kWarps; ++i) {
+          const unsigned x = s_wc[i];
+          s_wc[i] = tot;
+          tot += x;
+        }
+        s_base = tot ? atomicAdd(&a.cnt->n_moves, (unsigned long long)tot) : 0ull;
+        if (tot) atomicAdd(&a.cnt->approved, (unsigned long long)tot);
       }
-      pos0 = __shfl_sync(kFull, pos0, 0);
+      __syncthreads();
       if (ap) {
-        const unsigned long long pos = pos0 + __popc(bap & ((1u << lane) - 1));
+        const unsigned long long pos = s_base + s_wc[wid] + __popc(bap & ((1u << lane) - 1));
         a.mv_v[pos] = (int32_t)v;
         a.mv_st[pos] = (uint32_t)cand_s(r) | ((uint32_t)cand_t(r) << 16);
       }
+      __syncthreads();
     }
+  }
+  if (lane == 0) s_cand[wid] = ncand;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int i = 0; i < kWarps; ++i) t += s_cand[i];
+    if (t) atomicAdd(&a.cnt->n_cand, t);
   }
 }
 
@@ -271,20 +291,16 @@ __global__ void k_export_cand(const uint64_t *cand, int32_t n, int32_t *target, 
 }  // namespace
 
 cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi) {
-  (void)part;
+  (void)phi;  // phi_e[b] = |D_b| is tested through the non-candidate pins' blocks
   AbArgs a{};
   a.eptr = c->eptr;
   a.pins = c->pins;
   a.ewgt = c->ewgt;
-  a.phi = phi;
+  a.part = part;
   a.cand = c->cand;
   a.rg = c->rg;
   a.k = c->k;
   a.cnt = c->cnt;
-  a.deferred = c->e_big + c->n_big;
-  a.n_big = c->n_big;
-  cudaError_t e = cudaMemsetAsync(&c->cnt->n_deferred, 0, sizeof(unsigned long long), c->stream);
-  if (e != cudaSuccess) return e;
   if (c->n_tiny > 0) {
     a.elist = c->e_tiny;
     a.nlist = c->n_tiny;
@@ -294,13 +310,14 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
   if (c->n_mid > 0) {
     a.elist = c->e_mid;
     a.nlist = c->n_mid;
-    k_ab_warp<<<grid_for((int64_t)c->n_mid * 32, kAbWarps * 32, c->num_sms), kAbWarps * 32, 0, c->stream>>>(a);
+    const size_t smem = (size_t)kAbWarps * 2 * c->k * sizeof(unsigned long long);
+    k_ab_warp<<<grid_for((int64_t)c->n_mid * 32, kAbWarps * 32, c->num_sms), kAbWarps * 32, smem, c->stream>>>(a);
     ++c->kernel_launches;
   }
-  if (c->n_mid > 0 || c->n_big > 0) {
+  if (c->n_big > 0) {
     a.elist = c->e_big;
     a.nlist = c->n_big;
-    size_t smem = (size_t)c->k * (2 * sizeof(unsigned long long) + sizeof(int));
+    const size_t smem = (size_t)c->k * (2 * sizeof(unsigned long long) + sizeof(int));
     k_ab_block<<<c->num_sms * 2, 512, smem, c->stream>>>(a);
     ++c->kernel_launches;
   }

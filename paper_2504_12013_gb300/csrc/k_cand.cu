@@ -2,7 +2,8 @@
 //
 // gain(v, b) = conn(v, b) - A(v) for v in V_s, where conn(v, b) = sum of
 // omega(e) over e in I(v) with phi_e[b] >= 1 and A(v) = sum of omega(e) over
-// e in I(v) with phi_e[s] >= 2.  (Per edge, [phi_e[s] = 1] - [phi_e[b] = 0]
+// e in I(v) with phi_e[s] >= 2.  Both come from the two bitmasks of each
+// edge (phi_e[.] >= 1 and >= 2), so this pass reads no phi entry.  (Per edge, [phi_e[s] = 1] - [phi_e[b] = 0]
 // = [phi_e[b] >= 1] - [phi_e[s] >= 2], which is the +-omega rule of
 // Algorithm 2 summed over I(v).)
 //
@@ -32,30 +33,43 @@ struct CandArgs {
   uint64_t *cand;
   // rebalancing
   const RbBlock *rbb;
-  int32_t *rb_cursor;
-  uint64_t *rb_key;
+  uint64_t *rb_hi;
   int32_t *rb_v, *rb_ct;
   long long A;
   int32_t n;
   Counters *cnt;
+  int rb_compact;
+  long long rb_L, rb_Pmax;
 };
 
+// One edge's mask row: KWP words of Lambda(e) then KWP words of the blocks
+// with >= 2 pins of e (aligned vector loads, 2*KWP*4 bytes).
 template <int KWP>
-__device__ __forceinline__ void load_mask(const uint32_t *row, uint32_t (&M)[KWP]) {
+__device__ __forceinline__ void load_rows(const uint32_t *row, uint32_t (&M)[KWP], uint32_t (&M2)[KWP]) {
   if constexpr (KWP == 1) {
-    M[0] = __ldg(row);
+    const uint2 x = __ldg(reinterpret_cast<const uint2 *>(row));
+    M[0] = x.x; M2[0] = x.y;
   } else if constexpr (KWP == 2) {
-    uint2 x = __ldg(reinterpret_cast<const uint2 *>(row));
-    M[0] = x.x; M[1] = x.y;
-  } else if constexpr (KWP == 4) {
-    uint4 x = __ldg(reinterpret_cast<const uint4 *>(row));
-    M[0] = x.x; M[1] = x.y; M[2] = x.z; M[3] = x.w;
+    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(row));
+    M[0] = x.x; M[1] = x.y; M2[0] = x.z; M2[1] = x.w;
   } else {
-    uint4 x = __ldg(reinterpret_cast<const uint4 *>(row));
-    uint4 y = __ldg(reinterpret_cast<const uint4 *>(row) + 1);
-    M[0] = x.x; M[1] = x.y; M[2] = x.z; M[3] = x.w;
-    M[4] = y.x; M[5] = y.y; M[6] = y.z; M[7] = y.w;
+#pragma unroll
+    for (int h = 0; h < KWP / 4; ++h) {
+      const uint4 x = __ldg(reinterpret_cast<const uint4 *>(row) + h);
+      const uint4 y = __ldg(reinterpret_cast<const uint4 *>(row + KWP) + h);
+      M[4 * h] = x.x; M[4 * h + 1] = x.y; M[4 * h + 2] = x.z; M[4 * h + 3] = x.w;
+      M2[4 * h] = y.x; M2[4 * h + 1] = y.y; M2[4 * h + 2] = y.z; M2[4 * h + 3] = y.w;
+    }
   }
+}
+
+// bit b of a KWP-word mask (word chosen without dynamic register indexing)
+template <int KWP>
+__device__ __forceinline__ bool mask_bit(const uint32_t (&M)[KWP], int b) {
+  uint32_t x = 0;
+#pragma unroll
+  for (int q = 0; q < KWP; ++q) x |= (q == (b >> 5)) ? M[q] : 0u;
+  return (x >> (b & 31)) & 1u;
 }
 
 // planes += w * M  (w < 2^NP, no overflow past the top plane by construction)
@@ -124,10 +138,9 @@ __device__ __forceinline__ int32_t accumulate_light(const CandArgs &a, int v, in
   for (int64_t j = a.vptr[v]; j < j1; ++j) {
     const int e = a.inc[j];
     const int w = a.ewgt[e];
-    const int ph = a.phi[(int64_t)e * a.k + s];
-    A += ph >= 2 ? w : 0;
-    uint32_t M[KWP];
-    load_mask<KWP>(a.mask + (int64_t)e * KWP, M);
+    uint32_t M[KWP], M2[KWP];
+    load_rows<KWP>(a.mask + (int64_t)e * 2 * KWP, M, M2);
+    A += mask_bit<KWP>(M2, s) ? w : 0;  // phi_e[s] >= 2
 #pragma unroll
     for (int q = 0; q < KWP; ++q) any[q] |= M[q];
     add_weighted<KWP, NP>(pl, M, (uint32_t)w);
@@ -190,14 +203,14 @@ __device__ __forceinline__ int32_t accumulate_heavy(const CandArgs &a, int v, in
     const int64_t j = base + lane;
     const bool ok = j < j1;
     int e = 0, w = 0;
-    uint32_t M[KWP];
+    uint32_t M[KWP], M2[KWP];
 #pragma unroll
-    for (int q = 0; q < KWP; ++q) M[q] = 0;
+    for (int q = 0; q < KWP; ++q) M[q] = M2[q] = 0;
     if (ok) {
       e = a.inc[j];
       w = a.ewgt[e];
-      load_mask<KWP>(a.mask + (int64_t)e * KWP, M);
-      if (a.phi[(int64_t)e * a.k + s] >= 2) Ap += w;
+      load_rows<KWP>(a.mask + (int64_t)e * 2 * KWP, M, M2);
+      if (mask_bit<KWP>(M2, s)) Ap += w;  // phi_e[s] >= 2
     }
     const int cntc = (int)((j1 - base) < 32 ? (j1 - base) : 32);
     for (int l = 0; l < cntc; ++l) {
@@ -258,20 +271,22 @@ __global__ void __launch_bounds__(256) k_cand_heavy(CandArgs a) {
 // truncation keeps their order; equal ratios stay equal.  All gain < 0 keys
 // are <= -2^15 < 0 <= every gain >= 0 key, so the classes keep their order.
 // U = INT64_MAX - P (mod 2^64) turns "priority desc" into "U asc".
+// Compact form (rb_compact): with L = lcm(1..cmax), gain/c = gain*(L/c) / L,
+// so gain*(L/c) orders the gain < 0 class exactly (equal ratios stay equal)
+// and stays <= -1 < 0 <= gain*c of the gain >= 0 class; Pmax - P is then
+// below 2^32 (checked by the context) and needs far fewer key bits.
 __device__ __forceinline__ uint64_t rb_order_key(int32_t g, int32_t c) {
   long long P = g >= 0 ? (long long)g * c : ((long long)g * (1ll << kPrioShift)) / c;
   return (uint64_t)0x7fffffffffffffffull - (uint64_t)P;
 }
 
-__device__ __forceinline__ void rb_emit(const CandArgs &a, int s, int v, int32_t c, int t, int32_t g) {
-  const int pos = a.rbb[s].off + atomicAdd(&a.rb_cursor[s], 1);
-  if (pos >= a.n) {  // block sizes out of step with the partition: report instead of writing
-    atomicOr(&a.cnt->err, kErrPartRange);
-    return;
+// Record of v for the selection: the priority part of its key and (c, target).
+__device__ __forceinline__ uint64_t rb_hi_of(const CandArgs &a, int32_t g, int32_t c) {
+  if (a.rb_compact) {
+    const long long P = g >= 0 ? (long long)g * c : (long long)g * (a.rb_L / c);
+    return (uint64_t)(a.rb_Pmax - P);
   }
-  a.rb_key[pos] = rb_order_key(g, c);
-  a.rb_v[pos] = v;
-  a.rb_ct[pos] = (c << 8) | t;
+  return rb_order_key(g, c);
 }
 
 template <int KWP>
@@ -310,28 +325,48 @@ __global__ void __launch_bounds__(256) k_rbcand_light(CandArgs a) {
     s_elig[c - 1][q] = w;
   }
   __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nlist; i += gridDim.x * blockDim.x) {
-    const int v = a.vlist[i];
-    const int s = a.part[v];
-    if ((unsigned)s >= (unsigned)a.k || !s_over[s]) continue;
-    const int32_t c = a.vwgt[v];
-    if (2ll * c > 3ll * (s_bw[s] - a.A)) continue;  // heavy vertex: never moved
-    uint32_t C[KWP];
-    if (c <= kTab) {
+  __shared__ unsigned s_wc[8];
+  __shared__ unsigned long long s_base;
+  for (int base = blockIdx.x * blockDim.x; base < a.nlist; base += gridDim.x * blockDim.x) {
+    const int i = base + threadIdx.x;
+    bool rec = false;
+    int v = 0, s = 0;
+    uint64_t hi = 0;
+    int32_t ct = 0;
+    if (i < a.nlist) {
+      v = a.vlist[i];
+      s = a.part[v];
+      if ((unsigned)s < (unsigned)a.k && s_over[s]) {
+        const int32_t c = a.vwgt[v];
+        if (2ll * c <= 3ll * (s_bw[s] - a.A)) {  // heavy vertices are never moved
+          uint32_t C[KWP];
+          if (c <= kTab) {
 #pragma unroll
-      for (int q = 0; q < KWP; ++q) C[q] = s_elig[c - 1][q];
-    } else {
-      eligible_words<KWP>(s_cap, a.k, c, C);
+            for (int q = 0; q < KWP; ++q) C[q] = s_elig[c - 1][q];
+          } else {
+            eligible_words<KWP>(s_cap, a.k, c, C);
+          }
+          uint32_t nz = 0;
+#pragma unroll
+          for (int q = 0; q < KWP; ++q) nz |= C[q];
+          if (nz) {
+            uint32_t pl[NP][KWP], any[KWP];
+            const int32_t A = accumulate_light<KWP, NP>(a, v, s, pl, any);
+            int32_t conn;
+            const int t = argmax_planes<KWP, NP>(pl, C, conn);
+            hi = rb_hi_of(a, conn - A, c);
+            ct = (c << 16) | (s << 8) | t;
+            rec = true;
+          }
+        }
+      }
     }
-    uint32_t nz = 0;
-#pragma unroll
-    for (int q = 0; q < KWP; ++q) nz |= C[q];
-    if (!nz) continue;
-    uint32_t pl[NP][KWP], any[KWP];
-    const int32_t A = accumulate_light<KWP, NP>(a, v, s, pl, any);
-    int32_t conn;
-    const int t = argmax_planes<KWP, NP>(pl, C, conn);
-    rb_emit(a, s, v, c, t, conn - A);
+    const unsigned long long pos = block_append(rec, &a.cnt->n_rec, s_wc, &s_base);
+    if (rec) {
+      a.rb_hi[pos] = hi;
+      a.rb_v[pos] = v;
+      a.rb_ct[pos] = ct;
+    }
   }
 }
 
@@ -351,16 +386,16 @@ __global__ void __launch_bounds__(256) k_rbcand_heavy(CandArgs a) {
   for (int i = gw; i < a.nlist; i += nw) {
     const int v = a.vlist[i];
     const int s = a.part[v];
-    if ((unsigned)s >= (unsigned)a.k || !s_over[s]) continue;
     const int32_t c = a.vwgt[v];
-    if (2ll * c > 3ll * (s_bw[s] - a.A)) continue;
     bool any_elig = false;
+    if ((unsigned)s < (unsigned)a.k && s_over[s] && 2ll * c <= 3ll * (s_bw[s] - a.A)) {
 #pragma unroll
-    for (int q = 0; q < KWP; ++q) {
-      const int b = q * 32 + lane;
-      any_elig |= b < a.k && s_cap[b] >= c;
+      for (int q = 0; q < KWP; ++q) {
+        const int b = q * 32 + lane;
+        any_elig |= b < a.k && s_cap[b] >= c;
+      }
     }
-    if (!__any_sync(kFull, any_elig)) continue;
+    if (!__any_sync(kFull, any_elig)) continue;  // no record (warp-uniform: one vertex per warp)
     int32_t conn[KWP];
     uint32_t adj;
     const int32_t A = accumulate_heavy<KWP>(a, v, s, conn, adj);
@@ -372,7 +407,12 @@ __global__ void __launch_bounds__(256) k_rbcand_heavy(CandArgs a) {
       if (b < a.k && s_cap[b] >= c && (bb < 0 || conn[q] > bc)) { bb = b; bc = conn[q]; }
     }
     warp_argmax(bc, bb);
-    if (lane == 0) rb_emit(a, s, v, c, bb, bc - A);
+    if (lane == 0) {
+      const unsigned long long pos = atomicAdd(&a.cnt->n_rec, 1ull);
+      a.rb_hi[pos] = rb_hi_of(a, bc - A, c);
+      a.rb_v[pos] = v;
+      a.rb_ct[pos] = (c << 16) | (s << 8) | bb;
+    }
   }
 }
 
@@ -424,13 +464,15 @@ CandArgs make_args(jet_ctx *c, const int32_t *part, const int32_t *phi) {
   a.k = c->k;
   a.cand = c->cand;
   a.rbb = c->rbb;
-  a.rb_cursor = c->rb_cursor;
-  a.rb_key = c->rb_key;
+  a.rb_hi = c->rb_hi;
   a.rb_v = c->rb_v;
   a.rb_ct = c->rb_ct;
   a.A = c->A;
   a.n = c->n;
   a.cnt = c->cnt;
+  a.rb_compact = c->rb_compact;
+  a.rb_L = c->rb_L;
+  a.rb_Pmax = c->rb_Pmax;
   return a;
 }
 

@@ -3,8 +3,8 @@
 //
 // All updates are integer atomics whose final values do not depend on their
 // order: phi row entries +-1, block weights and counts aggregated per thread
-// block, and the Lambda(e) bitmasks (set the target bit during the move, then
-// clear the source bit only if the final phi entry is 0).
+// block; after all moves a second pass sets the bits of the source and target
+// blocks in both edge bitmasks from the final phi entries.
 #include "jet_internal.cuh"
 
 namespace jet {
@@ -49,12 +49,10 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
     atomicSub(&s_dc[s], 1);
     atomicAdd(&s_dc[t], 1);
     const int64_t j1 = a.vptr[v + 1];
-    const uint32_t tbit = 1u << (t & 31);
     for (int64_t j = a.vptr[v]; j < j1; ++j) {
       const int64_t e = a.inc[j];
       atomicSub(&a.phi[e * a.k + s], 1);
       atomicAdd(&a.phi[e * a.k + t], 1);
-      atomicOr(&a.mask[e * a.kwp + (t >> 5)], tbit);
     }
   }
   __syncthreads();
@@ -64,31 +62,61 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   }
 }
 
-// After all moves: clear the source bit of Lambda(e) where phi_e[s] reached 0.
+// Set one bit of a mask word to `on` (skipping the atomic if it already is).
+// Every writer of a bit writes its final value, so a stale read that already
+// shows that value can never hide a needed change.
+__device__ __forceinline__ void put_bit(uint32_t *w, uint32_t bit, bool on) {
+  const uint32_t cur = __ldcg(w);
+  if (((cur & bit) != 0) == on) return;
+  if (on) atomicOr(w, bit);
+  else atomicAnd(w, ~bit);
+}
+
+// After all moves: bring the bits of s and t in both masks of every e in I(v)
+// to their final values (phi_e[.] >= 1 and >= 2), read from the final phi.
 __global__ void __launch_bounds__(256) k_fix_masks(MoveArgs a) {
   const long long nm = (long long)a.cnt->n_moves;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nm; i += (long long)gridDim.x * blockDim.x) {
     const int v = a.mv_v[i];
-    const int s = a.mv_st[i] & 0xffff;
+    const uint32_t st = a.mv_st[i];
+    const int s = st & 0xffff, t = st >> 16;
+    const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
     const int64_t j1 = a.vptr[v + 1];
     for (int64_t j = a.vptr[v]; j < j1; ++j) {
       const int64_t e = a.inc[j];
-      if (a.phi[e * a.k + s] == 0) atomicAnd(&a.mask[e * a.kwp + (s >> 5)], ~(1u << (s & 31)));
+      const int ps = __ldcg(&a.phi[e * a.k + s]), pt = __ldcg(&a.phi[e * a.k + t]);
+      uint32_t *row = a.mask + e * 2 * a.kwp;
+      put_bit(&row[s >> 5], sbit, ps > 0);
+      put_bit(&row[a.kwp + (s >> 5)], sbit, ps > 1);
+      put_bit(&row[t >> 5], tbit, pt > 0);
+      put_bit(&row[a.kwp + (t >> 5)], tbit, pt > 1);
     }
   }
 }
 
 // ---------------------------------------------------------------- rebalancing
+// Selection of the minimal prefix per overloaded block (Section 4.3) as a
+// radix select over all records at once.  Every vertex v of an overloaded
+// block with a valid target has a record with the key
+// K(v) = hi(v) << vb | v  (priority descending, then id ascending, as one
+// ascending number of hb + vb bits; 64-bit when it fits, else 128-bit).
+// Per level (kRbDigitBits bits, from the top) one grid-wide kernel adds c(v)
+// of every record that matches its block's fixed prefix into the (block,
+// digit) histogram, and one small kernel per overloaded block picks the
+// digit at which the cumulative weight reaches the excess.  After the last
+// level the prefix is the threshold key, and every record up to it moves.
+typedef unsigned __int128 u128;
+
 struct RbArgs {
   const int64_t *bw;
-  const int32_t *vcount;
   RbBlock *rbb;
-  int32_t *rb_cursor;
-  const uint64_t *rb_key;
-  const int32_t *rb_v, *rb_ct;
+  const uint64_t *rb_hi;
+  const int32_t *rb_v, *rb_ct;  // record: vertex; c << 16 | block << 8 | target
+  unsigned long long *hist;
   int32_t *mv_v;
   uint32_t *mv_st;
-  int32_t k;
+  int32_t n, k;
+  int vbits, tbits;
   long long Lmax, dz_min;
   int32_t max_rounds;
   Counters *cnt;
@@ -106,148 +134,146 @@ __global__ void k_rb_check(RbArgs a) {
 }
 
 // Per-block state of the round: overloaded flag, excess, target capacity
-// (deadzone and L_max), record segment offsets (exclusive scan of |V_b|).
+// (deadzone and L_max), cleared selection state.
 __global__ void k_rb_prep(RbArgs a) {
-  __shared__ int s_scan[kMaxK];
   const int b = threadIdx.x;
-  long long bwb = 0;
-  int cntb = 0;
   if (b < a.k) {
-    bwb = a.bw[b];
-    cntb = a.vcount[b];
-  }
-  s_scan[b] = cntb;
-  __syncthreads();
-  for (int o = 1; o < kMaxK; o <<= 1) {  // inclusive Hillis-Steele scan over 256 entries
-    int x = b >= o ? s_scan[b - o] : 0;
-    __syncthreads();
-    s_scan[b] += x;
-    __syncthreads();
-  }
-  if (b < a.k) {
+    const long long bwb = a.bw[b];
     RbBlock r;
     r.bw = bwb;
     r.over = bwb > a.Lmax ? 1 : 0;
     r.excess = r.over ? bwb - a.Lmax : 0;
     r.cap = (r.over || bwb >= a.dz_min) ? -1 : a.Lmax - bwb;
-    r.off = s_scan[b] - cntb;
+    r.before = 0;
+    r.pre_hi = 0;
+    r.pre_lo = 0;
+    r.all = 0;
     a.rbb[b] = r;
-    a.rb_cursor[b] = 0;
   }
-  if (b == 0) a.cnt->n_moves = 0;
+  if (b == 0) {
+    a.cnt->n_moves = 0;
+    a.cnt->n_rec = 0;
+  }
 }
 
-// One block per overloaded block b: the minimal prefix of b's records in the
-// order (U asc, v asc) whose weight reaches the excess, found by an MSD radix
-// select over the 96-bit key (U, v) with 8-bit digits; then every record up to
-// that threshold joins the move list.
-constexpr int kSelThreads = 512;
+template <class KT>
+__device__ __forceinline__ KT rb_full_key(uint64_t hi, int v, int vbits) {
+  return ((KT)hi << vbits) | (KT)(uint32_t)v;
+}
 
-__global__ void __launch_bounds__(kSelThreads) k_rb_select(RbArgs a) {
+template <class KT>
+__device__ __forceinline__ KT rb_prefix(const RbBlock &r) {
+  if constexpr (sizeof(KT) > 8) return ((KT)r.pre_hi << 64) | (KT)r.pre_lo;
+  else return (KT)r.pre_lo;
+}
+
+// One level: digit = bits [lo, lo + w) of K(v) for the records whose higher bits
+// equal their block's prefix; weights aggregated per warp and (block, digit).
+template <class KT>
+__global__ void __launch_bounds__(256) k_rb_level(RbArgs a, int lo, int w) {
+  const int lane = threadIdx.x & 31;
+  const int up = lo + w;
+  const KT dmask = ((KT)1 << w) - 1;
+  const long long nrec = (long long)a.cnt->n_rec;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nrec; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    bool m = false;
+    int b = 0, d = 0;
+    unsigned c = 0;
+    if (i < nrec) {
+      const int32_t ct = a.rb_ct[i];
+      b = (ct >> 8) & 255;
+      const RbBlock &r = a.rbb[b];
+      if (!r.all) {
+        const KT K = rb_full_key<KT>(a.rb_hi[i], a.rb_v[i], a.vbits);
+        m = up >= a.tbits || (K >> up) == (rb_prefix<KT>(r) >> up);
+        d = (int)((K >> lo) & dmask);
+        c = (unsigned)(ct >> 16);
+      }
+    }
+    const int code = m ? (b << kRbDigitBits) | d : -1 - lane;
+    const unsigned grp = __match_any_sync(kFull, code);
+    const unsigned sum = __reduce_add_sync(grp, c);
+    if (m && lane == __ffs(grp) - 1) atomicAdd(&a.hist[(int64_t)b * kRbBins + d], (unsigned long long)sum);
+  }
+}
+
+// Per overloaded block: the digit at which the cumulative weight first reaches
+// the excess; at the first level a total below the excess selects everything.
+// Leaves the histogram row zeroed.
+__global__ void __launch_bounds__(256) k_rb_pick(RbArgs a, int lo, int first) {
   const int b = blockIdx.x;
-  const RbBlock bb = a.rbb[b];
-  if (!bb.over) return;
-  const int len = a.rb_cursor[b];
-  const uint64_t *key = a.rb_key + bb.off;
-  const int32_t *vv = a.rb_v + bb.off;
-  const int32_t *ct = a.rb_ct + bb.off;
-  __shared__ long long s_hist[256];
-  __shared__ long long s_part[kSelThreads / 32];
-  __shared__ unsigned long long s_pu;
-  __shared__ unsigned s_pv;
-  __shared__ long long s_before;
-  __shared__ int s_all;
+  RbBlock *r = &a.rbb[b];
+  if (!r->over || r->all) return;
+  constexpr int kPer = kRbBins / 256;
+  unsigned long long *row = a.hist + (int64_t)b * kRbBins;
+  __shared__ long long s_warp[8];
+  __shared__ long long s_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-
-  long long tw = 0;
-  for (int i = threadIdx.x; i < len; i += blockDim.x) tw += ct[i] >> 8;
-  for (int o = 16; o > 0; o >>= 1) tw += __shfl_xor_sync(kFull, tw, o);
-  if (lane == 0) s_part[wid] = tw;
+  long long loc[kPer];
+  long long sum = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    loc[q] = (long long)row[threadIdx.x * kPer + q];
+    sum += loc[q];
+  }
+  long long incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
   __syncthreads();
+  long long wbase = 0;
+  for (int i = 0; i < wid; ++i) wbase += s_warp[i];
   if (threadIdx.x == 0) {
     long long t = 0;
-    for (int i = 0; i < kSelThreads / 32; ++i) t += s_part[i];
-    s_all = t < bb.excess;
-    s_pu = 0;
-    s_pv = 0;
-    s_before = 0;
+    for (int i = 0; i < 8; ++i) t += s_warp[i];
+    s_total = t;
   }
+  const long long excl = wbase + incl - sum;
+  const long long before = r->before, need = r->excess;
   __syncthreads();
-  if (!s_all) {
-    for (int level = 0; level < 12; ++level) {
-      for (int d = threadIdx.x; d < 256; d += blockDim.x) s_hist[d] = 0;
-      __syncthreads();
-      const unsigned long long pu = s_pu;
-      const unsigned pv = s_pv;
-      for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        const unsigned long long U = key[i];
-        const unsigned v = (unsigned)vv[i];
-        bool match;
-        int digit;
-        if (level < 8) {
-          match = level == 0 || (U >> (64 - 8 * level)) == (pu >> (64 - 8 * level));
-          digit = (int)((U >> (56 - 8 * level)) & 255u);
-        } else {
-          const int lv = level - 8;
-          match = U == pu && (lv == 0 || (v >> (32 - 8 * lv)) == (pv >> (32 - 8 * lv)));
-          digit = (int)((v >> (24 - 8 * lv)) & 255u);
-        }
-        if (match) atomicAdd(reinterpret_cast<unsigned long long *>(&s_hist[digit]), (unsigned long long)(ct[i] >> 8));
-      }
-      __syncthreads();
-      if (wid == 0) {
-        // lane l owns digits 8l .. 8l+7
-        long long loc[8];
-        long long sum = 0;
+  if (first && s_total < need) {
+    if (threadIdx.x == 0) r->all = 1;
+  } else if (before + excl < need && before + excl + sum >= need) {
+    long long run = before + excl;
+    int d = threadIdx.x * kPer;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) { loc[q] = s_hist[8 * lane + q]; sum += loc[q]; }
-        long long incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          long long y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
-        }
-        const long long before = s_before;
-        const long long need = bb.excess;
-        const long long excl = incl - sum;
-        // the digit where before + cumulative weight first reaches the excess
-        const bool here = before + excl < need && before + incl >= need;
-        const unsigned who = __ballot_sync(kFull, here);
-        if (here && lane == __ffs(who) - 1) {
-          long long run = before + excl;
-          int d = 8 * lane;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (run + loc[q] >= need) { d = 8 * lane + q; break; }
-            run += loc[q];
-          }
-          s_before = run;
-          if (level < 8) s_pu = pu | ((unsigned long long)d << (56 - 8 * level));
-          else s_pv = pv | ((unsigned)d << (24 - 8 * (level - 8)));
-        }
-      }
-      __syncthreads();
+    for (int q = 0; q < kPer; ++q) {
+      if (run + loc[q] >= need) { d = threadIdx.x * kPer + q; break; }
+      run += loc[q];
     }
+    r->before = run;
+    const u128 pre = (((u128)r->pre_hi << 64) | r->pre_lo) | ((u128)(unsigned)d << lo);
+    r->pre_hi = (unsigned long long)(pre >> 64);
+    r->pre_lo = (unsigned long long)pre;
   }
-  const unsigned long long pu = s_pu;
-  const unsigned pv = s_pv;
-  const bool all = s_all;
-  for (int base = 0; base < len; base += blockDim.x) {
-    const int i = base + threadIdx.x;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) row[threadIdx.x * kPer + q] = 0ull;
+}
+
+// Every record with K(v) <= its block's threshold (or of an `all` block) moves.
+template <class KT>
+__global__ void __launch_bounds__(256) k_rb_mark(RbArgs a) {
+  __shared__ unsigned s_wc[8];
+  __shared__ unsigned long long s_base;
+  const long long nrec = (long long)a.cnt->n_rec;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nrec; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
     bool sel = false;
-    int v = 0, t = 0;
-    if (i < len) {
-      const unsigned long long U = key[i];
-      v = vv[i];
-      t = ct[i] & 255;
-      sel = all || U < pu || (U == pu && (unsigned)v <= pv);
+    int v = 0, b = 0, t = 0;
+    if (i < nrec) {
+      const int32_t ct = a.rb_ct[i];
+      b = (ct >> 8) & 255;
+      t = ct & 255;
+      v = a.rb_v[i];
+      const RbBlock &r = a.rbb[b];
+      sel = r.all || rb_full_key<KT>(a.rb_hi[i], v, a.vbits) <= rb_prefix<KT>(r);
     }
-    const unsigned bal = __ballot_sync(kFull, sel);
-    unsigned long long pos0 = 0;
-    if (lane == 0 && bal) pos0 = atomicAdd(&a.cnt->n_moves, (unsigned long long)__popc(bal));
-    pos0 = __shfl_sync(kFull, pos0, 0);
+    const unsigned long long pos = block_append(sel, &a.cnt->n_moves, s_wc, &s_base);
     if (sel) {
-      const unsigned long long pos = pos0 + __popc(bal & ((1u << lane) - 1));
       a.mv_v[pos] = v;
       a.mv_st[pos] = (uint32_t)b | ((uint32_t)t << 16);
     }
@@ -296,7 +322,8 @@ __global__ void k_stats(const int64_t *bw, int32_t k, long long Lmax, const Coun
 // Moves that take part back to best (rollback at the end of a phase).
 __global__ void __launch_bounds__(256) k_rollback_moves(const int32_t *part, const int32_t *best, int32_t n,
                                                         int32_t *mv_v, uint32_t *mv_st, Counters *cnt) {
-  const int lane = threadIdx.x & 31;
+  __shared__ unsigned s_wc[8];
+  __shared__ unsigned long long s_base;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     int s = 0, t = 0;
@@ -306,12 +333,8 @@ __global__ void __launch_bounds__(256) k_rollback_moves(const int32_t *part, con
       t = best[v];
       mv = s != t && (unsigned)s < kMaxK && (unsigned)t < kMaxK;
     }
-    const unsigned bal = __ballot_sync(kFull, mv);
-    unsigned long long pos0 = 0;
-    if (lane == 0 && bal) pos0 = atomicAdd(&cnt->n_moves, (unsigned long long)__popc(bal));
-    pos0 = __shfl_sync(kFull, pos0, 0);
+    const unsigned long long pos = block_append(mv, &cnt->n_moves, s_wc, &s_base);
     if (mv) {
-      const unsigned long long pos = pos0 + __popc(bal & ((1u << lane) - 1));
       mv_v[pos] = (int32_t)v;
       mv_st[pos] = (uint32_t)s | ((uint32_t)t << 16);
     }
@@ -336,18 +359,21 @@ MoveArgs move_args(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   return a;
 }
 
-RbArgs rb_args(jet_ctx *c, const int64_t *block_w) {
+RbArgs rb_args(jet_ctx *c, const int64_t *block_w, const int32_t *part) {
   RbArgs a{};
   a.bw = block_w;
-  a.vcount = c->vcount;
   a.rbb = c->rbb;
-  a.rb_cursor = c->rb_cursor;
-  a.rb_key = c->rb_key;
+  a.rb_hi = c->rb_hi;
   a.rb_v = c->rb_v;
   a.rb_ct = c->rb_ct;
+  (void)part;
+  a.hist = c->rb_hist;
   a.mv_v = c->mv_v;
   a.mv_st = c->mv_st;
+  a.n = c->n;
   a.k = c->k;
+  a.vbits = c->rb_vbits;
+  a.tbits = c->rb_hbits + c->rb_vbits;
   a.Lmax = c->Lmax;
   a.dz_min = c->dz_min;
   a.max_rounds = c->params.max_rebalance_rounds;
@@ -369,25 +395,43 @@ cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block
 }
 
 cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w) {
-  k_rb_check<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w));
+  k_rb_check<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr));
   ++c->kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_rb_prep(jet_ctx *c, const int64_t *block_w) {
-  k_rb_prep<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w));
+  k_rb_prep<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr));
   ++c->kernel_launches;
   return cudaGetLastError();
 }
 
-cudaError_t launch_rb_select(jet_ctx *c) {
-  k_rb_select<<<c->k, kSelThreads, 0, c->stream>>>(rb_args(c, nullptr));
+template <class KT>
+void rb_select_levels(jet_ctx *c, const RbArgs &a) {
+  const int g = grid_for(c->n, 256, c->num_sms);
+  int first = 1;
+  for (int hi = a.tbits; hi > 0; first = 0) {
+    const int lo = hi - kRbDigitBits > 0 ? hi - kRbDigitBits : 0;
+    k_rb_level<KT><<<g, 256, 0, c->stream>>>(a, lo, hi - lo);
+    ++c->kernel_launches;
+    k_rb_pick<<<c->k, 256, 0, c->stream>>>(a, lo, first);
+    ++c->kernel_launches;
+    hi = lo;
+  }
+  k_rb_mark<KT><<<g, 256, 0, c->stream>>>(a);
   ++c->kernel_launches;
+}
+
+cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part) {
+  if (c->n == 0) return cudaSuccess;
+  const RbArgs a = rb_args(c, nullptr, part);
+  if (a.tbits <= 64) rb_select_levels<unsigned long long>(c, a);
+  else rb_select_levels<u128>(c, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w) {
-  k_rb_post<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w));
+  k_rb_post<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr));
   ++c->kernel_launches;
   return cudaGetLastError();
 }

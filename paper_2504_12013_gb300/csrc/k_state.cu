@@ -169,8 +169,11 @@ __global__ void __launch_bounds__(256) k_pincounts(const int64_t *eptr, const in
       int b = q * 32 + lane;
       int val = b < k ? h[b] : 0;
       if (b < k) row[b] = val;
-      unsigned bits = __ballot_sync(kFull, val > 0);
-      if (lane == 0) mask[e * kwp + q] = bits;
+      const unsigned one = __ballot_sync(kFull, val > 0), two = __ballot_sync(kFull, val > 1);
+      if (lane == 0) {
+        mask[e * 2 * kwp + q] = one;        // Lambda(e)
+        mask[e * 2 * kwp + kwp + q] = two;  // blocks holding >= 2 pins of e
+      }
     }
     __syncwarp();
   }
@@ -202,7 +205,7 @@ __global__ void k_block_weights(const int32_t *part, const int32_t *vwgt, int32_
   if (err) atomicOr(&cnt->err, err);
 }
 
-// Bitmasks of Lambda(e) from a dense phi (warp per edge).
+// Bitmasks of Lambda(e) and of the blocks with >= 2 pins from a dense phi (warp per edge).
 __global__ void __launch_bounds__(256) k_masks_from_phi(const int32_t *phi, int32_t m, int32_t k, int32_t kwp,
                                                         uint32_t *mask) {
   const int lane = threadIdx.x & 31;
@@ -212,8 +215,12 @@ __global__ void __launch_bounds__(256) k_masks_from_phi(const int32_t *phi, int3
     const int32_t *row = phi + e * k;
     for (int q = 0; q < kwp; ++q) {
       int b = q * 32 + lane;
-      unsigned bits = __ballot_sync(kFull, b < k && row[b] > 0);
-      if (lane == 0) mask[e * kwp + q] = bits;
+      const int val = b < k ? row[b] : 0;
+      const unsigned one = __ballot_sync(kFull, val > 0), two = __ballot_sync(kFull, val > 1);
+      if (lane == 0) {
+        mask[e * 2 * kwp + q] = one;
+        mask[e * 2 * kwp + kwp + q] = two;
+      }
     }
   }
 }
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(256) k_objective_masks(const uint32_t *mask, c
   long long acc = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
     int lam = 0;
-    for (int q = 0; q < kwp; ++q) lam += __popc(mask[e * kwp + q]);
+    for (int q = 0; q < kwp; ++q) lam += __popc(mask[e * 2 * kwp + q]);
     if (lam > 0) acc += (long long)(lam - 1) * ewgt[e];
   }
   long long tot = block_sum_ll(acc);

@@ -51,12 +51,15 @@ def make_instances():
     inst["vlsi_k64"] = (h, 64, synth.part_perm(8, h.n, 64))
     h = _with_empty_edges()
     inst["empty_edges_k4"] = (h, 4, synth.part_random(9, h.n, 4))
+    # vertex weights up to 1000: lcm(1..1000) is huge, so rebalancing uses the 96-bit priority keys
+    h = synth.uniform(10, 12_000, 14_000, base=2, geo=(1, 2), size_cap=32, c_max=1000, w_max=2)
+    inst["bigc_k16"] = (h, 16, synth.part_perm(10, h.n, 16))
     return inst
 
 
 INSTANCES = make_instances() if torch.cuda.is_available() else {}
 NAMES = ["random10k_k8", "weighted_k11", "weighted_k27", "geo04_k64", "geo04_k2", "heavy_k128", "heavy_k256",
-         "rownet_k32", "vlsi_k64", "empty_edges_k4"]
+         "rownet_k32", "vlsi_k64", "empty_edges_k4", "bigc_k16"]
 
 
 def setup(name):
@@ -161,7 +164,7 @@ def test_rebalance_from_random_partition(name):
 
 
 @pytest.mark.parametrize("name", ["random10k_k8", "weighted_k11", "geo04_k2", "heavy_k128", "rownet_k32",
-                                  "empty_edges_k4"])
+                                  "empty_edges_k4", "bigc_k16"])
 def test_refine_to_convergence(name):
     hg, k, part, ctx = setup(name)
     st = jet.JetState(ctx, part)
