@@ -222,6 +222,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     c->W = (int64_t)hscal[0];
     c->max_wdeg = (int64_t)hscal[1];
     c->cmax = (int32_t)hscal[2];
+    c->unit_ewgt = hscal[3] <= 1 ? 1 : 0;
     if (c->max_wdeg >= (1ll << 31) - 1) {
       rc = fail(c, JET_ERR_OVERFLOW, "a sum of omega over I(v) (%lld) does not fit the int32 gains",
                 (long long)c->max_wdeg);

@@ -94,6 +94,7 @@ struct jet_ctx {
   int64_t W = 0, A = 0, Lmax = 0, dz_min = 0;
   int64_t max_wdeg = 0;
   int32_t cmax = 0;
+  int unit_ewgt = 0;  // every edge with pins has omega(e) = 1
   // compact rebalancing keys: priority gain*c (gain >= 0) or gain*(L/c) (gain < 0), L = lcm(1..cmax),
   // stored as (Pmax - P) << 32 | v when max_wdeg*(cmax + L) < 2^32
   int rb_compact = 0;

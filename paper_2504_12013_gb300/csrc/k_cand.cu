@@ -93,6 +93,26 @@ __device__ __forceinline__ void add_weighted(uint32_t (&pl)[NP][KWP], const uint
   }
 }
 
+// planes += M (unit weight): ripple carry that stops as soon as no carry is left
+template <int KWP, int NP>
+__device__ __forceinline__ void add_one(uint32_t (&pl)[NP][KWP], const uint32_t (&M)[KWP]) {
+  uint32_t carry[KWP];
+#pragma unroll
+  for (int q = 0; q < KWP; ++q) carry[q] = M[q];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    uint32_t nz = 0;
+#pragma unroll
+    for (int q = 0; q < KWP; ++q) {
+      const uint32_t c2 = pl[p][q] & carry[q];
+      pl[p][q] ^= carry[q];
+      carry[q] = c2;
+      nz |= c2;
+    }
+    if (!nz) break;
+  }
+}
+
 // smallest block id maximising conn over the nonempty set C; returns the id and conn
 template <int KWP, int NP>
 __device__ __forceinline__ int argmax_planes(const uint32_t (&pl)[NP][KWP], uint32_t (&C)[KWP], int32_t &conn) {
@@ -123,8 +143,9 @@ __device__ __forceinline__ int argmax_planes(const uint32_t (&pl)[NP][KWP], uint
   return t;
 }
 
-// conn planes, union of Lambda(e) and A(v) over I(v) for a light vertex
-template <int KWP, int NP>
+// conn planes, union of Lambda(e) and A(v) over I(v) for a light vertex.
+// UNIT: every omega(e) is 1 (no weight gathers, increments instead of adds).
+template <int KWP, int NP, bool UNIT>
 __device__ __forceinline__ int32_t accumulate_light(const CandArgs &a, int v, int s, uint32_t (&pl)[NP][KWP],
                                                     uint32_t (&any)[KWP]) {
 #pragma unroll
@@ -135,20 +156,45 @@ __device__ __forceinline__ int32_t accumulate_light(const CandArgs &a, int v, in
   }
   int32_t A = 0;
   const int64_t j1 = a.vptr[v + 1];
-  for (int64_t j = a.vptr[v]; j < j1; ++j) {
+  int64_t j = a.vptr[v];
+  // four incidences at a time: their gathers are issued before any is used
+  for (; j + 4 <= j1; j += 4) {
+    int e[4], w[4];
+    uint32_t M[4][KWP], M2[4][KWP];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) e[u] = a.inc[j + u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      w[u] = UNIT ? 1 : a.ewgt[e[u]];
+      load_rows<KWP>(a.mask + (int64_t)e[u] * 2 * KWP, M[u], M2[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      uint32_t Mu[KWP], M2u[KWP];
+#pragma unroll
+      for (int q = 0; q < KWP; ++q) { Mu[q] = M[u][q]; M2u[q] = M2[u][q]; }
+      A += mask_bit<KWP>(M2u, s) ? w[u] : 0;  // phi_e[s] >= 2
+#pragma unroll
+      for (int q = 0; q < KWP; ++q) any[q] |= Mu[q];
+      if (UNIT) add_one<KWP, NP>(pl, Mu);
+      else add_weighted<KWP, NP>(pl, Mu, (uint32_t)w[u]);
+    }
+  }
+  for (; j < j1; ++j) {
     const int e = a.inc[j];
-    const int w = a.ewgt[e];
+    const int w = UNIT ? 1 : a.ewgt[e];
     uint32_t M[KWP], M2[KWP];
     load_rows<KWP>(a.mask + (int64_t)e * 2 * KWP, M, M2);
-    A += mask_bit<KWP>(M2, s) ? w : 0;  // phi_e[s] >= 2
+    A += mask_bit<KWP>(M2, s) ? w : 0;
 #pragma unroll
     for (int q = 0; q < KWP; ++q) any[q] |= M[q];
-    add_weighted<KWP, NP>(pl, M, (uint32_t)w);
+    if (UNIT) add_one<KWP, NP>(pl, M);
+    else add_weighted<KWP, NP>(pl, M, (uint32_t)w);
   }
   return A;
 }
 
-template <int KWP>
+template <int KWP, bool UNIT>
 __global__ void __launch_bounds__(256) k_cand_light(CandArgs a) {
   constexpr int NP = kLightPlanes;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nlist; i += gridDim.x * blockDim.x) {
@@ -159,7 +205,7 @@ __global__ void __launch_bounds__(256) k_cand_light(CandArgs a) {
       atomicOr(&a.cnt->err, kErrPartRange);
     } else if (!a.locked[v]) {
       uint32_t pl[NP][KWP], any[KWP];
-      const int32_t A = accumulate_light<KWP, NP>(a, v, s, pl, any);
+      const int32_t A = accumulate_light<KWP, NP, UNIT>(a, v, s, pl, any);
       uint32_t C[KWP];
       uint32_t nz = 0;
 #pragma unroll
@@ -302,7 +348,7 @@ __device__ __forceinline__ void eligible_words(const long long *s_cap, int k, in
   }
 }
 
-template <int KWP>
+template <int KWP, bool UNIT>
 __global__ void __launch_bounds__(256) k_rbcand_light(CandArgs a) {
   constexpr int NP = kLightPlanes;
   constexpr int kTab = 32;  // eligibility words tabulated for c(v) <= 32
@@ -351,7 +397,7 @@ __global__ void __launch_bounds__(256) k_rbcand_light(CandArgs a) {
           for (int q = 0; q < KWP; ++q) nz |= C[q];
           if (nz) {
             uint32_t pl[NP][KWP], any[KWP];
-            const int32_t A = accumulate_light<KWP, NP>(a, v, s, pl, any);
+            const int32_t A = accumulate_light<KWP, NP, UNIT>(a, v, s, pl, any);
             int32_t conn;
             const int t = argmax_planes<KWP, NP>(pl, C, conn);
             hi = rb_hi_of(a, conn - A, c);
@@ -422,7 +468,8 @@ cudaError_t launch_cand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_light > 0) {
     a.vlist = c->v_light;
     a.nlist = c->n_light;
-    k_cand_light<KWP><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    if (c->unit_ewgt) k_cand_light<KWP, true><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    else k_cand_light<KWP, false><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
     ++c->kernel_launches;
   }
   if (c->n_heavy > 0) {
@@ -440,7 +487,8 @@ cudaError_t launch_rbcand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_light > 0) {
     a.vlist = c->v_light;
     a.nlist = c->n_light;
-    k_rbcand_light<KWP><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    if (c->unit_ewgt) k_rbcand_light<KWP, true><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    else k_rbcand_light<KWP, false><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
     ++c->kernel_launches;
   }
   if (c->n_heavy > 0) {

@@ -29,27 +29,36 @@ struct MoveArgs {
   Counters *cnt;
 };
 
-// Thread per move: Pi(v) <- t, phi_e[s]--, phi_e[t]++ and the bit of t in
-// Lambda(e) for every e in I(v); c(V_s), c(V_t) and |V_s|, |V_t| through
-// shared-memory partial sums.
+// A group of kMoveLanes lanes per move, the lanes striding over I(v): more
+// loads and atomics in flight than one thread per move when the move list is
+// short (rebalancing rounds).
+constexpr int kMoveLanes = 8;
+
+// Pi(v) <- t and phi_e[s]--, phi_e[t]++ for every e in I(v); c(V_s), c(V_t)
+// and |V_s|, |V_t| through shared-memory partial sums.
 __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   __shared__ long long s_dw[kMaxK];
   __shared__ int s_dc[kMaxK];
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) { s_dw[b] = 0; s_dc[b] = 0; }
   __syncthreads();
   const long long nm = (long long)a.cnt->n_moves;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nm; i += (long long)gridDim.x * blockDim.x) {
+  const int sub = threadIdx.x % kMoveLanes;
+  const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
+  const long long ng = ((long long)gridDim.x * blockDim.x) / kMoveLanes;
+  for (long long i = g0; i < nm; i += ng) {
     const int v = a.mv_v[i];
     const uint32_t st = a.mv_st[i];
     const int s = st & 0xffff, t = st >> 16;
-    a.part[v] = t;
-    const int c = a.vwgt[v];
-    atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[s]), (unsigned long long)(-(long long)c));
-    atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[t]), (unsigned long long)c);
-    atomicSub(&s_dc[s], 1);
-    atomicAdd(&s_dc[t], 1);
+    if (sub == 0) {
+      a.part[v] = t;
+      const int c = a.vwgt[v];
+      atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[s]), (unsigned long long)(-(long long)c));
+      atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[t]), (unsigned long long)c);
+      atomicSub(&s_dc[s], 1);
+      atomicAdd(&s_dc[t], 1);
+    }
     const int64_t j1 = a.vptr[v + 1];
-    for (int64_t j = a.vptr[v]; j < j1; ++j) {
+    for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
       const int64_t e = a.inc[j];
       atomicSub(&a.phi[e * a.k + s], 1);
       atomicAdd(&a.phi[e * a.k + t], 1);
@@ -62,34 +71,51 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   }
 }
 
-// Set one bit of a mask word to `on` (skipping the atomic if it already is).
-// Every writer of a bit writes its final value, so a stale read that already
-// shows that value can never hide a needed change.
-__device__ __forceinline__ void put_bit(uint32_t *w, uint32_t bit, bool on) {
-  const uint32_t cur = __ldcg(w);
-  if (((cur & bit) != 0) == on) return;
-  if (on) atomicOr(w, bit);
-  else atomicAnd(w, ~bit);
-}
-
 // After all moves: bring the bits of s and t in both masks of every e in I(v)
-// to their final values (phi_e[.] >= 1 and >= 2), read from the final phi.
+// (phi_e[.] >= 1 and >= 2) to their final values, read from the final phi.
+// Each word of the row is read once and changed by at most one atomicOr and
+// one atomicAnd, only where it differs.  Every writer of a bit writes its
+// final value, so a stale read that already shows that value can never hide
+// a needed change.
 __global__ void __launch_bounds__(256) k_fix_masks(MoveArgs a) {
   const long long nm = (long long)a.cnt->n_moves;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nm; i += (long long)gridDim.x * blockDim.x) {
+  const int sub = threadIdx.x % kMoveLanes;
+  const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
+  const long long ng = ((long long)gridDim.x * blockDim.x) / kMoveLanes;
+  for (long long i = g0; i < nm; i += ng) {
     const int v = a.mv_v[i];
     const uint32_t st = a.mv_st[i];
     const int s = st & 0xffff, t = st >> 16;
+    const int ws = s >> 5, wt = t >> 5;
     const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
     const int64_t j1 = a.vptr[v + 1];
-    for (int64_t j = a.vptr[v]; j < j1; ++j) {
+    for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
       const int64_t e = a.inc[j];
       const int ps = __ldcg(&a.phi[e * a.k + s]), pt = __ldcg(&a.phi[e * a.k + t]);
       uint32_t *row = a.mask + e * 2 * a.kwp;
-      put_bit(&row[s >> 5], sbit, ps > 0);
-      put_bit(&row[a.kwp + (s >> 5)], sbit, ps > 1);
-      put_bit(&row[t >> 5], tbit, pt > 0);
-      put_bit(&row[a.kwp + (t >> 5)], tbit, pt > 1);
+      // words: Lambda at [0, kwp), ">= 2" at [kwp, 2 kwp)
+      const int w1s = ws, w2s = a.kwp + ws, w1t = wt, w2t = a.kwp + wt;
+      uint32_t set1s = ps > 0 ? sbit : 0, set2s = ps > 1 ? sbit : 0, set1t = tbit, set2t = pt > 1 ? tbit : 0;
+      const uint32_t cur1s = __ldcg(&row[w1s]), cur2s = __ldcg(&row[w2s]);
+      const uint32_t cur1t = w1t == w1s ? cur1s : __ldcg(&row[w1t]);
+      const uint32_t cur2t = w2t == w2s ? cur2s : __ldcg(&row[w2t]);
+      if (w1t == w1s) {  // s and t share the words: one update per word
+        const uint32_t want1 = (cur1s & ~(sbit | tbit)) | set1s | set1t;
+        const uint32_t want2 = (cur2s & ~(sbit | tbit)) | set2s | set2t;
+        if (want1 != cur1s) {
+          if (want1 & ~cur1s) atomicOr(&row[w1s], want1 & ~cur1s);
+          if (cur1s & ~want1) atomicAnd(&row[w1s], ~(cur1s & ~want1));
+        }
+        if (want2 != cur2s) {
+          if (want2 & ~cur2s) atomicOr(&row[w2s], want2 & ~cur2s);
+          if (cur2s & ~want2) atomicAnd(&row[w2s], ~(cur2s & ~want2));
+        }
+      } else {
+        if ((cur1s & sbit) != set1s) { if (set1s) atomicOr(&row[w1s], sbit); else atomicAnd(&row[w1s], ~sbit); }
+        if ((cur2s & sbit) != set2s) { if (set2s) atomicOr(&row[w2s], sbit); else atomicAnd(&row[w2s], ~sbit); }
+        if ((cur1t & tbit) != set1t) { if (set1t) atomicOr(&row[w1t], tbit); else atomicAnd(&row[w1t], ~tbit); }
+        if ((cur2t & tbit) != set2t) { if (set2t) atomicOr(&row[w2t], tbit); else atomicAnd(&row[w2t], ~tbit); }
+      }
     }
   }
 }
@@ -386,7 +412,7 @@ RbArgs rb_args(jet_ctx *c, const int64_t *block_w, const int32_t *part) {
 cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   if (c->n == 0) return cudaSuccess;
   MoveArgs a = move_args(c, part, phi, block_w);
-  const int g = grid_for(c->n, 256, c->num_sms, 4);
+  const int g = grid_for((int64_t)c->n * kMoveLanes, 256, c->num_sms, 8);
   k_apply<<<g, 256, 0, c->stream>>>(a);
   ++c->kernel_launches;
   k_fix_masks<<<g, 256, 0, c->stream>>>(a);

@@ -70,18 +70,23 @@ __global__ void k_validate_ids(const int32_t *pins, const int32_t *inc, int32_t 
 }
 
 // Phase 3: degree of the transpose, weighted degree sum of omega over I(v), c(V), max c(v).
-// scal[0] = c(V), scal[1] = max weighted degree, scal[2] = max c(v).
+// scal[0] = c(V), scal[1] = max weighted degree, scal[2] = max c(v),
+// scal[3] = max omega(e) over edges with at least one pin.
 __global__ void k_validate_degrees(const int64_t *vptr, const int32_t *inc, const int32_t *vwgt,
                                    const int32_t *ewgt, int32_t n, const int32_t *degcount, int64_t *wdeg,
                                    unsigned long long *scal, Counters *cnt) {
   int err = 0;
   long long wsum = 0;
-  unsigned long long wmax = 0, cm = 0;
+  unsigned long long wmax = 0, cm = 0, om = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     int64_t j0 = vptr[v], j1 = vptr[v + 1];
     if (j1 - j0 != degcount[v]) err |= kErrTranspose;
     long long d = 0;
-    for (int64_t j = j0; j < j1; ++j) d += ewgt[inc[j]];
+    for (int64_t j = j0; j < j1; ++j) {
+      const int32_t w = ewgt[inc[j]];
+      d += w;
+      om = (unsigned long long)w > om ? (unsigned long long)w : om;
+    }
     wdeg[v] = d;
     wmax = d > (long long)wmax ? (unsigned long long)d : wmax;
     int32_t c = vwgt[v];
@@ -92,39 +97,39 @@ __global__ void k_validate_degrees(const int64_t *vptr, const int32_t *inc, cons
   if (threadIdx.x == 0) atomicAdd(&scal[0], (unsigned long long)tot);
   atomicMax(&scal[1], wmax);
   atomicMax(&scal[2], cm);
+  atomicMax(&scal[3], om);
   if (err) atomicOr(&cnt->err, err);
 }
 
 // ---------------------------------------------------------------- classes
-// Stable three-way partition of ids [0, count) by class code (0, 1, 2).
+// Stable partition of ids [0, count) by class code (0 .. kClasses-1).
+constexpr int kClasses = 16;
+
 __global__ void k_class_count(const uint8_t *code, int32_t count, int32_t *blk_counts) {
-  __shared__ int s_c[3];
-  if (threadIdx.x < 3) s_c[threadIdx.x] = 0;
+  __shared__ int s_c[kClasses];
+  if (threadIdx.x < kClasses) s_c[threadIdx.x] = 0;
   __syncthreads();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int c = i < count ? code[i] : 3;
-  for (int cl = 0; cl < 3; ++cl) {
-    unsigned b = __ballot_sync(kFull, c == cl);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(&s_c[cl], __popc(b));
-  }
+  int c = i < count ? code[i] : kClasses;
+  const unsigned grp = __match_any_sync(kFull, c);
+  if (c < kClasses && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&s_c[c], __popc(grp));
   __syncthreads();
-  if (threadIdx.x < 3) blk_counts[blockIdx.x * 3 + threadIdx.x] = s_c[threadIdx.x];
+  if (threadIdx.x < kClasses) blk_counts[blockIdx.x * kClasses + threadIdx.x] = s_c[threadIdx.x];
 }
 
 __global__ void k_class_scatter(const uint8_t *code, int32_t count, const int32_t *blk_off, int32_t *out) {
-  __shared__ int s_w[32][3];
+  __shared__ int s_w[32][kClasses];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int c = i < count ? code[i] : 3;
-  unsigned rank = 0;
-  for (int cl = 0; cl < 3; ++cl) {
-    unsigned b = __ballot_sync(kFull, c == cl);
-    if (lane == 0) s_w[w][cl] = __popc(b);
-    if (c == cl) rank = __popc(b & ((1u << lane) - 1));
-  }
+  for (int x = threadIdx.x; x < 32 * kClasses; x += blockDim.x) s_w[x / kClasses][x % kClasses] = 0;
   __syncthreads();
-  if (c < 3) {
-    int base = blk_off[blockIdx.x * 3 + c];
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int c = i < count ? code[i] : kClasses;
+  const unsigned grp = __match_any_sync(kFull, c);
+  const unsigned rank = __popc(grp & ((1u << lane) - 1));
+  if (c < kClasses && lane == __ffs(grp) - 1) s_w[w][c] = __popc(grp);
+  __syncthreads();
+  if (c < kClasses) {
+    int base = blk_off[blockIdx.x * kClasses + c];
     for (int ww = 0; ww < w; ++ww) base += s_w[ww][c];
     out[base + rank] = (int32_t)i;
   }
@@ -135,10 +140,12 @@ __global__ void k_vertex_codes(const int64_t *wdeg, int32_t n, uint8_t *code) {
     code[v] = wdeg[v] < (1ll << kLightPlanes) ? 0 : 1;
 }
 
+// Edge classes: code = |e| for |e| <= kTinyEdge (so the tiny list comes out
+// ordered by size and a warp's edges tend to share one size), then mid, big.
 __global__ void k_edge_codes(const int64_t *eptr, int32_t m, uint8_t *code) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t sz = eptr[e + 1] - eptr[e];
-    code[e] = sz <= kTinyEdge ? 0 : (sz <= kWarpEdge ? 1 : 2);
+    code[e] = sz <= kTinyEdge ? (uint8_t)sz : (sz <= kWarpEdge ? kTinyEdge + 1 : kTinyEdge + 2);
   }
 }
 
@@ -290,38 +297,39 @@ cudaError_t launch_validate(jet_ctx *c, int64_t *wdeg_tmp, int32_t *degcount_tmp
 
 // Builds the class lists into one id array per kind (vertex: light, heavy;
 // edge: tiny, mid, big).  Synchronizes.
-static cudaError_t stable_partition(jet_ctx *c, const uint8_t *code, int32_t count, int32_t *out, int32_t totals[3]) {
-  totals[0] = totals[1] = totals[2] = 0;
+static cudaError_t stable_partition(jet_ctx *c, const uint8_t *code, int32_t count, int32_t *out,
+                                    int32_t totals[kClasses]) {
+  for (int cl = 0; cl < kClasses; ++cl) totals[cl] = 0;
   if (count == 0) return cudaSuccess;
   const int bs = 1024;
   const int nb = (int)((count + bs - 1) / bs);
   int32_t *d_cnt = nullptr, *d_off = nullptr;
-  cudaError_t e = cudaMallocAsync(&d_cnt, sizeof(int32_t) * 3 * nb, c->stream);
+  cudaError_t e = cudaMallocAsync(&d_cnt, sizeof(int32_t) * kClasses * nb, c->stream);
   if (e != cudaSuccess) return e;
-  e = cudaMallocAsync(&d_off, sizeof(int32_t) * 3 * nb, c->stream);
+  e = cudaMallocAsync(&d_off, sizeof(int32_t) * kClasses * nb, c->stream);
   if (e != cudaSuccess) { cudaFreeAsync(d_cnt, c->stream); return e; }
-  std::vector<int32_t> h(3 * (size_t)nb);
+  std::vector<int32_t> h((size_t)kClasses * nb);
   k_class_count<<<nb, bs, 0, c->stream>>>(code, count, d_cnt);
-  ++c->kernel_launches;
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_cnt, sizeof(int32_t) * 3 * nb, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), d_cnt, sizeof(int32_t) * kClasses * nb, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) {
-    int64_t tot[3] = {0, 0, 0};
+    int64_t tot[kClasses] = {0}, run[kClasses];
     for (int b = 0; b < nb; ++b)
-      for (int cl = 0; cl < 3; ++cl) tot[cl] += h[3 * b + cl];
-    int64_t run[3] = {0, tot[0], tot[0] + tot[1]};
+      for (int cl = 0; cl < kClasses; ++cl) tot[cl] += h[(size_t)kClasses * b + cl];
+    int64_t acc = 0;
+    for (int cl = 0; cl < kClasses; ++cl) { run[cl] = acc; acc += tot[cl]; }
     for (int b = 0; b < nb; ++b)
-      for (int cl = 0; cl < 3; ++cl) {
-        int32_t x = h[3 * b + cl];
-        h[3 * b + cl] = (int32_t)run[cl];
+      for (int cl = 0; cl < kClasses; ++cl) {
+        const int32_t x = h[(size_t)kClasses * b + cl];
+        h[(size_t)kClasses * b + cl] = (int32_t)run[cl];
         run[cl] += x;
       }
-    for (int cl = 0; cl < 3; ++cl) totals[cl] = (int32_t)tot[cl];
-    e = cudaMemcpyAsync(d_off, h.data(), sizeof(int32_t) * 3 * nb, cudaMemcpyHostToDevice, c->stream);
+    for (int cl = 0; cl < kClasses; ++cl) totals[cl] = (int32_t)tot[cl];
+    e = cudaMemcpyAsync(d_off, h.data(), sizeof(int32_t) * kClasses * nb, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) {
       k_class_scatter<<<nb, bs, 0, c->stream>>>(code, count, d_off, out);
-      ++c->kernel_launches;
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -338,10 +346,9 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
   uint8_t *code = nullptr;
   cudaError_t e = cudaMallocAsync(&code, mx > 0 ? mx : 1, c->stream);
   if (e != cudaSuccess) return e;
-  int32_t t[3];
+  int32_t t[kClasses];
   if (c->n > 0) {
     k_vertex_codes<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(wdeg, c->n, code);
-    ++c->kernel_launches;
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = stable_partition(c, code, c->n, c->v_light, t);
@@ -351,17 +358,17 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
     c->v_heavy = c->v_light + t[0];
     if (c->m > 0) {
       k_edge_codes<<<grid_for(c->m, 256, c->num_sms), 256, 0, c->stream>>>(c->eptr, c->m, code);
-      ++c->kernel_launches;
       e = cudaGetLastError();
     }
   }
   if (e == cudaSuccess) e = stable_partition(c, code, c->m, c->e_tiny, t);
   if (e == cudaSuccess) {
-    c->n_tiny = t[0];
-    c->n_mid = t[1];
-    c->n_big = t[2];
-    c->e_mid = c->e_tiny + t[0];
-    c->e_big = c->e_mid + t[1];
+    c->n_tiny = 0;
+    for (int cl = 0; cl <= kTinyEdge; ++cl) c->n_tiny += t[cl];
+    c->n_mid = t[kTinyEdge + 1];
+    c->n_big = t[kTinyEdge + 2];
+    c->e_mid = c->e_tiny + c->n_tiny;
+    c->e_big = c->e_mid + c->n_mid;
   }
   cudaFreeAsync(code, c->stream);
   return e;
