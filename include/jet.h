@@ -148,12 +148,23 @@ int jet_connectivity(jet_ctx *ctx, const int32_t *phi, int64_t *objective_out);
  * jet_rebalance.  part[n], phi[m*k], block_w[k], locked[n] (uint8) are
  * updated in place and must describe one consistent state (as left by
  * jet_build_pincounts or a previous call).  stats (device, may be NULL)
- * receives the iteration's statistics.  Synchronizes the stream once per
- * rebalancing round that runs.
+ * receives the iteration's statistics.  See jet_set_graph_mode for whether
+ * it synchronizes.
  * Errors: JET_ERR_INVALID_ARG for tau outside [0,1) or NULL state arrays.
  */
 int jet_refine_round(jet_ctx *ctx, int32_t tau_num, int32_t tau_den, int32_t *part, int32_t *phi,
                      int64_t *block_w, uint8_t *locked, jet_round_stats *stats);
+
+/*
+ * Execution form of jet_refine_round (default enable = 1): a CUDA graph per
+ * argument set (captured on first use and cached, up to 6 per context), whose
+ * rebalancing rounds run in a conditional WHILE node decided on the device,
+ * so the call returns without synchronizing and device-detected data errors
+ * surface at the next synchronizing call.  enable = 0 runs the same kernels
+ * one by one with a stream synchronization per rebalancing round; results
+ * are identical.
+ */
+int jet_set_graph_mode(jet_ctx *ctx, int enable);
 
 /*
  * Deterministic rebalancing (Section 4.3) until no block exceeds L_max, a

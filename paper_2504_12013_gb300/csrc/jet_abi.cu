@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "jet_internal.cuh"
 
@@ -99,7 +100,7 @@ struct ProfScope {
   long long l0;
   int slot = -1;
   ProfScope(jet_ctx *c_, int f) : c(c_), fam(f), l0(c_->kernel_launches) {
-    if (c->prof_on && c->prof_ev) {
+    if (c->prof_on && c->prof_ev && !c->capturing) {
       if (c->prof_n == jet_ctx::kProfPairs) prof_flush(c);
       slot = c->prof_n++;
       c->prof_fam[slot] = fam;
@@ -107,6 +108,7 @@ struct ProfScope {
     }
   }
   ~ProfScope() {
+    if (c->capturing) return;  // a graph's kernels are counted when the eager path runs them
     c->fam_launches[fam] += c->kernel_launches - l0;
     c->fam_calls[fam] += 1;
     if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
@@ -126,7 +128,7 @@ int check_ctx(jet_ctx *c) {
 
 // Rebalancing rounds (Section 4.3) until balanced, nothing moved or the cap.
 int rebalance_loop(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
-  CKP(F_RB_CTL, launch_rb_check(c, block_w), "rebalance check");
+  CKP(F_RB_CTL, launch_rb_check(c, block_w), "rebalance check");  // eager form; the graph form is below
   int rc = sync_counters(c);
   if (rc) return rc;
   if (!c->cnt_host->rb_any || c->params.max_rebalance_rounds <= 0) return JET_OK;
@@ -146,6 +148,154 @@ int rebalance_loop(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
 int check_tau(jet_ctx *c, int32_t tau_num, int32_t tau_den) {
   if (tau_den <= 0 || tau_num < 0 || tau_num >= tau_den)
     return fail(c, JET_ERR_INVALID_ARG, "temperature %d/%d is outside [0, 1)", tau_num, tau_den);
+  return JET_OK;
+}
+
+// ---- CUDA-graph form of jet_refine_round
+// The kernels of one iteration are captured once per argument set: the
+// candidate, afterburner, approval and apply kernels, then a WHILE node whose
+// body is one rebalancing round (its condition is set on the device by the
+// check kernel before the node and by the post kernel at the end of each
+// round), then the objective and statistics.  One launch, no host
+// synchronization.  Event-record nodes bracket the candidate kernels so the
+// profiler can time them inside the graph.
+cudaError_t capture_round(jet_ctx *c, int32_t tn, int32_t td, int32_t *part, int32_t *phi, int64_t *bw, uint8_t *locked,
+                          jet_round_stats *stats, cudaGraphConditionalHandle h, cudaEvent_t ev0, cudaEvent_t ev1,
+                          cudaGraphNode_t ev_nodes[2]) {
+  cudaStream_t s0 = c->cap_stream[0], s1 = c->cap_stream[1];
+  cudaError_t e;
+  cudaStreamCaptureStatus st;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  c->stream = s0;
+  if ((e = reset_counters(c)) != cudaSuccess) return e;
+  // external records become event-record nodes (a plain record in capture only orders streams);
+  // the nodes are looked up after the capture
+  (void)ev_nodes;
+  if ((e = cudaEventRecordWithFlags(ev0, s0, cudaEventRecordExternal)) != cudaSuccess) return e;
+  if ((e = launch_candidates(c, tn, td, part, phi, locked)) != cudaSuccess) return e;
+  if ((e = cudaEventRecordWithFlags(ev1, s0, cudaEventRecordExternal)) != cudaSuccess) return e;
+  if ((e = launch_afterburner(c, part, phi)) != cudaSuccess) return e;
+  if ((e = launch_approve(c, locked, nullptr, nullptr, true)) != cudaSuccess) return e;
+  if ((e = launch_apply(c, part, phi, bw)) != cudaSuccess) return e;
+  if ((e = launch_rb_check(c, bw, h, 1)) != cudaSuccess) return e;
+  // WHILE node: rebalancing rounds
+  if ((e = cudaStreamGetCaptureInfo(s0, &st, nullptr, &cg, &deps, &ed, &nd)) != cudaSuccess) return e;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  if ((e = cudaGraphAddNode(&cn, cg, deps, ed, nd, &cp)) != cudaSuccess) return e;
+  if ((e = cudaStreamUpdateCaptureDependencies(s0, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
+    return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    return e;
+  c->stream = s1;
+  cudaError_t eb = launch_rb_prep(c, bw);
+  if (eb == cudaSuccess) eb = launch_rebalance_candidates(c, part, phi);
+  if (eb == cudaSuccess) eb = launch_rb_select(c, part);
+  if (eb == cudaSuccess) eb = launch_apply(c, part, phi, bw);
+  if (eb == cudaSuccess) eb = launch_rb_post(c, bw, h, 1);
+  cudaGraph_t tmp = nullptr;
+  e = cudaStreamEndCapture(s1, &tmp);
+  c->stream = s0;
+  if (eb != cudaSuccess) return eb;
+  if (e != cudaSuccess) return e;
+  if ((e = launch_objective_masks(c)) != cudaSuccess) return e;
+  return launch_stats(c, bw, stats, 0);
+}
+
+int round_graph(jet_ctx *c, int32_t tn, int32_t td, int32_t *part, int32_t *phi, int64_t *bw, uint8_t *locked,
+                jet_round_stats *stats) {
+  jet_ctx::RoundGraph *G = nullptr;
+  for (auto &g : c->graphs)
+    if (g.exec && g.tau_num == tn && g.tau_den == td && g.part == part && g.phi == phi && g.bw == bw &&
+        g.locked == locked && g.stats == stats)
+      G = &g;
+  if (!G) {
+    if (!c->cap_stream[0]) {
+      CK(cudaStreamCreateWithFlags(&c->cap_stream[0], cudaStreamNonBlocking), "capture stream");
+      CK(cudaStreamCreateWithFlags(&c->cap_stream[1], cudaStreamNonBlocking), "capture stream");
+      CK(cudaEventCreate(&c->graph_ev[0]), "graph events");
+      CK(cudaEventCreate(&c->graph_ev[1]), "graph events");
+    }
+    G = &c->graphs[c->graph_next];
+    c->graph_next = (c->graph_next + 1) % jet_ctx::kGraphCache;
+    if (G->exec) {
+      cudaGraphExecDestroy(G->exec);
+      G->exec = nullptr;
+    }
+    if (G->graph) {
+      cudaGraphDestroy(G->graph);
+      G->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0), "graph");
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    cudaStream_t user = c->stream;
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(c->cap_stream[0], g, nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      c->capturing = 1;
+      cudaError_t ec = capture_round(c, tn, td, part, phi, bw, locked, stats, h, c->graph_ev[0], c->graph_ev[1],
+                                     G->ev_nodes);
+      c->capturing = 0;
+      cudaGraph_t done = nullptr;
+      e = cudaStreamEndCapture(c->cap_stream[0], &done);
+      if (ec != cudaSuccess) e = ec;
+    }
+    c->stream = user;
+    G->ev_nodes[0] = G->ev_nodes[1] = nullptr;
+    if (e == cudaSuccess) {  // the event-record nodes around the candidate kernels
+      size_t nn = 0;
+      e = cudaGraphGetNodes(g, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+      for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) continue;
+        if (ev == c->graph_ev[0]) G->ev_nodes[0] = nodes[i];
+        if (ev == c->graph_ev[1]) G->ev_nodes[1] = nodes[i];
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      G->exec = nullptr;
+      return cuda_fail(c, e, "round graph");
+    }
+    G->graph = g;
+    G->tau_num = tn;
+    G->tau_den = td;
+    G->part = part;
+    G->phi = phi;
+    G->bw = bw;
+    G->locked = locked;
+    G->stats = stats;
+  }
+  // the candidate kernels' event pair: a profiler slot while profiling, else the idle pair
+  cudaEvent_t e0 = c->graph_ev[0], e1 = c->graph_ev[1];
+  if (c->prof_on && c->prof_ev) {
+    if (c->prof_n == jet_ctx::kProfPairs) prof_flush(c);
+    const int slot = c->prof_n++;
+    c->prof_fam[slot] = F_CAND;
+    e0 = c->prof_ev[2 * slot];
+    e1 = c->prof_ev[2 * slot + 1];
+    c->fam_calls[F_CAND] += 1;
+  }
+  if (G->ev_nodes[0] && G->ev_nodes[1]) {
+    CK(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_nodes[0], e0), "graph event");
+    CK(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->ev_nodes[1], e1), "graph event");
+  }
+  CK(cudaGraphLaunch(G->exec, c->stream), "graph launch");
   return JET_OK;
 }
 
@@ -264,7 +414,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
         (e = dalloc(c, &c->rg, c->n)) != cudaSuccess || (e = dalloc(c, &c->mv_v, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->mv_st, c->n)) != cudaSuccess || (e = dalloc(c, &c->vcount, c->k)) != cudaSuccess ||
         (e = dalloc(c, &c->rbb, c->k)) != cudaSuccess || (e = dalloc(c, &c->rb_hi, c->n)) != cudaSuccess ||
-        (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess || (e = dalloc(c, &c->mtag, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_hist, (size_t)c->k * kRbBins)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_ct, c->n)) != cudaSuccess || (e = dalloc(c, &c->best_part, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->locked_ws, c->n)) != cudaSuccess || (e = dalloc(c, &c->stats_scratch, 1)) != cudaSuccess ||
@@ -275,6 +425,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     if ((e = cudaMemsetAsync(c->rg, 0, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->cand, 0, sizeof(uint64_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->mtag, 0xff, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->rb_hist, 0, sizeof(unsigned long long) * c->k * kRbBins, c->stream)) != cudaSuccess) {
       rc = cuda_fail(c, e, "workspace init");
       break;
@@ -298,9 +449,17 @@ void jet_ctx_destroy(jet_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
-                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->stats_scratch};
+                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->mtag, c->best_part, c->locked_ws, c->stats_scratch};
   for (void *p : dev) dfree(c, p);
   cudaStreamSynchronize(c->stream);
+  for (auto &g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (c->cap_stream[i]) cudaStreamDestroy(c->cap_stream[i]);
+    if (c->graph_ev[i]) cudaEventDestroy(c->graph_ev[i]);
+  }
   if (c->prof_ev) {
     for (int i = 0; i < 2 * jet_ctx::kProfPairs; ++i) cudaEventDestroy(c->prof_ev[i]);
     delete[] c->prof_ev;
@@ -374,6 +533,8 @@ int jet_refine_round(jet_ctx *c, int32_t tau_num, int32_t tau_den, int32_t *part
   if ((c->n > 0 && (!part || !locked)) || (c->m > 0 && !phi) || !block_w)
     return fail(c, JET_ERR_INVALID_ARG, "part, phi, block_w or locked is NULL");
   CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
+  if (!stats) stats = c->stats_scratch;
+  if (c->use_graphs) return round_graph(c, tau_num, tau_den, part, phi, block_w, locked, stats);
   CK(reset_counters(c), "counters");
   CKP(F_CAND, launch_candidates(c, tau_num, tau_den, part, phi, locked), "candidates");
   CKP(F_AB, launch_afterburner(c, part, phi), "afterburner");
@@ -381,7 +542,14 @@ int jet_refine_round(jet_ctx *c, int32_t tau_num, int32_t tau_den, int32_t *part
   CKP(F_APPLY, launch_apply(c, part, phi, block_w), "apply");
   if ((rc = rebalance_loop(c, part, phi, block_w))) return rc;
   CKP(F_OBJ, launch_objective_masks(c), "objective");
-  CKP(F_OBJ, launch_stats(c, block_w, stats ? stats : c->stats_scratch, 0), "stats");
+  CKP(F_OBJ, launch_stats(c, block_w, stats, 0), "stats");
+  return JET_OK;
+}
+
+int jet_set_graph_mode(jet_ctx *c, int enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->use_graphs = enable ? 1 : 0;
   return JET_OK;
 }
 

@@ -53,10 +53,11 @@ struct Counters {
   long long rb_rounds;
   long long rb_moves;
   unsigned long long n_rec;       // rebalancing records of the current round
+  unsigned long long mv_inc;      // incidences of the vertices in the move list
   int rb_done;                    // rebalancing loop may stop
   int rb_any;                     // an overloaded block exists
   int err;                        // bit flags of data errors found on the device
-  int pad[5];
+  int pad[3];
 };
 
 enum : int { kErrPartRange = 1, kErrPinRange = 2, kErrIncRange = 4, kErrOffsets = 8, kErrWeight = 16,
@@ -119,6 +120,7 @@ struct jet_ctx {
   uint64_t *rb_hi = nullptr;          // per record: priority part of the rebalancing key
   int32_t *rb_v = nullptr;            // per record: vertex
   int32_t *rb_ct = nullptr;           // per record: c(v) << 16 | block << 8 | target
+  int32_t *mtag = nullptr;            // per vertex: source | target << 8 while in the move list, else -1
   unsigned long long *rb_hist = nullptr;  // k x kRbBins weighted digit histograms (zero between uses)
   int rb_hbits = 0, rb_vbits = 1;     // key = rb_hi << rb_vbits | v, rb_hbits + rb_vbits significant bits
   int32_t *best_part = nullptr;       // best balanced partition of jet_refine
@@ -128,6 +130,22 @@ struct jet_ctx {
 
   const int32_t *phi_owner = nullptr;  // phi whose bitmasks `mask` holds
   char err[256] = {0};
+
+  // CUDA graphs of jet_refine_round (one per argument set, small cache)
+  struct RoundGraph {
+    int32_t tau_num = 0, tau_den = 0;
+    const void *part = nullptr, *phi = nullptr, *bw = nullptr, *locked = nullptr, *stats = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;                       // template, kept for the event-node updates
+    cudaGraphNode_t ev_nodes[2] = {nullptr, nullptr};  // event records around the candidate kernels
+  };
+  static constexpr int kGraphCache = 6;
+  RoundGraph graphs[kGraphCache];
+  int graph_next = 0;
+  int use_graphs = 1;
+  int capturing = 0;
+  cudaStream_t cap_stream[2] = {nullptr, nullptr};
+  cudaEvent_t graph_ev[2] = {nullptr, nullptr};  // idle targets of the graphs' event-record nodes
 
   // profiling: kernel launches (always counted) and event pairs per family
   long long kernel_launches = 0;
@@ -160,11 +178,13 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
 cudaError_t launch_approve(jet_ctx *c, uint8_t *locked, int32_t *rg_out, uint8_t *approved_out, bool build_moves);
 cudaError_t launch_export_candidates(jet_ctx *c, int32_t *target, int32_t *gain, uint8_t *in_m);
 // moves, rebalancing, loop control (k_moves.cu)
-cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w);
-cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w);
+cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w);  // applies the move list
+cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond = 0,
+                            int use_cond = 0);
 cudaError_t launch_rb_prep(jet_ctx *c, const int64_t *block_w);
 cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part);
-cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w);
+cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond = 0,
+                           int use_cond = 0);
 cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *stats, int rebalance_only);
 cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best);
 

@@ -157,19 +157,21 @@ __device__ __forceinline__ int32_t accumulate_light(const CandArgs &a, int v, in
   int32_t A = 0;
   const int64_t j1 = a.vptr[v + 1];
   int64_t j = a.vptr[v];
-  // four incidences at a time: their gathers are issued before any is used
-  for (; j + 4 <= j1; j += 4) {
-    int e[4], w[4];
-    uint32_t M[4][KWP], M2[4][KWP];
+  // B incidences at a time: their gathers are issued before any is used
+  // (fewer for wide masks, to keep registers and occupancy in balance)
+  constexpr int B = KWP >= 4 ? 2 : 4;
+  for (; j + B <= j1; j += B) {
+    int e[B], w[B];
+    uint32_t M[B][KWP], M2[B][KWP];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) e[u] = a.inc[j + u];
+    for (int u = 0; u < B; ++u) e[u] = a.inc[j + u];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < B; ++u) {
       w[u] = UNIT ? 1 : a.ewgt[e[u]];
       load_rows<KWP>(a.mask + (int64_t)e[u] * 2 * KWP, M[u], M2[u]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < B; ++u) {
       uint32_t Mu[KWP], M2u[KWP];
 #pragma unroll
       for (int q = 0; q < KWP; ++q) { Mu[q] = M[u][q]; M2u[q] = M2[u][q]; }

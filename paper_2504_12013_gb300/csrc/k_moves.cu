@@ -17,8 +17,12 @@ __device__ __forceinline__ void add_i64(long long *p, long long v) {
 }
 
 struct MoveArgs {
-  const int64_t *vptr;
-  const int32_t *inc, *vwgt;
+  const int64_t *vptr, *eptr;
+  const int32_t *inc, *vwgt, *pins;
+  int32_t *mtag;
+  const int32_t *elist;
+  int32_t nlist;
+  long long P;
   int32_t *part, *phi;
   int64_t *bw;
   int32_t *vcount;
@@ -34,6 +38,169 @@ struct MoveArgs {
 // short (rebalancing rounds).
 constexpr int kMoveLanes = 8;
 
+// Large move lists are applied edge by edge: every edge's owner (a thread, a
+// warp or a block) adds the net +-1 of its moved pins to its own phi row and
+// rewrites its own mask words, with no atomics and no fix-up pass.  Small
+// lists are applied move by move with atomics plus the mask fix-up.  The
+// choice is made on the device from the moved incidences: edge by edge when
+// more than half of all incidences move (the phi row traffic is the same
+// either way; the edge pass saves the atomics and the fix-up pass but has to
+// read every pin).
+__device__ __forceinline__ bool edge_centric(const MoveArgs &a) { return (long long)a.cnt->mv_inc * 2 > a.P; }
+
+// Tags every moved vertex (source | target << 8) and sums the moved incidences.
+__global__ void __launch_bounds__(256) k_apply_prep(MoveArgs a) {
+  const long long nm = (long long)a.cnt->n_moves;
+  unsigned long long inc = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nm; i += (long long)gridDim.x * blockDim.x) {
+    const int v = a.mv_v[i];
+    const uint32_t st = a.mv_st[i];
+    a.mtag[v] = (int32_t)((st & 0xffff) | ((st >> 16) << 8));
+    inc += (unsigned long long)(a.vptr[v + 1] - a.vptr[v]);
+  }
+  for (int o = 16; o > 0; o >>= 1) inc += __shfl_xor_sync(kFull, inc, o);
+  if ((threadIdx.x & 31) == 0 && inc) atomicAdd(&a.cnt->mv_inc, inc);
+}
+
+// Owner of row e: one bit of both mask words of block b from its count `val`.
+__device__ __forceinline__ void owner_set_bits(uint32_t *mrow, int kwp, int b, int val) {
+  const uint32_t bit = 1u << (b & 31);
+  uint32_t *w1 = &mrow[b >> 5], *w2 = &mrow[kwp + (b >> 5)];
+  *w1 = (*w1 & ~bit) | (val > 0 ? bit : 0u);
+  *w2 = (*w2 & ~bit) | (val > 1 ? bit : 0u);
+}
+
+// Edges of at most kTinyEdge pins, one thread each.
+__global__ void __launch_bounds__(256) k_apply_edges_tiny(MoveArgs a) {
+  if (!edge_centric(a)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nlist; i += gridDim.x * blockDim.x) {
+    const int64_t e = a.elist[i];
+    const int64_t p0 = a.eptr[e];
+    const int sz = (int)(a.eptr[e + 1] - p0);
+    int tg[kTinyEdge];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q) {
+      tg[q] = q < sz ? a.mtag[a.pins[p0 + q]] : -1;
+      any |= tg[q] >= 0;
+    }
+    if (!any) continue;
+    int32_t *row = a.phi + e * a.k;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q)
+      if (tg[q] >= 0) {
+        row[tg[q] & 255] -= 1;
+        row[tg[q] >> 8] += 1;
+      }
+    uint32_t *mrow = a.mask + e * 2 * a.kwp;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q)
+      if (tg[q] >= 0) {
+        const int s = tg[q] & 255, t = tg[q] >> 8;
+        owner_set_bits(mrow, a.kwp, s, row[s]);
+        owner_set_bits(mrow, a.kwp, t, row[t]);
+      }
+  }
+}
+
+// Edges of 9..2048 pins, one warp each: net deltas per block in shared memory,
+// then only the changed entries of the row and their mask bits are written.
+constexpr int kApplyWarps = 8;
+
+__global__ void __launch_bounds__(kApplyWarps * 32) k_apply_edges_warp(MoveArgs a) {
+  if (!edge_centric(a)) return;
+  __shared__ int s_delta[kApplyWarps][kMaxK];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int *delta = s_delta[w];
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = gw; i < a.nlist; i += nw) {
+    const int64_t e = a.elist[i];
+    const int64_t p1 = a.eptr[e + 1];
+    for (int b = lane; b < a.k; b += 32) delta[b] = 0;
+    __syncwarp();
+    bool any = false;
+    for (int64_t p = a.eptr[e] + lane; p < p1; p += 32) {
+      const int tg = a.mtag[a.pins[p]];
+      if (tg >= 0) {
+        any = true;
+        atomicSub(&delta[tg & 255], 1);
+        atomicAdd(&delta[tg >> 8], 1);
+      }
+    }
+    any = __any_sync(kFull, any);
+    __syncwarp();
+    if (any) {
+      int32_t *row = a.phi + e * a.k;
+      uint32_t *mrow = a.mask + e * 2 * a.kwp;
+      for (int q = 0; q < a.kwp; ++q) {
+        const int b = q * 32 + lane;
+        const int d = b < a.k ? delta[b] : 0;
+        int val = 0;
+        if (d) {  // only the changed entries of the row are read and written
+          val = row[b] + d;
+          row[b] = val;
+        }
+        const unsigned chg = __ballot_sync(kFull, d != 0);
+        if (!chg) continue;
+        const unsigned one = __ballot_sync(kFull, val > 0), two = __ballot_sync(kFull, val > 1);
+        if (lane == 0) {
+          mrow[q] = (mrow[q] & ~chg) | (one & chg);
+          mrow[a.kwp + q] = (mrow[a.kwp + q] & ~chg) | (two & chg);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Edges of more than 2048 pins, one block each.
+__global__ void __launch_bounds__(512) k_apply_edges_block(MoveArgs a) {
+  if (!edge_centric(a)) return;
+  __shared__ int s_delta[kMaxK];
+  __shared__ int s_any;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = blockIdx.x; i < a.nlist; i += gridDim.x) {
+    const int64_t e = a.elist[i];
+    const int64_t p1 = a.eptr[e + 1];
+    for (int b = threadIdx.x; b < a.k; b += blockDim.x) s_delta[b] = 0;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    bool any = false;
+    for (int64_t p = a.eptr[e] + threadIdx.x; p < p1; p += blockDim.x) {
+      const int tg = a.mtag[a.pins[p]];
+      if (tg >= 0) {
+        any = true;
+        atomicSub(&s_delta[tg & 255], 1);
+        atomicAdd(&s_delta[tg >> 8], 1);
+      }
+    }
+    if (__any_sync(kFull, any) && lane == 0) s_any = 1;
+    __syncthreads();
+    if (s_any) {
+      int32_t *row = a.phi + e * a.k;
+      uint32_t *mrow = a.mask + e * 2 * a.kwp;
+      for (int q = w; q < a.kwp; q += blockDim.x / 32) {  // warp q owns mask word q
+        const int b = q * 32 + lane;
+        const int d = b < a.k ? s_delta[b] : 0;
+        int val = 0;
+        if (d) {
+          val = row[b] + d;
+          row[b] = val;
+        }
+        const unsigned chg = __ballot_sync(kFull, d != 0);
+        if (!chg) continue;
+        const unsigned one = __ballot_sync(kFull, val > 0), two = __ballot_sync(kFull, val > 1);
+        if (lane == 0) {
+          mrow[q] = (mrow[q] & ~chg) | (one & chg);
+          mrow[a.kwp + q] = (mrow[a.kwp + q] & ~chg) | (two & chg);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Pi(v) <- t and phi_e[s]--, phi_e[t]++ for every e in I(v); c(V_s), c(V_t)
 // and |V_s|, |V_t| through shared-memory partial sums.
 __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
@@ -42,6 +209,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) { s_dw[b] = 0; s_dc[b] = 0; }
   __syncthreads();
   const long long nm = (long long)a.cnt->n_moves;
+  const bool edge_mode = edge_centric(a);
   const int sub = threadIdx.x % kMoveLanes;
   const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
   const long long ng = ((long long)gridDim.x * blockDim.x) / kMoveLanes;
@@ -51,12 +219,14 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
     const int s = st & 0xffff, t = st >> 16;
     if (sub == 0) {
       a.part[v] = t;
+      a.mtag[v] = -1;
       const int c = a.vwgt[v];
       atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[s]), (unsigned long long)(-(long long)c));
       atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[t]), (unsigned long long)c);
       atomicSub(&s_dc[s], 1);
       atomicAdd(&s_dc[t], 1);
     }
+    if (edge_mode) continue;  // the edge owners updated phi and the masks
     const int64_t j1 = a.vptr[v + 1];
     for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
       const int64_t e = a.inc[j];
@@ -78,6 +248,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 // final value, so a stale read that already shows that value can never hide
 // a needed change.
 __global__ void __launch_bounds__(256) k_fix_masks(MoveArgs a) {
+  if (edge_centric(a)) return;
   const long long nm = (long long)a.cnt->n_moves;
   const int sub = threadIdx.x % kMoveLanes;
   const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
@@ -148,14 +319,16 @@ struct RbArgs {
   Counters *cnt;
 };
 
-// Any block above L_max?  One block of 256 threads (k <= 256).
-__global__ void k_rb_check(RbArgs a) {
+// Any block above L_max?  One block of 256 threads (k <= 256).  In a CUDA
+// graph (use_cond) it also sets the condition of the rebalancing WHILE node.
+__global__ void k_rb_check(RbArgs a, cudaGraphConditionalHandle cond, int use_cond) {
   const int b = threadIdx.x;
   const bool over = b < a.k && a.bw[b] > a.Lmax;
   const int any = __syncthreads_or(over);
   if (b == 0) {
     a.cnt->rb_any = any;
     a.cnt->rb_done = !any;
+    if (use_cond) cudaGraphSetConditional(cond, (any && a.max_rounds > 0) ? 1u : 0u);
   }
 }
 
@@ -179,6 +352,7 @@ __global__ void k_rb_prep(RbArgs a) {
   if (b == 0) {
     a.cnt->n_moves = 0;
     a.cnt->n_rec = 0;
+    a.cnt->mv_inc = 0;
   }
 }
 
@@ -308,7 +482,7 @@ __global__ void __launch_bounds__(256) k_rb_mark(RbArgs a) {
 
 // End of a round: count it, and stop if nothing moved, nothing is overloaded
 // any more, or the round cap is reached.
-__global__ void k_rb_post(RbArgs a) {
+__global__ void k_rb_post(RbArgs a, cudaGraphConditionalHandle cond, int use_cond) {
   const int b = threadIdx.x;
   const bool over = b < a.k && a.bw[b] > a.Lmax;
   const int any = __syncthreads_or(over);
@@ -317,7 +491,9 @@ __global__ void k_rb_post(RbArgs a) {
     a.cnt->rb_rounds += 1;
     a.cnt->rb_moves += moved;
     a.cnt->rb_any = any;
-    a.cnt->rb_done = (moved == 0) || !any || (a.cnt->rb_rounds >= a.max_rounds);
+    const int done = (moved == 0) || !any || (a.cnt->rb_rounds >= a.max_rounds);
+    a.cnt->rb_done = done;
+    if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
   }
 }
 
@@ -370,8 +546,12 @@ __global__ void __launch_bounds__(256) k_rollback_moves(const int32_t *part, con
 MoveArgs move_args(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   MoveArgs a{};
   a.vptr = c->vptr;
+  a.eptr = c->eptr;
   a.inc = c->inc;
   a.vwgt = c->vwgt;
+  a.pins = c->pins;
+  a.mtag = c->mtag;
+  a.P = c->P;
   a.part = part;
   a.phi = phi;
   a.bw = block_w;
@@ -413,6 +593,27 @@ cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block
   if (c->n == 0) return cudaSuccess;
   MoveArgs a = move_args(c, part, phi, block_w);
   const int g = grid_for((int64_t)c->n * kMoveLanes, 256, c->num_sms, 8);
+  k_apply_prep<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(a);
+  ++c->kernel_launches;
+  if (c->n_tiny > 0) {
+    a.elist = c->e_tiny;
+    a.nlist = c->n_tiny;
+    k_apply_edges_tiny<<<grid_for(c->n_tiny, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    ++c->kernel_launches;
+  }
+  if (c->n_mid > 0) {
+    a.elist = c->e_mid;
+    a.nlist = c->n_mid;
+    k_apply_edges_warp<<<grid_for((int64_t)c->n_mid * 32, kApplyWarps * 32, c->num_sms), kApplyWarps * 32, 0,
+                         c->stream>>>(a);
+    ++c->kernel_launches;
+  }
+  if (c->n_big > 0) {
+    a.elist = c->e_big;
+    a.nlist = c->n_big;
+    k_apply_edges_block<<<c->num_sms * 2, 512, 0, c->stream>>>(a);
+    ++c->kernel_launches;
+  }
   k_apply<<<g, 256, 0, c->stream>>>(a);
   ++c->kernel_launches;
   k_fix_masks<<<g, 256, 0, c->stream>>>(a);
@@ -420,8 +621,8 @@ cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block
   return cudaGetLastError();
 }
 
-cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w) {
-  k_rb_check<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr));
+cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond, int use_cond) {
+  k_rb_check<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr), cond, use_cond);
   ++c->kernel_launches;
   return cudaGetLastError();
 }
@@ -456,8 +657,8 @@ cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w) {
-  k_rb_post<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr));
+cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond, int use_cond) {
+  k_rb_post<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr), cond, use_cond);
   ++c->kernel_launches;
   return cudaGetLastError();
 }
@@ -470,6 +671,7 @@ cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *st
 
 cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best) {
   cudaError_t e = cudaMemsetAsync(&c->cnt->n_moves, 0, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->cnt->mv_inc, 0, sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess || c->n == 0) return e;
   k_rollback_moves<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(part, best, c->n, c->mv_v, c->mv_st,
                                                                          c->cnt);

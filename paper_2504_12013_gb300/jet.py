@@ -23,7 +23,8 @@ ERRORS = {-1: "JET_ERR_INVALID_ARG", -2: "JET_ERR_OOM", -3: "JET_ERR_CUDA", -4: 
 # every symbol include/jet.h declares
 EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pincounts", "jet_connectivity",
            "jet_refine_round", "jet_rebalance", "jet_refine", "jet_candidates", "jet_afterburner",
-           "jet_refine_host", "jet_profile_enable", "jet_profile_read", "jet_block_weights_noalloc")
+           "jet_refine_host", "jet_profile_enable", "jet_profile_read", "jet_block_weights_noalloc",
+           "jet_set_graph_mode")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -97,6 +98,7 @@ def load_library():
             lib.jet_profile_enable.argtypes = [_P, ctypes.c_int]
             lib.jet_profile_read.argtypes = [_P, pp(ctypes.c_double), pp(i64), pp(i64), ctypes.c_int]
             lib.jet_block_weights_noalloc.argtypes = [_P, _P, i32, i32, _P, _P, _P]
+            lib.jet_set_graph_mode.argtypes = [_P, ctypes.c_int]
             for f in EXPORTS:
                 if f not in ("jet_ctx_destroy", "jet_last_error"):
                     getattr(lib, f).restype = ctypes.c_int
@@ -261,6 +263,10 @@ def jet_refine_host(hg, p: JetParams, schedule, limit, part: np.ndarray) -> dict
                                         part.ctypes.data, ctypes.byref(res))
     _check(rc)
     return res.as_dict()
+
+
+def jet_set_graph_mode(ctx: Ctx, enable: bool = True):
+    _check(load_library().jet_set_graph_mode(ctx.handle, 1 if enable else 0), ctx)
 
 
 def jet_profile_enable(ctx: Ctx, enable: bool = True):

@@ -11,9 +11,10 @@
  * (unbiased).  Discrete distributions are sampled by binary search over an
  * integer cumulative table, so the same seed gives the same instance on any
  * little- or big-endian, signed- or unsigned-char platform.  The log-normal
- * length table is built with libm (erfc/log) and quantised to 62-bit
- * integers; a last-ulp libm difference between machines could move a table
- * entry by one unit, which no stored expected value depends on.
+ * length table uses no libm function: its log, exp and normal CDF are
+ * series in IEEE-754 double +, -, *, / (correctly rounded everywhere, built
+ * without FMA contraction), so x86 and Arm hosts produce identical tables
+ * and therefore identical instances.
  *
  * Every generated hyperedge holds distinct pins, sorted by vertex id.  The
  * vertex-major CSR (incidence lists I(v)) is the exact transpose, listing the
@@ -75,6 +76,49 @@ static uint64_t isqrt_u128(__uint128_t x) {
     if ((__uint128_t)mid * mid <= x) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+/* ------------------------------------------- host-independent log/exp/CDF */
+static const double kLn2 = 0.69314718055994530942;
+
+/* natural log for x > 0: x = m * 2^e with m in [sqrt(1/2), sqrt(2)), then
+   log m = 2 atanh((m-1)/(m+1)) by its series */
+static double det_log(double x) {
+  int e = 0;
+  double m = frexp(x, &e); /* exact: x = m * 2^e, m in [0.5, 1) */
+  if (m < 0.70710678118654752440) { m *= 2.0; e -= 1; }
+  const double u = (m - 1.0) / (m + 1.0), u2 = u * u;
+  double term = u, sum = 0.0;
+  for (int k = 1; k < 80; k += 2) {
+    sum += term / k;
+    term *= u2;
+  }
+  return 2.0 * sum + e * kLn2;
+}
+
+/* e^x: x = n ln2 + r with |r| <= ln2/2, Taylor series of e^r, exact scaling by 2^n */
+static double det_exp(double x) {
+  const double n = floor(x / kLn2 + 0.5);
+  const double r = x - n * kLn2;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 30; ++k) {
+    term *= r / k;
+    sum += term;
+  }
+  return ldexp(sum, (int)n);
+}
+
+/* standard normal CDF: 1/2 + phi(z) (z + z^3/3 + z^5/(3*5) + ...), phi the density */
+static double det_normal_cdf(double z) {
+  const double phi = det_exp(-0.5 * z * z) * 0.39894228040143267794;
+  double term = z, sum = z;
+  for (int k = 1; k < 400; ++k) {
+    term *= z * z / (2 * k + 1);
+    sum += term;
+    if (term < 1e-30 * sum && k > 2 * (int)(z * z)) break;
+  }
+  double F = 0.5 + phi * sum;
+  return F < 0.0 ? 0.0 : (F > 1.0 ? 1.0 : F);
 }
 
 /* ---------------------------------------------------------------- output */
@@ -268,8 +312,8 @@ int synth_rownet(uint64_t seed, int32_t n, int32_t m, int32_t n_hubs, int32_t hu
   uint64_t acc = 0;
   double prev = 0.0;
   for (int64_t l = 1; l <= tlen; ++l) {
-    double z = (log((double)l + 0.5) - mu) / sigma;
-    double F = 0.5 * erfc(-z / sqrt(2.0));
+    double z = (det_log((double)l + 0.5) - mu) / sigma;
+    double F = det_normal_cdf(z);
     if (l == tlen) F = 1.0;
     double p = F - prev;
     prev = F;

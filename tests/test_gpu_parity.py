@@ -131,8 +131,10 @@ def _compare_state(hg, k, st, ost, where):
 
 
 @pytest.mark.parametrize("name", NAMES)
-def test_refine_rounds_state(name):
+@pytest.mark.parametrize("mode", ["graph", "eager"])
+def test_refine_rounds_state(name, mode):
     hg, k, part, ctx = setup(name)
+    jet.jet_set_graph_mode(ctx, mode == "graph")
     st = jet.JetState(ctx, part)
     orc = oracle.Oracle(hg)
     ost = oracle.State(orc, k, part)
