@@ -414,7 +414,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
         (e = dalloc(c, &c->rg, c->n)) != cudaSuccess || (e = dalloc(c, &c->mv_v, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->mv_st, c->n)) != cudaSuccess || (e = dalloc(c, &c->vcount, c->k)) != cudaSuccess ||
         (e = dalloc(c, &c->rbb, c->k)) != cudaSuccess || (e = dalloc(c, &c->rb_hi, c->n)) != cudaSuccess ||
-        (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess || (e = dalloc(c, &c->mtag, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_hist, (size_t)c->k * kRbBins)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_ct, c->n)) != cudaSuccess || (e = dalloc(c, &c->best_part, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->locked_ws, c->n)) != cudaSuccess || (e = dalloc(c, &c->stats_scratch, 1)) != cudaSuccess ||
@@ -425,7 +425,6 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     if ((e = cudaMemsetAsync(c->rg, 0, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->cand, 0, sizeof(uint64_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->mtag, 0xff, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->rb_hist, 0, sizeof(unsigned long long) * c->k * kRbBins, c->stream)) != cudaSuccess) {
       rc = cuda_fail(c, e, "workspace init");
       break;
@@ -449,7 +448,7 @@ void jet_ctx_destroy(jet_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
-                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->mtag, c->best_part, c->locked_ws, c->stats_scratch};
+                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->stats_scratch};
   for (void *p : dev) dfree(c, p);
   cudaStreamSynchronize(c->stream);
   for (auto &g : c->graphs) {

@@ -53,11 +53,10 @@ struct Counters {
   long long rb_rounds;
   long long rb_moves;
   unsigned long long n_rec;       // rebalancing records of the current round
-  unsigned long long mv_inc;      // incidences of the vertices in the move list
   int rb_done;                    // rebalancing loop may stop
   int rb_any;                     // an overloaded block exists
   int err;                        // bit flags of data errors found on the device
-  int pad[3];
+  int pad[5];
 };
 
 enum : int { kErrPartRange = 1, kErrPinRange = 2, kErrIncRange = 4, kErrOffsets = 8, kErrWeight = 16,
@@ -120,7 +119,6 @@ struct jet_ctx {
   uint64_t *rb_hi = nullptr;          // per record: priority part of the rebalancing key
   int32_t *rb_v = nullptr;            // per record: vertex
   int32_t *rb_ct = nullptr;           // per record: c(v) << 16 | block << 8 | target
-  int32_t *mtag = nullptr;            // per vertex: source | target << 8 while in the move list, else -1
   unsigned long long *rb_hist = nullptr;  // k x kRbBins weighted digit histograms (zero between uses)
   int rb_hbits = 0, rb_vbits = 1;     // key = rb_hi << rb_vbits | v, rb_hbits + rb_vbits significant bits
   int32_t *best_part = nullptr;       // best balanced partition of jet_refine

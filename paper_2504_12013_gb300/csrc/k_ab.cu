@@ -110,7 +110,11 @@ constexpr int kAbWarps = 8;
 // shared memory, one table per warp: max key of the departures and min key
 // of the arrivals of every block, and the blocks holding a non-candidate pin.
 // A key is never 0 (its high word is INT32_MAX - gain >= 1), so max = 0 means
-// "no departure" and min = ~0 "no arrival".
+// "no departure" and min = ~0 "no arrival".  Only the entries (and mask
+// words) of blocks some candidate of the edge leaves or enters are reset and
+// read, so the cost is O(|e|) and not O(k) per edge: pass 1 resets them,
+// pass 2 adds the departures, arrivals and non-candidate blocks, pass 3 lets
+// the last departure and the first arrival of each block decide.
 __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
   extern __shared__ unsigned long long s_tab[];  // per warp: maxd[k], mina[k]
   __shared__ uint32_t s_nm[kAbWarps][kMaxK / 32];
@@ -123,18 +127,60 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
   for (int i = gw; i < a.nlist; i += nw) {
     const int e = a.elist[i];
     const int64_t p0 = a.eptr[e], p1 = a.eptr[e + 1];
-    for (int b = lane; b < a.k; b += 32) {
-      maxd[b] = 0ull;
-      mina[b] = ~0ull;
+    if (p1 - p0 <= 32) {  // one pin per lane: the pin's data stays in registers for the three passes
+      const bool has = lane < p1 - p0;
+      const int v = has ? a.pins[p0 + lane] : 0;
+      const uint64_t r = has ? a.cand[v] : 0ull;
+      const int b = (has && !r) ? (a.part[v] & 255) : -1;
+      const int s = cand_s(r), t = cand_t(r);
+      if (r) {
+        maxd[s] = 0ull;
+        mina[s] = ~0ull;
+        maxd[t] = 0ull;
+        mina[t] = ~0ull;
+        nm[s >> 5] = 0u;
+        nm[t >> 5] = 0u;
+      }
+      if (!__any_sync(kFull, r != 0)) continue;
+      __syncwarp();
+      const uint64_t K = cand_key(r, v);
+      if (r) {
+        atomicMax(&maxd[s], (unsigned long long)K);
+        atomicMin(&mina[t], (unsigned long long)K);
+      } else if (b >= 0) {
+        atomicOr(&nm[b >> 5], 1u << (b & 31));
+      }
+      __syncwarp();
+      if (r) {
+        const int wt = a.ewgt[e];
+        int delta = 0;
+        if (maxd[s] == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina[s] == ~0ull || K < mina[s])) delta += wt;
+        if (mina[t] == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd[t] < K) delta -= wt;
+        if (delta) atomicAdd(&a.rg[v], delta);
+      }
+      __syncwarp();
+      continue;
     }
-    if (lane < kMaxK / 32) nm[lane] = 0;
-    __syncwarp();
     bool any = false;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const uint64_t r = a.cand[a.pins[p]];
+      if (r) {
+        any = true;
+        const int s = cand_s(r), t = cand_t(r);
+        maxd[s] = 0ull;
+        mina[s] = ~0ull;
+        maxd[t] = 0ull;
+        mina[t] = ~0ull;
+        nm[s >> 5] = 0u;
+        nm[t >> 5] = 0u;
+      }
+    }
+    if (!__any_sync(kFull, any)) continue;
+    __syncwarp();
     for (int64_t p = p0 + lane; p < p1; p += 32) {
       const int v = a.pins[p];
       const uint64_t r = a.cand[v];
       if (r) {
-        any = true;
         const uint64_t K = cand_key(r, v);
         atomicMax(&maxd[cand_s(r)], (unsigned long long)K);
         atomicMin(&mina[cand_t(r)], (unsigned long long)K);
@@ -143,19 +189,20 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
         atomicOr(&nm[b >> 5], 1u << (b & 31));
       }
     }
-    any = __any_sync(kFull, any);
     __syncwarp();
-    if (any) {
-      const int wt = a.ewgt[e];
-      for (int b = lane; b < a.k; b += 32) {
-        const unsigned long long md = maxd[b], ma = mina[b];
-        const bool has_d = md != 0ull, has_a = ma != ~0ull;
-        if (!has_d && !has_a) continue;
-        if ((nm[b >> 5] >> (b & 31)) & 1u) continue;  // a pin of e in b stays
-        if (has_d && has_a && !(md < ma)) continue;
-        if (has_d) atomicAdd(&a.rg[(int)(md & 0xffffffffu)], wt);
-        if (has_a) atomicAdd(&a.rg[(int)(ma & 0xffffffffu)], -wt);
-      }
+    const int wt = a.ewgt[e];
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+      const int v = a.pins[p];
+      const uint64_t r = a.cand[v];
+      if (!r) continue;
+      const uint64_t K = cand_key(r, v);
+      const int s = cand_s(r), t = cand_t(r);
+      int delta = 0;
+      // last departure from s, no arrival to s before it, no pin of e staying in s
+      if (maxd[s] == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina[s] == ~0ull || K < mina[s])) delta += wt;
+      // first arrival to t, every departure from t before it, no pin of e staying in t
+      if (mina[t] == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd[t] < K) delta -= wt;
+      if (delta) atomicAdd(&a.rg[v], delta);
     }
     __syncwarp();
   }

@@ -373,8 +373,6 @@ __global__ void __launch_bounds__(256) k_rbcand_light(CandArgs a) {
     s_elig[c - 1][q] = w;
   }
   __syncthreads();
-  __shared__ unsigned s_wc[8];
-  __shared__ unsigned long long s_base;
   for (int base = blockIdx.x * blockDim.x; base < a.nlist; base += gridDim.x * blockDim.x) {
     const int i = base + threadIdx.x;
     bool rec = false;
@@ -409,8 +407,13 @@ __global__ void __launch_bounds__(256) k_rbcand_light(CandArgs a) {
         }
       }
     }
-    const unsigned long long pos = block_append(rec, &a.cnt->n_rec, s_wc, &s_base);
+    // warp-level append: the gain work between appends spreads these atomics out in time
+    const unsigned bal = __ballot_sync(kFull, rec);
+    unsigned long long pos0 = 0;
+    if ((threadIdx.x & 31) == 0 && bal) pos0 = atomicAdd(&a.cnt->n_rec, (unsigned long long)__popc(bal));
+    pos0 = __shfl_sync(kFull, pos0, 0);
     if (rec) {
+      const unsigned long long pos = pos0 + __popc(bal & ((1u << (threadIdx.x & 31)) - 1));
       a.rb_hi[pos] = hi;
       a.rb_v[pos] = v;
       a.rb_ct[pos] = ct;

@@ -3,8 +3,7 @@
 //
 // All updates are integer atomics whose final values do not depend on their
 // order: phi row entries +-1, block weights and counts aggregated per thread
-// block; after all moves a second pass sets the bits of the source and target
-// blocks in both edge bitmasks from the final phi entries.
+// block, and XOR toggles of the edge bitmasks at the phi crossings.
 #include "jet_internal.cuh"
 
 namespace jet {
@@ -17,12 +16,8 @@ __device__ __forceinline__ void add_i64(long long *p, long long v) {
 }
 
 struct MoveArgs {
-  const int64_t *vptr, *eptr;
-  const int32_t *inc, *vwgt, *pins;
-  int32_t *mtag;
-  const int32_t *elist;
-  int32_t nlist;
-  long long P;
+  const int64_t *vptr;
+  const int32_t *inc, *vwgt;
   int32_t *part, *phi;
   int64_t *bw;
   int32_t *vcount;
@@ -38,178 +33,19 @@ struct MoveArgs {
 // short (rebalancing rounds).
 constexpr int kMoveLanes = 8;
 
-// Large move lists are applied edge by edge: every edge's owner (a thread, a
-// warp or a block) adds the net +-1 of its moved pins to its own phi row and
-// rewrites its own mask words, with no atomics and no fix-up pass.  Small
-// lists are applied move by move with atomics plus the mask fix-up.  The
-// choice is made on the device from the moved incidences: edge by edge when
-// more than half of all incidences move (the phi row traffic is the same
-// either way; the edge pass saves the atomics and the fix-up pass but has to
-// read every pin).
-__device__ __forceinline__ bool edge_centric(const MoveArgs &a) { return (long long)a.cnt->mv_inc * 2 > a.P; }
-
-// Tags every moved vertex (source | target << 8) and sums the moved incidences.
-__global__ void __launch_bounds__(256) k_apply_prep(MoveArgs a) {
-  const long long nm = (long long)a.cnt->n_moves;
-  unsigned long long inc = 0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nm; i += (long long)gridDim.x * blockDim.x) {
-    const int v = a.mv_v[i];
-    const uint32_t st = a.mv_st[i];
-    a.mtag[v] = (int32_t)((st & 0xffff) | ((st >> 16) << 8));
-    inc += (unsigned long long)(a.vptr[v + 1] - a.vptr[v]);
-  }
-  for (int o = 16; o > 0; o >>= 1) inc += __shfl_xor_sync(kFull, inc, o);
-  if ((threadIdx.x & 31) == 0 && inc) atomicAdd(&a.cnt->mv_inc, inc);
-}
-
-// Owner of row e: one bit of both mask words of block b from its count `val`.
-__device__ __forceinline__ void owner_set_bits(uint32_t *mrow, int kwp, int b, int val) {
-  const uint32_t bit = 1u << (b & 31);
-  uint32_t *w1 = &mrow[b >> 5], *w2 = &mrow[kwp + (b >> 5)];
-  *w1 = (*w1 & ~bit) | (val > 0 ? bit : 0u);
-  *w2 = (*w2 & ~bit) | (val > 1 ? bit : 0u);
-}
-
-// Edges of at most kTinyEdge pins, one thread each.
-__global__ void __launch_bounds__(256) k_apply_edges_tiny(MoveArgs a) {
-  if (!edge_centric(a)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nlist; i += gridDim.x * blockDim.x) {
-    const int64_t e = a.elist[i];
-    const int64_t p0 = a.eptr[e];
-    const int sz = (int)(a.eptr[e + 1] - p0);
-    int tg[kTinyEdge];
-    bool any = false;
-#pragma unroll
-    for (int q = 0; q < kTinyEdge; ++q) {
-      tg[q] = q < sz ? a.mtag[a.pins[p0 + q]] : -1;
-      any |= tg[q] >= 0;
-    }
-    if (!any) continue;
-    int32_t *row = a.phi + e * a.k;
-#pragma unroll
-    for (int q = 0; q < kTinyEdge; ++q)
-      if (tg[q] >= 0) {
-        row[tg[q] & 255] -= 1;
-        row[tg[q] >> 8] += 1;
-      }
-    uint32_t *mrow = a.mask + e * 2 * a.kwp;
-#pragma unroll
-    for (int q = 0; q < kTinyEdge; ++q)
-      if (tg[q] >= 0) {
-        const int s = tg[q] & 255, t = tg[q] >> 8;
-        owner_set_bits(mrow, a.kwp, s, row[s]);
-        owner_set_bits(mrow, a.kwp, t, row[t]);
-      }
-  }
-}
-
-// Edges of 9..2048 pins, one warp each: net deltas per block in shared memory,
-// then only the changed entries of the row and their mask bits are written.
-constexpr int kApplyWarps = 8;
-
-__global__ void __launch_bounds__(kApplyWarps * 32) k_apply_edges_warp(MoveArgs a) {
-  if (!edge_centric(a)) return;
-  __shared__ int s_delta[kApplyWarps][kMaxK];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int *delta = s_delta[w];
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = gw; i < a.nlist; i += nw) {
-    const int64_t e = a.elist[i];
-    const int64_t p1 = a.eptr[e + 1];
-    for (int b = lane; b < a.k; b += 32) delta[b] = 0;
-    __syncwarp();
-    bool any = false;
-    for (int64_t p = a.eptr[e] + lane; p < p1; p += 32) {
-      const int tg = a.mtag[a.pins[p]];
-      if (tg >= 0) {
-        any = true;
-        atomicSub(&delta[tg & 255], 1);
-        atomicAdd(&delta[tg >> 8], 1);
-      }
-    }
-    any = __any_sync(kFull, any);
-    __syncwarp();
-    if (any) {
-      int32_t *row = a.phi + e * a.k;
-      uint32_t *mrow = a.mask + e * 2 * a.kwp;
-      for (int q = 0; q < a.kwp; ++q) {
-        const int b = q * 32 + lane;
-        const int d = b < a.k ? delta[b] : 0;
-        int val = 0;
-        if (d) {  // only the changed entries of the row are read and written
-          val = row[b] + d;
-          row[b] = val;
-        }
-        const unsigned chg = __ballot_sync(kFull, d != 0);
-        if (!chg) continue;
-        const unsigned one = __ballot_sync(kFull, val > 0), two = __ballot_sync(kFull, val > 1);
-        if (lane == 0) {
-          mrow[q] = (mrow[q] & ~chg) | (one & chg);
-          mrow[a.kwp + q] = (mrow[a.kwp + q] & ~chg) | (two & chg);
-        }
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// Edges of more than 2048 pins, one block each.
-__global__ void __launch_bounds__(512) k_apply_edges_block(MoveArgs a) {
-  if (!edge_centric(a)) return;
-  __shared__ int s_delta[kMaxK];
-  __shared__ int s_any;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = blockIdx.x; i < a.nlist; i += gridDim.x) {
-    const int64_t e = a.elist[i];
-    const int64_t p1 = a.eptr[e + 1];
-    for (int b = threadIdx.x; b < a.k; b += blockDim.x) s_delta[b] = 0;
-    if (threadIdx.x == 0) s_any = 0;
-    __syncthreads();
-    bool any = false;
-    for (int64_t p = a.eptr[e] + threadIdx.x; p < p1; p += blockDim.x) {
-      const int tg = a.mtag[a.pins[p]];
-      if (tg >= 0) {
-        any = true;
-        atomicSub(&s_delta[tg & 255], 1);
-        atomicAdd(&s_delta[tg >> 8], 1);
-      }
-    }
-    if (__any_sync(kFull, any) && lane == 0) s_any = 1;
-    __syncthreads();
-    if (s_any) {
-      int32_t *row = a.phi + e * a.k;
-      uint32_t *mrow = a.mask + e * 2 * a.kwp;
-      for (int q = w; q < a.kwp; q += blockDim.x / 32) {  // warp q owns mask word q
-        const int b = q * 32 + lane;
-        const int d = b < a.k ? s_delta[b] : 0;
-        int val = 0;
-        if (d) {
-          val = row[b] + d;
-          row[b] = val;
-        }
-        const unsigned chg = __ballot_sync(kFull, d != 0);
-        if (!chg) continue;
-        const unsigned one = __ballot_sync(kFull, val > 0), two = __ballot_sync(kFull, val > 1);
-        if (lane == 0) {
-          mrow[q] = (mrow[q] & ~chg) | (one & chg);
-          mrow[a.kwp + q] = (mrow[a.kwp + q] & ~chg) | (two & chg);
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // Pi(v) <- t and phi_e[s]--, phi_e[t]++ for every e in I(v); c(V_s), c(V_t)
-// and |V_s|, |V_t| through shared-memory partial sums.
+// and |V_s|, |V_t| through shared-memory partial sums; and both bitmasks of
+// every touched edge, exactly, without a second pass: the atomic updates of
+// one phi entry are serialized in some order, so its 0 <-> 1 crossings (and
+// 1 <-> 2 crossings) alternate, and the final bit is the initial bit XOR the
+// parity of the crossings.  Each thread whose own atomic crosses toggles the
+// bit with atomicXor; XOR commutes, so the order of the toggles is irrelevant.
 __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   __shared__ long long s_dw[kMaxK];
   __shared__ int s_dc[kMaxK];
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) { s_dw[b] = 0; s_dc[b] = 0; }
   __syncthreads();
   const long long nm = (long long)a.cnt->n_moves;
-  const bool edge_mode = edge_centric(a);
   const int sub = threadIdx.x % kMoveLanes;
   const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
   const long long ng = ((long long)gridDim.x * blockDim.x) / kMoveLanes;
@@ -219,75 +55,29 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
     const int s = st & 0xffff, t = st >> 16;
     if (sub == 0) {
       a.part[v] = t;
-      a.mtag[v] = -1;
       const int c = a.vwgt[v];
       atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[s]), (unsigned long long)(-(long long)c));
       atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[t]), (unsigned long long)c);
       atomicSub(&s_dc[s], 1);
       atomicAdd(&s_dc[t], 1);
     }
-    if (edge_mode) continue;  // the edge owners updated phi and the masks
+    const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
     const int64_t j1 = a.vptr[v + 1];
     for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
       const int64_t e = a.inc[j];
-      atomicSub(&a.phi[e * a.k + s], 1);
-      atomicAdd(&a.phi[e * a.k + t], 1);
+      const int os = atomicSub(&a.phi[e * a.k + s], 1);  // os -> os - 1
+      const int ot = atomicAdd(&a.phi[e * a.k + t], 1);  // ot -> ot + 1
+      uint32_t *row = a.mask + e * 2 * a.kwp;
+      if (os == 1) atomicXor(&row[s >> 5], sbit);           // 1 -> 0
+      if (os == 2) atomicXor(&row[a.kwp + (s >> 5)], sbit);  // 2 -> 1
+      if (ot == 0) atomicXor(&row[t >> 5], tbit);           // 0 -> 1
+      if (ot == 1) atomicXor(&row[a.kwp + (t >> 5)], tbit);  // 1 -> 2
     }
   }
   __syncthreads();
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
     if (s_dw[b]) add_i64(reinterpret_cast<long long *>(&a.bw[b]), s_dw[b]);
     if (s_dc[b]) atomicAdd(&a.vcount[b], s_dc[b]);
-  }
-}
-
-// After all moves: bring the bits of s and t in both masks of every e in I(v)
-// (phi_e[.] >= 1 and >= 2) to their final values, read from the final phi.
-// Each word of the row is read once and changed by at most one atomicOr and
-// one atomicAnd, only where it differs.  Every writer of a bit writes its
-// final value, so a stale read that already shows that value can never hide
-// a needed change.
-__global__ void __launch_bounds__(256) k_fix_masks(MoveArgs a) {
-  if (edge_centric(a)) return;
-  const long long nm = (long long)a.cnt->n_moves;
-  const int sub = threadIdx.x % kMoveLanes;
-  const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
-  const long long ng = ((long long)gridDim.x * blockDim.x) / kMoveLanes;
-  for (long long i = g0; i < nm; i += ng) {
-    const int v = a.mv_v[i];
-    const uint32_t st = a.mv_st[i];
-    const int s = st & 0xffff, t = st >> 16;
-    const int ws = s >> 5, wt = t >> 5;
-    const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
-    const int64_t j1 = a.vptr[v + 1];
-    for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
-      const int64_t e = a.inc[j];
-      const int ps = __ldcg(&a.phi[e * a.k + s]), pt = __ldcg(&a.phi[e * a.k + t]);
-      uint32_t *row = a.mask + e * 2 * a.kwp;
-      // words: Lambda at [0, kwp), ">= 2" at [kwp, 2 kwp)
-      const int w1s = ws, w2s = a.kwp + ws, w1t = wt, w2t = a.kwp + wt;
-      uint32_t set1s = ps > 0 ? sbit : 0, set2s = ps > 1 ? sbit : 0, set1t = tbit, set2t = pt > 1 ? tbit : 0;
-      const uint32_t cur1s = __ldcg(&row[w1s]), cur2s = __ldcg(&row[w2s]);
-      const uint32_t cur1t = w1t == w1s ? cur1s : __ldcg(&row[w1t]);
-      const uint32_t cur2t = w2t == w2s ? cur2s : __ldcg(&row[w2t]);
-      if (w1t == w1s) {  // s and t share the words: one update per word
-        const uint32_t want1 = (cur1s & ~(sbit | tbit)) | set1s | set1t;
-        const uint32_t want2 = (cur2s & ~(sbit | tbit)) | set2s | set2t;
-        if (want1 != cur1s) {
-          if (want1 & ~cur1s) atomicOr(&row[w1s], want1 & ~cur1s);
-          if (cur1s & ~want1) atomicAnd(&row[w1s], ~(cur1s & ~want1));
-        }
-        if (want2 != cur2s) {
-          if (want2 & ~cur2s) atomicOr(&row[w2s], want2 & ~cur2s);
-          if (cur2s & ~want2) atomicAnd(&row[w2s], ~(cur2s & ~want2));
-        }
-      } else {
-        if ((cur1s & sbit) != set1s) { if (set1s) atomicOr(&row[w1s], sbit); else atomicAnd(&row[w1s], ~sbit); }
-        if ((cur2s & sbit) != set2s) { if (set2s) atomicOr(&row[w2s], sbit); else atomicAnd(&row[w2s], ~sbit); }
-        if ((cur1t & tbit) != set1t) { if (set1t) atomicOr(&row[w1t], tbit); else atomicAnd(&row[w1t], ~tbit); }
-        if ((cur2t & tbit) != set2t) { if (set2t) atomicOr(&row[w2t], tbit); else atomicAnd(&row[w2t], ~tbit); }
-      }
-    }
   }
 }
 
@@ -352,7 +142,6 @@ __global__ void k_rb_prep(RbArgs a) {
   if (b == 0) {
     a.cnt->n_moves = 0;
     a.cnt->n_rec = 0;
-    a.cnt->mv_inc = 0;
   }
 }
 
@@ -546,12 +335,8 @@ __global__ void __launch_bounds__(256) k_rollback_moves(const int32_t *part, con
 MoveArgs move_args(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   MoveArgs a{};
   a.vptr = c->vptr;
-  a.eptr = c->eptr;
   a.inc = c->inc;
   a.vwgt = c->vwgt;
-  a.pins = c->pins;
-  a.mtag = c->mtag;
-  a.P = c->P;
   a.part = part;
   a.phi = phi;
   a.bw = block_w;
@@ -591,32 +376,8 @@ RbArgs rb_args(jet_ctx *c, const int64_t *block_w, const int32_t *part) {
 
 cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   if (c->n == 0) return cudaSuccess;
-  MoveArgs a = move_args(c, part, phi, block_w);
-  const int g = grid_for((int64_t)c->n * kMoveLanes, 256, c->num_sms, 8);
-  k_apply_prep<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(a);
-  ++c->kernel_launches;
-  if (c->n_tiny > 0) {
-    a.elist = c->e_tiny;
-    a.nlist = c->n_tiny;
-    k_apply_edges_tiny<<<grid_for(c->n_tiny, 256, c->num_sms), 256, 0, c->stream>>>(a);
-    ++c->kernel_launches;
-  }
-  if (c->n_mid > 0) {
-    a.elist = c->e_mid;
-    a.nlist = c->n_mid;
-    k_apply_edges_warp<<<grid_for((int64_t)c->n_mid * 32, kApplyWarps * 32, c->num_sms), kApplyWarps * 32, 0,
-                         c->stream>>>(a);
-    ++c->kernel_launches;
-  }
-  if (c->n_big > 0) {
-    a.elist = c->e_big;
-    a.nlist = c->n_big;
-    k_apply_edges_block<<<c->num_sms * 2, 512, 0, c->stream>>>(a);
-    ++c->kernel_launches;
-  }
-  k_apply<<<g, 256, 0, c->stream>>>(a);
-  ++c->kernel_launches;
-  k_fix_masks<<<g, 256, 0, c->stream>>>(a);
+  const MoveArgs a = move_args(c, part, phi, block_w);
+  k_apply<<<grid_for((int64_t)c->n * kMoveLanes, 256, c->num_sms, 8), 256, 0, c->stream>>>(a);
   ++c->kernel_launches;
   return cudaGetLastError();
 }
@@ -671,7 +432,6 @@ cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *st
 
 cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best) {
   cudaError_t e = cudaMemsetAsync(&c->cnt->n_moves, 0, sizeof(unsigned long long), c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&c->cnt->mv_inc, 0, sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess || c->n == 0) return e;
   k_rollback_moves<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(part, best, c->n, c->mv_v, c->mv_st,
                                                                          c->cnt);
