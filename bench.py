@@ -36,6 +36,11 @@ WORKLOADS = {
                   "k=128, eps=3/100", synth.config_rownet_4m),
     "random_10k": ("random hypergraph n=10,000 m=12,000 |e|=2+Geometric(1/2)<=64, k=8, eps=3/100",
                    synth.config_random_10k),
+    # the VLSI shape at a quarter of the size (phi 141 MB, still larger than L2), for multi-pass ncu captures
+    "vlsi_500k": ("VLSI-shaped hypergraph n=500,000 m=550,000 power-law(2.5)[2,5000] sizes, 80% pins within +-5,000, "
+                  "c in 1..4, k=64, eps=3/100",
+                  lambda seed: (lambda h: (h, 64, synth.part_perm(seed, h.n, 64)))(
+                      synth.vlsi(seed, 500_000, 550_000, window=5_000))),
 }
 TAU = (3, 4)
 SCHEDULE = ((3, 4), (3, 8), (0, 1))
@@ -120,6 +125,23 @@ def kernel_bytes(hg, k, deg, st_before, round_stats):
     return b
 
 
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the candidate kernel from the committed ncu summary, or None if the
+    kernel source changed since that capture (or no capture exists for this workload)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "k_cand_light.md")
+    src = os.path.join(ROOT, "paper_2504_12013_gb300", "csrc", "k_cand.cu")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"kernel_source_sha256 = ([0-9a-f]{64})", txt)
+    if not m or m.group(1) != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None
+    m = re.search(r"traffic_per_launch\[" + re.escape(workload) + r"\] = (\d+)", txt)
+    return int(m.group(1)) if m else None
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world):
     import torch
@@ -136,6 +158,8 @@ def run_gpu(args, rank, world):
     dh = jet.DeviceHypergraph(hg, dev)
     stream = torch.cuda.current_stream(dev)
     ctx = jet.jet_ctx_create(dh, jet.params(k), stream)
+    if args.eager:
+        jet.jet_set_graph_mode(ctx, False)
     st = jet.JetState(ctx, part0)
     part_init = st.part.clone()
     phi_init = st.phi.clone()
@@ -178,6 +202,8 @@ def run_gpu(args, rank, world):
     # times and kernel launches from the profiler, and per-step locks and stats for the byte model
     reset()
     jet.jet_set_graph_mode(ctx, False)
+    if args.eager:  # the timed region already ran kernel by kernel: its family times are the ones
+        prof_eager_timed = prof_timed
     jet.jet_profile_read(ctx, reset=True)
     deg = np.diff(hg.vptr)
     model_bytes = 0
@@ -189,6 +215,8 @@ def run_gpu(args, rank, world):
         trace.append(s)
         model_bytes += kernel_bytes(hg, k, deg, locked_before, s)
     prof = jet.jet_profile_read(ctx, reset=True)
+    if args.eager:
+        prof = prof_eager_timed
     jet.jet_profile_enable(ctx, False)
     assert trace[-1] == final_stats, "replay diverged from the timed run"
 
@@ -259,6 +287,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="time the kernel-by-kernel form instead of the CUDA graphs (same work and results; "
+                         "ncu cannot profile kernels inside graphs with conditional nodes)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", 0))
@@ -314,11 +345,15 @@ def main():
         "data": "synthetic (seeded generator shaped like the paper's VLSI benchmark instances)",
         "config": {"workload": r["desc"], "n": hg.n, "m": hg.m, "pins": hg.P, "k": k, "tau": "3/4",
                    "step": "one Jet iteration (candidates, afterburner, apply, rebalancing, objective)",
+                   "execution": "kernel by kernel" if args.eager else "one CUDA graph per iteration (device-side "
+                                                                          "rebalancing loop)",
                    "l2": "inputs larger than L2 (phi %d MB)" % (hg.m * k * 4 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "candidates (k_cand_light/k_cand_heavy)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None,
+                     "traffic": ncu_traffic(args.workload),
+                     "traffic_note": "DRAM bytes of the first timed launch (profiles/k_cand_light.md)",
                      "peak_source": peak_src,
                      "dominant_family": dom, "family_share": {f: round(v / total_fam, 4) for f, v in fam_ms.items()}
                      if total_fam > 0 else {},
