@@ -373,6 +373,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     c->max_wdeg = (int64_t)hscal[1];
     c->cmax = (int32_t)hscal[2];
     c->unit_ewgt = hscal[3] <= 1 ? 1 : 0;
+    if ((e = prepare_candidate_kernels(c)) != cudaSuccess) { rc = cuda_fail(c, e, "kernel set-up"); break; }
     if (c->max_wdeg >= (1ll << 31) - 1) {
       rc = fail(c, JET_ERR_OVERFLOW, "a sum of omega over I(v) (%lld) does not fit the int32 gains",
                 (long long)c->max_wdeg);
@@ -417,7 +418,8 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
         (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_hist, (size_t)c->k * kRbBins)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_ct, c->n)) != cudaSuccess || (e = dalloc(c, &c->best_part, c->n)) != cudaSuccess ||
-        (e = dalloc(c, &c->locked_ws, c->n)) != cudaSuccess || (e = dalloc(c, &c->stats_scratch, 1)) != cudaSuccess ||
+        (e = dalloc(c, &c->locked_ws, c->n)) != cudaSuccess || (e = dalloc(c, &c->vheavy, c->n)) != cudaSuccess ||
+        (e = dalloc(c, &c->stats_scratch, 1)) != cudaSuccess ||
         (e = cudaMallocHost(reinterpret_cast<void **>(&c->stats_host), sizeof(jet_round_stats))) != cudaSuccess) {
       rc = cuda_fail(c, e, "workspace allocation");
       break;
@@ -448,7 +450,7 @@ void jet_ctx_destroy(jet_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
-                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->stats_scratch};
+                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->vheavy, c->stats_scratch};
   for (void *p : dev) dfree(c, p);
   cudaStreamSynchronize(c->stream);
   for (auto &g : c->graphs) {

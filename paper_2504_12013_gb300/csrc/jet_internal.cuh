@@ -95,6 +95,7 @@ struct jet_ctx {
   int64_t max_wdeg = 0;
   int32_t cmax = 0;
   int unit_ewgt = 0;  // every edge with pins has omega(e) = 1
+  int stage_bps[2] = {1, 1};  // resident blocks per SM: staged candidate / rebalancing-target kernels
   // compact rebalancing keys: priority gain*c (gain >= 0) or gain*(L/c) (gain < 0), L = lcm(1..cmax),
   // stored as (Pmax - P) << 32 | v when max_wdeg*(cmax + L) < 2^32
   int rb_compact = 0;
@@ -103,6 +104,7 @@ struct jet_ctx {
   // size classes
   int32_t *v_light = nullptr, *v_heavy = nullptr;
   int32_t n_light = 0, n_heavy = 0;
+  uint8_t *vheavy = nullptr;  // per vertex: 1 if heavy (weighted degree >= 2^kLightPlanes)
   int32_t *e_tiny = nullptr, *e_mid = nullptr, *e_big = nullptr;  // one array of m ids: [tiny | mid | big]
   int32_t n_tiny = 0, n_mid = 0, n_big = 0;
 
@@ -168,6 +170,7 @@ cudaError_t launch_masks_from_phi(jet_ctx *c, const int32_t *phi);
 cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *out);
 cudaError_t launch_objective_masks(jet_ctx *c);
 // candidates (k_cand.cu)
+cudaError_t prepare_candidate_kernels(jet_ctx *c);
 cudaError_t launch_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, const int32_t *part, const int32_t *phi,
                               const uint8_t *locked);
 cudaError_t launch_rebalance_candidates(jet_ctx *c, const int32_t *part, const int32_t *phi);

@@ -27,6 +27,7 @@ struct CandArgs {
   const int32_t *inc, *ewgt, *vwgt, *part, *phi;
   const uint32_t *mask;
   const uint8_t *locked;
+  const uint8_t *vheavy;
   const int32_t *vlist;
   int32_t nlist, k;
   int32_t tau_num, tau_den;
@@ -141,89 +142,6 @@ __device__ __forceinline__ int argmax_planes(const uint32_t (&pl)[NP][KWP], uint
     conn |= (int32_t)bit << p;
   }
   return t;
-}
-
-// conn planes, union of Lambda(e) and A(v) over I(v) for a light vertex.
-// UNIT: every omega(e) is 1 (no weight gathers, increments instead of adds).
-template <int KWP, int NP, bool UNIT>
-__device__ __forceinline__ int32_t accumulate_light(const CandArgs &a, int v, int s, uint32_t (&pl)[NP][KWP],
-                                                    uint32_t (&any)[KWP]) {
-#pragma unroll
-  for (int q = 0; q < KWP; ++q) {
-    any[q] = 0;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) pl[p][q] = 0;
-  }
-  int32_t A = 0;
-  const int64_t j1 = a.vptr[v + 1];
-  int64_t j = a.vptr[v];
-  // B incidences at a time: their gathers are issued before any is used
-  // (fewer for wide masks, to keep registers and occupancy in balance)
-  constexpr int B = KWP >= 4 ? 2 : 4;
-  for (; j + B <= j1; j += B) {
-    int e[B], w[B];
-    uint32_t M[B][KWP], M2[B][KWP];
-#pragma unroll
-    for (int u = 0; u < B; ++u) e[u] = a.inc[j + u];
-#pragma unroll
-    for (int u = 0; u < B; ++u) {
-      w[u] = UNIT ? 1 : a.ewgt[e[u]];
-      load_rows<KWP>(a.mask + (int64_t)e[u] * 2 * KWP, M[u], M2[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < B; ++u) {
-      uint32_t Mu[KWP], M2u[KWP];
-#pragma unroll
-      for (int q = 0; q < KWP; ++q) { Mu[q] = M[u][q]; M2u[q] = M2[u][q]; }
-      A += mask_bit<KWP>(M2u, s) ? w[u] : 0;  // phi_e[s] >= 2
-#pragma unroll
-      for (int q = 0; q < KWP; ++q) any[q] |= Mu[q];
-      if (UNIT) add_one<KWP, NP>(pl, Mu);
-      else add_weighted<KWP, NP>(pl, Mu, (uint32_t)w[u]);
-    }
-  }
-  for (; j < j1; ++j) {
-    const int e = a.inc[j];
-    const int w = UNIT ? 1 : a.ewgt[e];
-    uint32_t M[KWP], M2[KWP];
-    load_rows<KWP>(a.mask + (int64_t)e * 2 * KWP, M, M2);
-    A += mask_bit<KWP>(M2, s) ? w : 0;
-#pragma unroll
-    for (int q = 0; q < KWP; ++q) any[q] |= M[q];
-    if (UNIT) add_one<KWP, NP>(pl, M);
-    else add_weighted<KWP, NP>(pl, M, (uint32_t)w);
-  }
-  return A;
-}
-
-template <int KWP, bool UNIT>
-__global__ void __launch_bounds__(256) k_cand_light(CandArgs a) {
-  constexpr int NP = kLightPlanes;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nlist; i += gridDim.x * blockDim.x) {
-    const int v = a.vlist[i];
-    uint64_t rec = 0;
-    const int s = a.part[v];
-    if ((unsigned)s >= (unsigned)a.k) {  // invalid block id: report, never index with it
-      atomicOr(&a.cnt->err, kErrPartRange);
-    } else if (!a.locked[v]) {
-      uint32_t pl[NP][KWP], any[KWP];
-      const int32_t A = accumulate_light<KWP, NP, UNIT>(a, v, s, pl, any);
-      uint32_t C[KWP];
-      uint32_t nz = 0;
-#pragma unroll
-      for (int q = 0; q < KWP; ++q) {
-        C[q] = any[q] & ~((s >> 5) == q ? (1u << (s & 31)) : 0u);
-        nz |= C[q];
-      }
-      if (nz) {
-        int32_t conn;
-        const int t = argmax_planes<KWP, NP>(pl, C, conn);
-        const int32_t g = conn - A;
-        if ((long long)a.tau_den * g >= -(long long)a.tau_num * A) rec = pack_cand(g, s, t);
-      }
-    }
-    a.cand[v] = rec;
-  }
 }
 
 // Warp argmax of (conn desc, block asc); block -1 = none.  Result on all lanes.
@@ -350,13 +268,320 @@ __device__ __forceinline__ void eligible_words(const long long *s_cap, int k, in
   }
 }
 
+// ------------------------------------------------------------ light vertices
+// A warp takes 32 consecutive vertex ids; each lane evaluates one light
+// vertex.  Its incidences I(v) are processed in batches of kBatch: the mask
+// rows of a batch are copied into the lane's slots of a double-buffered
+// shared-memory stage with cp.async, so batch b+1's gathers (and batch b+2's
+// incidence loads) are in flight while batch b is added into the bit planes.
+// Slot t of lane l is row t*32 + l of a buffer, so the lanes' reads of the
+// stage are bank-conflict free.  Lanes never read each other's slots.
+
+template <int KWP>
+struct Stage {
+  static constexpr int kRow = 2 * KWP;                          // words of one mask row
+  static constexpr int kBatch = KWP <= 2 ? 4 : (KWP == 4 ? 3 : 2);  // rows per lane per batch
+  // per-warp stage: 2 buffers x kBatch x 32 rows | the same for omega (weighted only)
+  template <bool UNIT>
+  static constexpr int bytes() {
+    return 2 * kBatch * 32 * (kRow + (UNIT ? 0 : 1)) * 4;
+  }
+};
+
+__device__ __forceinline__ void cp_async_16(uint32_t *dst, const uint32_t *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(uint32_t *dst, const uint32_t *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(int32_t *dst, const int32_t *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// every committed group but the most recent one has completed
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int KWP>
+__device__ __forceinline__ void smem_row(const uint32_t *r, uint32_t (&M)[KWP]) {
+  if constexpr (KWP == 1) {
+    M[0] = r[0];
+  } else if constexpr (KWP == 2) {
+    const uint2 x = *reinterpret_cast<const uint2 *>(r);
+    M[0] = x.x; M[1] = x.y;
+  } else {
+#pragma unroll
+    for (int h = 0; h < KWP / 4; ++h) {
+      const uint4 x = reinterpret_cast<const uint4 *>(r)[h];
+      M[4 * h] = x.x; M[4 * h + 1] = x.y; M[4 * h + 2] = x.z; M[4 * h + 3] = x.w;
+    }
+  }
+}
+
+// conn(v, .) bit planes, the union of Lambda(e) and A(v) over I(v) for this
+// lane's vertex: deg incidences starting at inc[j0] (deg = 0 on a lane with
+// no vertex to evaluate; s is read only when deg > 0).  UNIT: every omega(e)
+// is 1 (no weight gathers).
+template <int KWP, int NP, bool UNIT>
+__device__ __forceinline__ int32_t stage_accumulate(const CandArgs &a, uint8_t *stage, int64_t j0, int deg, int s,
+                                                    uint32_t (&pl)[NP][KWP], uint32_t (&any)[KWP]) {
+  using S = Stage<KWP>;
+  constexpr int R = S::kBatch;
+  const int lane = threadIdx.x & 31;
+  uint32_t *rows = reinterpret_cast<uint32_t *>(stage);
+  int32_t *wts = reinterpret_cast<int32_t *>(rows + 2 * R * 32 * S::kRow);
+#pragma unroll
+  for (int q = 0; q < KWP; ++q) {
+    any[q] = 0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) pl[p][q] = 0;
+  }
+  int32_t A = 0;
+  const int nb = (deg + R - 1) / R;
+  int e[R];
+  auto load_inc = [&](int b) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int j = b * R + t;
+      e[t] = j < deg ? a.inc[j0 + j] : -1;
+    }
+  };
+  auto issue_rows = [&](int b) {
+    const int q = b & 1;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      if (e[t] >= 0) {
+        const int slot = (q * R + t) * 32 + lane;
+        const uint32_t *src = a.mask + (int64_t)e[t] * S::kRow;
+        uint32_t *dst = rows + slot * S::kRow;
+        if constexpr (KWP == 1) {
+          cp_async_8(dst, src);
+        } else {
+#pragma unroll
+          for (int h = 0; h < S::kRow / 4; ++h) cp_async_16(dst + 4 * h, src + 4 * h);
+        }
+        if constexpr (!UNIT) cp_async_4(wts + slot, a.ewgt + e[t]);
+      }
+    }
+    cp_async_commit();
+  };
+  if (nb > 0) {
+    load_inc(0);
+    issue_rows(0);
+    if (nb > 1) load_inc(1);
+  }
+  for (int b = 0; b < nb; ++b) {
+    if (b + 1 < nb) {
+      issue_rows(b + 1);
+      if (b + 2 < nb) load_inc(b + 2);
+      cp_async_wait_prior();  // batch b has landed, batch b+1 may be in flight
+    } else {
+      cp_async_wait_all();
+    }
+    const int q = b & 1;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      if (b * R + t < deg) {
+        const int slot = (q * R + t) * 32 + lane;
+        const uint32_t *r = rows + slot * S::kRow;
+        uint32_t M[KWP];
+        smem_row<KWP>(r, M);
+        const int w = UNIT ? 1 : wts[slot];
+        if ((r[KWP + (s >> 5)] >> (s & 31)) & 1u) A += w;  // phi_e[s] >= 2
+#pragma unroll
+        for (int qq = 0; qq < KWP; ++qq) any[qq] |= M[qq];
+        if (UNIT) add_one<KWP, NP>(pl, M);
+        else add_weighted<KWP, NP>(pl, M, (uint32_t)w);
+      }
+    }
+  }
+  return A;
+}
+
+// Light vertices are scanned in groups of 32 consecutive ids per warp.  The
+// ones to evaluate (unlocked for move candidates; in an overloaded block with
+// an eligible target for rebalancing) are appended to a per-warp queue, and
+// the warp evaluates them 32 at a time, so lanes are not left idle by the
+// vertices a pass skips (locked ones, or blocks that are not overloaded).
+// Heavy vertices are skipped here and handled by the warp-per-vertex kernels.
+struct WarpQueue {
+  static constexpr int kCap = 64;
+  int v[kCap], s[kCap], c[kCap], deg[kCap];
+  long long j0[kCap];
+};
+
+// Raw inputs of a scan group, loaded one group ahead so that their latency
+// overlaps the previous group's work (first used in the next iteration).
+struct GroupRaw {
+  int s, hv, lk;
+};
+
+__device__ __forceinline__ GroupRaw fetch_group(const CandArgs &a, int64_t v, bool want_lock) {
+  GroupRaw r{0, 1, 1};
+  if (v < a.n) {
+    r.s = a.part[v];
+    r.hv = a.vheavy[v];
+    r.lk = want_lock ? a.locked[v] : 0;
+  }
+  return r;
+}
+
+// Appends this lane's vertex (if `act`) to the warp queue; returns the new
+// (warp-uniform) queue length.
+__device__ __forceinline__ int enqueue(WarpQueue *q, int qn, bool act, int v, int s, int c, int64_t j0, int deg) {
+  const int lane = threadIdx.x & 31;
+  const unsigned bal = __ballot_sync(kFull, act);
+  if (act) {
+    const int pos = qn + __popc(bal & ((1u << lane) - 1));
+    q->v[pos] = v;
+    q->s[pos] = s;
+    q->c[pos] = c;
+    q->deg[pos] = deg;
+    q->j0[pos] = j0;
+  }
+  __syncwarp();
+  return qn + __popc(bal);
+}
+
+// Removes the first 32 entries of the queue (qn >= 32).
+__device__ __forceinline__ int dequeue32(WarpQueue *q, int qn) {
+  const int lane = threadIdx.x & 31;
+  const int rest = qn - 32;
+  int v = 0, s = 0, c = 0, deg = 0;
+  long long j0 = 0;
+  if (lane < rest) {
+    v = q->v[32 + lane]; s = q->s[32 + lane]; c = q->c[32 + lane]; deg = q->deg[32 + lane]; j0 = q->j0[32 + lane];
+  }
+  __syncwarp();
+  if (lane < rest) {
+    q->v[lane] = v; q->s[lane] = s; q->c[lane] = c; q->deg[lane] = deg; q->j0[lane] = j0;
+  }
+  __syncwarp();
+  return rest;
+}
+
+// Evaluates queue entries 0..cnt-1 (lane l takes entry l) for move candidates.
 template <int KWP, bool UNIT>
-__global__ void __launch_bounds__(256) k_rbcand_light(CandArgs a) {
+__device__ __forceinline__ void cand_batch(const CandArgs &a, uint8_t *stage, const WarpQueue *q, int cnt) {
   constexpr int NP = kLightPlanes;
+  const int lane = threadIdx.x & 31;
+  const bool mine = lane < cnt;
+  const int v = mine ? q->v[lane] : 0, s = mine ? q->s[lane] : 0, deg = mine ? q->deg[lane] : 0;
+  const int64_t j0 = mine ? q->j0[lane] : 0;
+  uint32_t pl[NP][KWP], any[KWP];
+  const int32_t A = stage_accumulate<KWP, NP, UNIT>(a, stage, j0, deg, s, pl, any);
+  if (!mine) return;
+  uint64_t rec = 0;
+  uint32_t C[KWP];
+  uint32_t nz = 0;
+#pragma unroll
+  for (int qq = 0; qq < KWP; ++qq) {
+    C[qq] = any[qq] & ~((s >> 5) == qq ? (1u << (s & 31)) : 0u);
+    nz |= C[qq];
+  }
+  if (nz) {
+    int32_t conn;
+    const int t = argmax_planes<KWP, NP>(pl, C, conn);
+    const int32_t g = conn - A;
+    if ((long long)a.tau_den * g >= -(long long)a.tau_num * A) rec = pack_cand(g, s, t);
+  }
+  a.cand[v] = rec;
+}
+
+template <int KWP, bool UNIT>
+__global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_cand_light(CandArgs a) {
+  extern __shared__ __align__(16) uint8_t dyn_smem[];
+  __shared__ WarpQueue s_q[8];
+  const int w = threadIdx.x >> 5;
+  uint8_t *stage = dyn_smem + w * Stage<KWP>::template bytes<UNIT>();
+  WarpQueue *q = &s_q[w];
+  const int lane = threadIdx.x & 31;
+  const int warps = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * warps * 32;
+  int64_t base = ((int64_t)blockIdx.x * warps + w) * 32;
+  GroupRaw cur = fetch_group(a, base + lane, true);
+  int qn = 0;
+  for (; base < a.n; base += stride) {
+    const GroupRaw nxt = fetch_group(a, base + stride + lane, true);
+    const int64_t v = base + lane;
+    bool act = false;
+    int64_t j0 = 0;
+    int deg = 0;
+    if (v < a.n && !cur.hv) {
+      if ((unsigned)cur.s >= (unsigned)a.k) {  // invalid block id: report, never index with it
+        atomicOr(&a.cnt->err, kErrPartRange);
+        a.cand[v] = 0;
+      } else if (cur.lk) {
+        a.cand[v] = 0;
+      } else {
+        act = true;
+        j0 = a.vptr[v];
+        deg = (int)(a.vptr[v + 1] - j0);
+      }
+    }
+    qn = enqueue(q, qn, act, (int)v, cur.s, 0, j0, deg);
+    if (qn >= 32) {
+      cand_batch<KWP, UNIT>(a, stage, q, 32);
+      qn = dequeue32(q, qn);
+    }
+    cur = nxt;
+  }
+  if (qn > 0) cand_batch<KWP, UNIT>(a, stage, q, qn);
+}
+
+// Evaluates queue entries 0..cnt-1 for rebalancing and appends their records.
+template <int KWP, bool UNIT, int kTab>
+__device__ __forceinline__ void rb_batch(const CandArgs &a, uint8_t *stage, const WarpQueue *q, int cnt,
+                                         const long long *s_cap, const uint32_t (*s_elig)[KWP]) {
+  constexpr int NP = kLightPlanes;
+  const int lane = threadIdx.x & 31;
+  const bool mine = lane < cnt;
+  const int v = mine ? q->v[lane] : 0, s = mine ? q->s[lane] : 0, deg = mine ? q->deg[lane] : 0;
+  const int32_t c = mine ? q->c[lane] : 0;
+  const int64_t j0 = mine ? q->j0[lane] : 0;
+  uint32_t pl[NP][KWP], any[KWP];
+  const int32_t A = stage_accumulate<KWP, NP, UNIT>(a, stage, j0, deg, s, pl, any);
+  uint64_t hi = 0;
+  int32_t ct = 0;
+  if (mine) {
+    uint32_t C[KWP];
+    if (c <= kTab) {
+#pragma unroll
+      for (int qq = 0; qq < KWP; ++qq) C[qq] = s_elig[c - 1][qq];
+    } else {
+      eligible_words<KWP>(s_cap, a.k, c, C);
+    }
+    int32_t conn;
+    const int t = argmax_planes<KWP, NP>(pl, C, conn);
+    hi = rb_hi_of(a, conn - A, c);
+    ct = (c << 16) | (s << 8) | t;
+  }
+  const unsigned bal = __ballot_sync(kFull, mine);
+  unsigned long long pos0 = 0;
+  if (lane == 0) pos0 = atomicAdd(&a.cnt->n_rec, (unsigned long long)__popc(bal));
+  pos0 = __shfl_sync(kFull, pos0, 0);
+  if (mine) {
+    const unsigned long long pos = pos0 + lane;
+    a.rb_hi[pos] = hi;
+    a.rb_v[pos] = v;
+    a.rb_ct[pos] = ct;
+  }
+}
+
+template <int KWP, bool UNIT>
+__global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_rbcand_light(CandArgs a) {
   constexpr int kTab = 32;  // eligibility words tabulated for c(v) <= 32
   __shared__ long long s_cap[kMaxK], s_bw[kMaxK];
   __shared__ int s_over[kMaxK];
   __shared__ uint32_t s_elig[kTab][KWP];
+  __shared__ WarpQueue s_q[8];
+  extern __shared__ __align__(16) uint8_t dyn_smem[];
+  const int w = threadIdx.x >> 5;
+  uint8_t *stage = dyn_smem + w * Stage<KWP>::template bytes<UNIT>();
+  WarpQueue *q = &s_q[w];
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
     s_cap[b] = a.rbb[b].cap;
     s_bw[b] = a.rbb[b].bw;
@@ -364,61 +589,57 @@ __global__ void __launch_bounds__(256) k_rbcand_light(CandArgs a) {
   }
   __syncthreads();
   for (int x = threadIdx.x; x < kTab * KWP; x += blockDim.x) {
-    const int c = x / KWP + 1, q = x % KWP;
-    uint32_t w = 0;
+    const int c = x / KWP + 1, qq = x % KWP;
+    uint32_t wd = 0;
     for (int bit = 0; bit < 32; ++bit) {
-      const int b = q * 32 + bit;
-      if (b < a.k && s_cap[b] >= c) w |= 1u << bit;
+      const int b = qq * 32 + bit;
+      if (b < a.k && s_cap[b] >= c) wd |= 1u << bit;
     }
-    s_elig[c - 1][q] = w;
+    s_elig[c - 1][qq] = wd;
   }
   __syncthreads();
-  for (int base = blockIdx.x * blockDim.x; base < a.nlist; base += gridDim.x * blockDim.x) {
-    const int i = base + threadIdx.x;
-    bool rec = false;
-    int v = 0, s = 0;
-    uint64_t hi = 0;
-    int32_t ct = 0;
-    if (i < a.nlist) {
-      v = a.vlist[i];
-      s = a.part[v];
-      if ((unsigned)s < (unsigned)a.k && s_over[s]) {
-        const int32_t c = a.vwgt[v];
-        if (2ll * c <= 3ll * (s_bw[s] - a.A)) {  // heavy vertices are never moved
+  const int lane = threadIdx.x & 31;
+  const int warps = blockDim.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * warps * 32;
+  int64_t base = ((int64_t)blockIdx.x * warps + w) * 32;
+  GroupRaw cur = fetch_group(a, base + lane, false);
+  int qn = 0;
+  for (; base < a.n; base += stride) {
+    const GroupRaw nxt = fetch_group(a, base + stride + lane, false);
+    const int64_t v = base + lane;
+    const int s = cur.s;
+    bool act = false;
+    int32_t c = 0;
+    int64_t j0 = 0;
+    int deg = 0;
+    if (v < a.n && !cur.hv && (unsigned)s < (unsigned)a.k && s_over[s]) {
+      c = a.vwgt[v];
+      if (2ll * c <= 3ll * (s_bw[s] - a.A)) {  // heavy vertices (Section 4.3) are never moved
+        uint32_t nz = 0;
+        if (c <= kTab) {
+#pragma unroll
+          for (int qq = 0; qq < KWP; ++qq) nz |= s_elig[c - 1][qq];
+        } else {
           uint32_t C[KWP];
-          if (c <= kTab) {
+          eligible_words<KWP>(s_cap, a.k, c, C);
 #pragma unroll
-            for (int q = 0; q < KWP; ++q) C[q] = s_elig[c - 1][q];
-          } else {
-            eligible_words<KWP>(s_cap, a.k, c, C);
-          }
-          uint32_t nz = 0;
-#pragma unroll
-          for (int q = 0; q < KWP; ++q) nz |= C[q];
-          if (nz) {
-            uint32_t pl[NP][KWP], any[KWP];
-            const int32_t A = accumulate_light<KWP, NP, UNIT>(a, v, s, pl, any);
-            int32_t conn;
-            const int t = argmax_planes<KWP, NP>(pl, C, conn);
-            hi = rb_hi_of(a, conn - A, c);
-            ct = (c << 16) | (s << 8) | t;
-            rec = true;
-          }
+          for (int qq = 0; qq < KWP; ++qq) nz |= C[qq];
+        }
+        if (nz) {
+          act = true;
+          j0 = a.vptr[v];
+          deg = (int)(a.vptr[v + 1] - j0);
         }
       }
     }
-    // warp-level append: the gain work between appends spreads these atomics out in time
-    const unsigned bal = __ballot_sync(kFull, rec);
-    unsigned long long pos0 = 0;
-    if ((threadIdx.x & 31) == 0 && bal) pos0 = atomicAdd(&a.cnt->n_rec, (unsigned long long)__popc(bal));
-    pos0 = __shfl_sync(kFull, pos0, 0);
-    if (rec) {
-      const unsigned long long pos = pos0 + __popc(bal & ((1u << (threadIdx.x & 31)) - 1));
-      a.rb_hi[pos] = hi;
-      a.rb_v[pos] = v;
-      a.rb_ct[pos] = ct;
+    qn = enqueue(q, qn, act, (int)v, s, c, j0, deg);
+    if (qn >= 32) {
+      rb_batch<KWP, UNIT, kTab>(a, stage, q, 32, s_cap, s_elig);
+      qn = dequeue32(q, qn);
     }
+    cur = nxt;
   }
+  if (qn > 0) rb_batch<KWP, UNIT, kTab>(a, stage, q, qn, s_cap, s_elig);
 }
 
 template <int KWP>
@@ -473,8 +694,9 @@ cudaError_t launch_cand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_light > 0) {
     a.vlist = c->v_light;
     a.nlist = c->n_light;
-    if (c->unit_ewgt) k_cand_light<KWP, true><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
-    else k_cand_light<KWP, false><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    const int g = grid_for(c->n, 256, c->num_sms, c->stage_bps[0]);
+    if (c->unit_ewgt) k_cand_light<KWP, true><<<g, 256, 8 * Stage<KWP>::template bytes<true>(), c->stream>>>(a);
+    else k_cand_light<KWP, false><<<g, 256, 8 * Stage<KWP>::template bytes<false>(), c->stream>>>(a);
     ++c->kernel_launches;
   }
   if (c->n_heavy > 0) {
@@ -492,8 +714,9 @@ cudaError_t launch_rbcand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_light > 0) {
     a.vlist = c->v_light;
     a.nlist = c->n_light;
-    if (c->unit_ewgt) k_rbcand_light<KWP, true><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
-    else k_rbcand_light<KWP, false><<<grid_for(c->n_light, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    const int g = grid_for(c->n, 256, c->num_sms, c->stage_bps[1]);
+    if (c->unit_ewgt) k_rbcand_light<KWP, true><<<g, 256, 8 * Stage<KWP>::template bytes<true>(), c->stream>>>(a);
+    else k_rbcand_light<KWP, false><<<g, 256, 8 * Stage<KWP>::template bytes<false>(), c->stream>>>(a);
     ++c->kernel_launches;
   }
   if (c->n_heavy > 0) {
@@ -511,6 +734,7 @@ CandArgs make_args(jet_ctx *c, const int32_t *part, const int32_t *phi) {
   a.inc = c->inc;
   a.ewgt = c->ewgt;
   a.vwgt = c->vwgt;
+  a.vheavy = c->vheavy;
   a.part = part;
   a.phi = phi;
   a.mask = c->mask;
@@ -529,7 +753,38 @@ CandArgs make_args(jet_ctx *c, const int32_t *part, const int32_t *phi) {
   return a;
 }
 
+// Dynamic shared memory limits and resident blocks per SM of the staged light
+// kernels this context launches (grids are sized to one resident wave).
+template <int KWP, bool UNIT>
+cudaError_t prepare_stage(jet_ctx *c) {
+  const int bytes = 8 * Stage<KWP>::template bytes<UNIT>();
+  cudaError_t e = cudaFuncSetAttribute(k_cand_light<KWP, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rbcand_light<KWP, UNIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->stage_bps[0], k_cand_light<KWP, UNIT>, 256, bytes);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->stage_bps[1], k_rbcand_light<KWP, UNIT>, 256, bytes);
+  for (int i = 0; i < 2; ++i)
+    if (c->stage_bps[i] < 1) c->stage_bps[i] = 1;
+  return e;
+}
+
+template <int KWP>
+cudaError_t prepare_stage_kwp(jet_ctx *c) {
+  return c->unit_ewgt ? prepare_stage<KWP, true>(c) : prepare_stage<KWP, false>(c);
+}
+
 }  // namespace
+
+cudaError_t prepare_candidate_kernels(jet_ctx *c) {
+  switch (c->kwp) {
+    case 1: return prepare_stage_kwp<1>(c);
+    case 2: return prepare_stage_kwp<2>(c);
+    case 4: return prepare_stage_kwp<4>(c);
+    default: return prepare_stage_kwp<8>(c);
+  }
+}
 
 cudaError_t launch_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, const int32_t *part, const int32_t *phi,
                               const uint8_t *locked) {

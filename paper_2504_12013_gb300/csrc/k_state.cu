@@ -348,10 +348,10 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
   if (e != cudaSuccess) return e;
   int32_t t[kClasses];
   if (c->n > 0) {
-    k_vertex_codes<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(wdeg, c->n, code);
+    k_vertex_codes<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(wdeg, c->n, c->vheavy);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = stable_partition(c, code, c->n, c->v_light, t);
+  if (e == cudaSuccess) e = stable_partition(c, c->vheavy, c->n, c->v_light, t);
   if (e == cudaSuccess) {
     c->n_light = t[0];
     c->n_heavy = t[1];
