@@ -258,6 +258,109 @@ def run_e2e(args, hg, k, part0, dev):
             "objective": res["objective"]}
 
 
+def run_batched(args, dev):
+    """The batched form: 256 independent random hypergraphs (n log-uniform in [1k, 200k], m = 1.1 n,
+    |e| = 2 + Geometric(0.4) <= 256, k in {2, 8, 32}, unit weights), each refined to convergence
+    (Algorithm 1, schedule 3/4, 3/8, 0, limit 8) -- all of them by ONE batch-graph launch per step, against
+    the plain path (jet_refine on each instance in turn).  Each step restores the initial partitions first.
+    The end-to-end figure also re-uploads every hypergraph and partition from pinned host memory and reads
+    the partitions back, per step."""
+    import torch
+
+    from paper_2504_12013_gb300 import jet
+    t0 = time.time()
+    insts = synth.config_batched(args.seed)
+    stream = torch.cuda.current_stream(dev)
+    dhs = [jet.DeviceHypergraph(h, dev) for h, _, _ in insts]
+    ctxs = [jet.jet_ctx_create(d, jet.params(k), stream) for d, (_, k, _) in zip(dhs, insts)]
+    states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, insts)]
+    init = [st.part.clone() for st in states]
+    pins = [h.P for h, _, _ in insts]
+    log(f"batched: {len(insts)} instances, sum n={sum(h.n for h, _, _ in insts)}, sum P={sum(pins)} "
+        f"(set up in {time.time() - t0:.1f}s)")
+
+    def restore():
+        for st, p in zip(states, init):
+            st.part.copy_(p)
+
+    b = jet.jet_batch_create(ctxs, stream)
+    split, tune_ms = jet.jet_batch_tune(b, SCHEDULE, LIMIT, states, [0, 1, 2, 4, 8])
+    for _ in range(max(args.warmup, 1)):
+        restore()
+        res = jet.jet_batch_refine(b, SCHEDULE, LIMIT, states)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.batch_steps):
+        restore()
+        res = jet.jet_batch_refine(b, SCHEDULE, LIMIT, states)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_batch = ev0.elapsed_time(ev1) / args.batch_steps
+    pin_rounds = sum(p * r["iterations"] for p, r in zip(pins, res))
+    parts_batch = [st.part[: h.n].cpu().numpy().copy() for st, (h, _, _) in zip(states, insts)]
+    b.close()
+
+    # plain path: one jet_refine (device-side loop, one graph launch and one synchronization) per instance
+    for c, st in zip(ctxs[:8], states[:8]):  # warm the per-context graphs
+        jet.jet_refine(c, SCHEDULE, LIMIT, st.part, st.phi, st.block_w)
+    restore()
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    res_plain = [jet.jet_refine(c, SCHEDULE, LIMIT, st.part, st.phi, st.block_w) for c, st in zip(ctxs, states)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plain = ev0.elapsed_time(ev1)
+    same = all(a["iterations"] == r["iterations"] and a["objective"] == r["objective"] for a, r in zip(res_plain, res))
+    same = same and all(np.array_equal(st.part[: h.n].cpu().numpy(), pb)
+                        for st, (h, _, _), pb in zip(states, insts, parts_batch))
+
+    # end to end: inputs from pinned host memory every step
+    host_bufs = []
+    for d, (h, _, p) in zip(dhs, insts):
+        bufs = {}
+        for name in ("eptr", "pins", "vptr", "inc", "vwgt", "ewgt"):
+            a = getattr(h, name)
+            t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True)
+            t.numpy()[:] = a
+            bufs[name] = t
+        pt = torch.empty(h.n, dtype=torch.int32, pin_memory=True)
+        pt.numpy()[:] = p
+        host_bufs.append((bufs, pt))
+    out_parts = [torch.empty(h.n, dtype=torch.int32, pin_memory=True) for h, _, _ in insts]
+    b = jet.jet_batch_create(ctxs, stream)
+    jet.jet_batch_set_split(b, split)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    for _ in range(args.batch_steps):
+        for d, st, (bufs, pt) in zip(dhs, states, host_bufs):
+            for name, t in bufs.items():
+                getattr(d, name).copy_(t, non_blocking=True)
+            st.part[: pt.numel()].copy_(pt, non_blocking=True)
+        jet.jet_batch_refine(b, SCHEDULE, LIMIT, states)
+        for st, o in zip(states, out_parts):
+            o.copy_(st.part[: o.numel()], non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t1) / args.batch_steps
+    b.close()
+    h2d = sum(h.nbytes() + 4 * h.n for h, _, _ in insts)
+    d2h = sum(4 * h.n for h, _, _ in insts)
+    for c in ctxs:
+        c.close()
+    return {"metric": "Jet-round pins/s, batched (256 instances to convergence, one graph launch per step)",
+            "value": pin_rounds / (ms_batch / 1e3), "unit": "pins/s", "ms_per_step": ms_batch,
+            "steps": args.batch_steps, "instances": len(insts), "pins": sum(pins),
+            "jet_iterations": sum(r["iterations"] for r in res),
+            "plain": {"value": pin_rounds / (ms_plain / 1e3), "unit": "pins/s", "ms_per_step": ms_plain,
+                      "how": "jet_refine on each instance in turn (one graph launch + synchronization each)"},
+            "speedup_vs_plain": ms_plain / ms_batch, "results_identical_to_plain": bool(same),
+            "work_split": {"chosen": split, "tuned_ms": tune_ms},
+            "e2e": {"value": pin_rounds / e2e_s, "unit": "pins/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "config": "256 random hypergraphs, n log-uniform [1k, 200k], m = 1.1 n, |e| = 2 + Geometric(0.4) <= 256, "
+                      "k from {2, 8, 32}, unit weights, eps = 3/100, hash partitions"}
+
+
 def cpu_baseline(hg, k, part0, budget_s):
     """The oracle as it stands (single thread), rounds at tau = 3/4 from the same start until budget_s."""
     import oracle
@@ -287,6 +390,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="time the kernel-by-kernel form instead of the CUDA graphs (same work and results; "
                          "ncu cannot profile kernels inside graphs with conditional nodes)")
@@ -311,6 +416,7 @@ def main():
             dist.destroy_process_group()
         return
     e2e = None if args.no_e2e else run_e2e(args, hg, k, r["part0"], r["dev"])
+    batched = None if args.no_batched else run_batched(args, r["dev"])
     cpu = None if args.no_cpu_baseline else cpu_baseline(hg, k, r["part0"], args.cpu_budget)
 
     import json as _j
@@ -365,6 +471,7 @@ def main():
         "gpu_launches": launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "batched": batched,
         "trace_first_steps": r["trace"][:3],
     }
     print(json.dumps(line), flush=True)

@@ -190,10 +190,53 @@ int jet_rebalance(jet_ctx *ctx, int32_t *part, int32_t *phi, int64_t *block_w, j
  * `limit` iterations in a row bring no strictly better balanced partition,
  * then rolls back to the best balanced partition seen.  part (device, n)
  * is updated in place; phi/block_w (device, caller-sized m*k and k) hold the
- * final state.  *result (HOST) receives the summary.  Synchronizes.
+ * final state.  *result (HOST) receives the summary.  Synchronizes.  In graph
+ * mode (the default, see jet_set_graph_mode) the whole schedule runs as one
+ * CUDA graph with the loop control on the device and one synchronization at
+ * the end; the kernel-by-kernel form reads each iteration's statistics.
  */
 int jet_refine(jet_ctx *ctx, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *part, int32_t *phi,
                int64_t *block_w, jet_refine_result *result);
+
+/*
+ * Batches: many independent instances refined by ONE CUDA-graph launch
+ * (Algorithm 1 per instance, as in jet_refine).  Each instance has its own
+ * context (its own hypergraph, k and eps); jet_batch_create takes `count`
+ * distinct contexts (HOST array) and a stream for the launches (NULL =
+ * legacy default stream).  The batch graph holds every instance's refinement
+ * as an independent branch, so their kernels overlap on the device; results
+ * are identical to running jet_refine on each context alone.
+ *
+ * jet_batch_refine: part[i], phi[i], block_w[i] (HOST arrays of DEVICE
+ * pointers, one per instance, sized as for jet_refine) are refined in place;
+ * results (HOST, count entries, may be NULL) receive the summaries.  The
+ * graph is built on the first call and reused while the schedule, limit and
+ * state pointers are unchanged.  Synchronizes.  Errors as jet_refine, for
+ * the first failing instance; the message is in jet_batch_last_error.
+ *
+ * Work split: with split s = 0 every instance sizes its grids for all SMs;
+ * with s > 0 instance i sizes them for max(1, s * num_SMs * P_i / sum P)
+ * SMs (P = pins), so many small instances share the device instead of each
+ * asking for all of it.  jet_batch_tune runs the batch once per candidate
+ * split (splits, HOST, n_splits entries, each in [0, 64]), restoring every
+ * part[i] before each run, keeps the fastest split, and leaves the
+ * partitions as they were; ms_out (HOST, may be NULL) gets each run's
+ * device time.  The contexts' grid sizes return to all SMs when the batch
+ * is destroyed.  The paper has no batched form; this is the serving-side
+ * pattern of running many refinements on one GPU.
+ */
+typedef struct jet_batch jet_batch;
+
+int jet_batch_create(jet_batch **out, jet_ctx *const *ctxs, int32_t count, void *stream);
+void jet_batch_destroy(jet_batch *batch);
+const char *jet_batch_last_error(const jet_batch *batch);
+int jet_batch_refine(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
+                     int32_t *const *phi, int64_t *const *block_w, jet_refine_result *results);
+int jet_batch_set_split(jet_batch *batch, int32_t split);
+int jet_batch_get_split(const jet_batch *batch);
+int jet_batch_tune(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
+                   int32_t *const *phi, int64_t *const *block_w, const int32_t *splits, int32_t n_splits,
+                   float *ms_out);
 
 /*
  * The candidate step of jet_refine_round alone (Section 4.1), for

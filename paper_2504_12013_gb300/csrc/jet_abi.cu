@@ -13,8 +13,10 @@
 using namespace jet;
 
 namespace {
-
 thread_local char g_err[256] = {0};
+}  // namespace
+
+namespace jet {
 
 int fail(jet_ctx *c, int code, const char *fmt, ...) {
   char *dst = c ? c->err : g_err;
@@ -151,63 +153,82 @@ int check_tau(jet_ctx *c, int32_t tau_num, int32_t tau_den) {
   return JET_OK;
 }
 
+// Streams and events used while capturing this context's graphs (created once).
+cudaError_t ensure_capture_streams(jet_ctx *c) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+    if (!c->cap_stream[i]) e = cudaStreamCreateWithFlags(&c->cap_stream[i], cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (!c->graph_ev[i]) e = cudaEventCreate(&c->graph_ev[i]);
+  return e;
+}
+
 // ---- CUDA-graph form of jet_refine_round
 // The kernels of one iteration are captured once per argument set: the
 // candidate, afterburner, approval and apply kernels, then a WHILE node whose
 // body is one rebalancing round (its condition is set on the device by the
 // check kernel before the node and by the post kernel at the end of each
 // round), then the objective and statistics.  One launch, no host
-// synchronization.  Event-record nodes bracket the candidate kernels so the
-// profiler can time them inside the graph.
-cudaError_t capture_round(jet_ctx *c, int32_t tn, int32_t td, int32_t *part, int32_t *phi, int64_t *bw, uint8_t *locked,
-                          jet_round_stats *stats, cudaGraphConditionalHandle h, cudaEvent_t ev0, cudaEvent_t ev1,
-                          cudaGraphNode_t ev_nodes[2]) {
-  cudaStream_t s0 = c->cap_stream[0], s1 = c->cap_stream[1];
-  cudaError_t e;
-  cudaStreamCaptureStatus st;
-  cudaGraph_t cg = nullptr;
-  const cudaGraphNode_t *deps = nullptr;
-  const cudaGraphEdgeData *ed = nullptr;
-  size_t nd = 0;
-  c->stream = s0;
-  if ((e = reset_counters(c)) != cudaSuccess) return e;
-  // external records become event-record nodes (a plain record in capture only orders streams);
-  // the nodes are looked up after the capture
-  (void)ev_nodes;
-  if ((e = cudaEventRecordWithFlags(ev0, s0, cudaEventRecordExternal)) != cudaSuccess) return e;
-  if ((e = launch_candidates(c, tn, td, part, phi, locked)) != cudaSuccess) return e;
-  if ((e = cudaEventRecordWithFlags(ev1, s0, cudaEventRecordExternal)) != cudaSuccess) return e;
-  if ((e = launch_afterburner(c, part, phi)) != cudaSuccess) return e;
-  if ((e = launch_approve(c, locked, nullptr, nullptr, true)) != cudaSuccess) return e;
-  if ((e = launch_apply(c, part, phi, bw)) != cudaSuccess) return e;
-  if ((e = launch_rb_check(c, bw, h, 1)) != cudaSuccess) return e;
-  // WHILE node: rebalancing rounds
-  if ((e = cudaStreamGetCaptureInfo(s0, &st, nullptr, &cg, &deps, &ed, &nd)) != cudaSuccess) return e;
-  cudaGraphNodeParams cp{};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  cudaGraphNode_t cn;
-  if ((e = cudaGraphAddNode(&cn, cg, deps, ed, nd, &cp)) != cudaSuccess) return e;
-  if ((e = cudaStreamUpdateCaptureDependencies(s0, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) != cudaSuccess)
-    return e;
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if ((e = cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
-    return e;
-  c->stream = s1;
-  cudaError_t eb = launch_rb_prep(c, bw);
-  if (eb == cudaSuccess) eb = launch_rebalance_candidates(c, part, phi);
-  if (eb == cudaSuccess) eb = launch_rb_select(c, part);
-  if (eb == cudaSuccess) eb = launch_apply(c, part, phi, bw);
-  if (eb == cudaSuccess) eb = launch_rb_post(c, bw, h, 1);
-  cudaGraph_t tmp = nullptr;
-  e = cudaStreamEndCapture(s1, &tmp);
-  c->stream = s0;
-  if (eb != cudaSuccess) return eb;
-  if (e != cudaSuccess) return e;
-  if ((e = launch_objective_masks(c)) != cudaSuccess) return e;
-  return launch_stats(c, bw, stats, 0);
+// synchronization.  Event-record nodes (ev0/ev1, optional) bracket the
+// candidate kernels so the profiler can time them inside the graph.
+// s_main must be capturing (into a top-level graph or into the body of an
+// enclosing conditional node); the rebalancing body is captured on s_body.
+cudaError_t capture_iteration(jet_ctx *c, cudaStream_t s_main, cudaStream_t s_body, int32_t tn, int32_t td,
+                              int32_t *part, int32_t *phi, int64_t *bw, uint8_t *locked, jet_round_stats *stats,
+                              cudaEvent_t ev0, cudaEvent_t ev1) {
+  cudaStream_t saved = c->stream;
+  c->stream = s_main;
+  cudaError_t e = [&]() -> cudaError_t {
+    cudaError_t e;
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    if ((e = cudaStreamGetCaptureInfo(s_main, &st, nullptr, &cg, &deps, &ed, &nd)) != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    if ((e = reset_counters(c)) != cudaSuccess) return e;
+    // external records become event-record nodes (a plain record in capture only orders streams)
+    if (ev0 && (e = cudaEventRecordWithFlags(ev0, s_main, cudaEventRecordExternal)) != cudaSuccess) return e;
+    if ((e = launch_candidates(c, tn, td, part, phi, locked)) != cudaSuccess) return e;
+    if (ev1 && (e = cudaEventRecordWithFlags(ev1, s_main, cudaEventRecordExternal)) != cudaSuccess) return e;
+    if ((e = launch_afterburner(c, part, phi)) != cudaSuccess) return e;
+    if ((e = launch_approve(c, locked, nullptr, nullptr, true)) != cudaSuccess) return e;
+    if ((e = launch_apply(c, part, phi, bw)) != cudaSuccess) return e;
+    if ((e = launch_rb_check(c, bw, h, 1)) != cudaSuccess) return e;
+    // WHILE node: rebalancing rounds
+    if ((e = cudaStreamGetCaptureInfo(s_main, &st, nullptr, &cg, &deps, &ed, &nd)) != cudaSuccess) return e;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn;
+    if ((e = cudaGraphAddNode(&cn, cg, deps, ed, nd, &cp)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(s_main, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+      return e;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+        cudaSuccess)
+      return e;
+    c->stream = s_body;
+    cudaError_t eb = launch_rb_prep(c, bw);
+    if (eb == cudaSuccess) eb = launch_rebalance_candidates(c, part, phi);
+    if (eb == cudaSuccess) eb = launch_rb_select(c, part);
+    if (eb == cudaSuccess) eb = launch_apply(c, part, phi, bw);
+    if (eb == cudaSuccess) eb = launch_rb_post(c, bw, h, 1);
+    cudaGraph_t tmp = nullptr;
+    e = cudaStreamEndCapture(s_body, &tmp);
+    c->stream = s_main;
+    if (eb != cudaSuccess) return eb;
+    if (e != cudaSuccess) return e;
+    if ((e = launch_objective_masks(c)) != cudaSuccess) return e;
+    return launch_stats(c, bw, stats, 0);
+  }();
+  c->stream = saved;
+  return e;
 }
 
 int round_graph(jet_ctx *c, int32_t tn, int32_t td, int32_t *part, int32_t *phi, int64_t *bw, uint8_t *locked,
@@ -218,12 +239,7 @@ int round_graph(jet_ctx *c, int32_t tn, int32_t td, int32_t *part, int32_t *phi,
         g.locked == locked && g.stats == stats)
       G = &g;
   if (!G) {
-    if (!c->cap_stream[0]) {
-      CK(cudaStreamCreateWithFlags(&c->cap_stream[0], cudaStreamNonBlocking), "capture stream");
-      CK(cudaStreamCreateWithFlags(&c->cap_stream[1], cudaStreamNonBlocking), "capture stream");
-      CK(cudaEventCreate(&c->graph_ev[0]), "graph events");
-      CK(cudaEventCreate(&c->graph_ev[1]), "graph events");
-    }
+    CK(ensure_capture_streams(c), "capture streams");
     G = &c->graphs[c->graph_next];
     c->graph_next = (c->graph_next + 1) % jet_ctx::kGraphCache;
     if (G->exec) {
@@ -236,21 +252,17 @@ int round_graph(jet_ctx *c, int32_t tn, int32_t td, int32_t *part, int32_t *phi,
     }
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0), "graph");
-    cudaGraphConditionalHandle h;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
-    cudaStream_t user = c->stream;
-    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(c->cap_stream[0], g, nullptr, nullptr, 0,
-                                                            cudaStreamCaptureModeRelaxed);
+    cudaError_t e = cudaStreamBeginCaptureToGraph(c->cap_stream[0], g, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
       c->capturing = 1;
-      cudaError_t ec = capture_round(c, tn, td, part, phi, bw, locked, stats, h, c->graph_ev[0], c->graph_ev[1],
-                                     G->ev_nodes);
+      cudaError_t ec = capture_iteration(c, c->cap_stream[0], c->cap_stream[1], tn, td, part, phi, bw, locked, stats,
+                                         c->graph_ev[0], c->graph_ev[1]);
       c->capturing = 0;
       cudaGraph_t done = nullptr;
       e = cudaStreamEndCapture(c->cap_stream[0], &done);
       if (ec != cudaSuccess) e = ec;
     }
-    c->stream = user;
     G->ev_nodes[0] = G->ev_nodes[1] = nullptr;
     if (e == cudaSuccess) {  // the event-record nodes around the candidate kernels
       size_t nn = 0;
@@ -299,7 +311,7 @@ int round_graph(jet_ctx *c, int32_t tn, int32_t td, int32_t *part, int32_t *phi,
   return JET_OK;
 }
 
-}  // namespace
+}  // namespace jet
 
 void jet::set_global_error(const char *fmt, ...) {
   va_list ap;
@@ -349,6 +361,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) { rc = cuda_fail(c, e, "device query"); break; }
+    c->launch_sms = c->num_sms;
     if ((e = dalloc(c, &c->cnt, 1)) != cudaSuccess ||
         (e = cudaMallocHost(reinterpret_cast<void **>(&c->cnt_host), sizeof(Counters))) != cudaSuccess ||
         (e = dalloc(c, &wdeg, c->n)) != cudaSuccess || (e = dalloc(c, &degc, c->n)) != cudaSuccess ||
@@ -457,10 +470,11 @@ void jet_ctx_destroy(jet_ctx *c) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
   }
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i)
     if (c->cap_stream[i]) cudaStreamDestroy(c->cap_stream[i]);
+  for (int i = 0; i < 2; ++i)
     if (c->graph_ev[i]) cudaEventDestroy(c->graph_ev[i]);
-  }
+  destroy_refine_graph(c);
   if (c->prof_ev) {
     for (int i = 0; i < 2 * jet_ctx::kProfPairs; ++i) cudaEventDestroy(c->prof_ev[i]);
     delete[] c->prof_ev;
@@ -565,6 +579,7 @@ int jet_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limi
   if ((c->n > 0 && !part) || (c->m > 0 && !phi) || !block_w || !result)
     return fail(c, JET_ERR_INVALID_ARG, "part, phi, block_w or result is NULL");
   memset(result, 0, sizeof(*result));
+  if (c->use_graphs) return refine_graph(c, tau_pairs, n_tau, limit, part, phi, block_w, result);
   jet_round_stats *st = c->stats_host;
   auto read_stats = [&]() -> int {
     CK(cudaMemcpyAsync(st, c->stats_scratch, sizeof(jet_round_stats), cudaMemcpyDeviceToHost, c->stream), "stats");

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "jet.h"
 
 namespace jet {
@@ -74,6 +76,16 @@ struct RbBlock {
   int all;                       // selection: every record of b moves
 };
 
+// Device-side state of jet_refine's loop control (Algorithm 1).
+struct RefineState {
+  long long best;         // (lambda-1) of the best balanced partition so far
+  int have_best;          // a balanced partition has been seen
+  int snap;               // the last iteration improved: snapshot the partition
+  int it;                 // iterations since the last improvement (Algorithm 1's counter)
+  int in_phase;           // iterations of the current temperature
+  jet_refine_result res;  // the summary returned to the caller
+};
+
 constexpr int kRbDigitBits = 11;  // radix-select digit width
 constexpr int kRbBins = 1 << kRbDigitBits;
 
@@ -89,6 +101,7 @@ struct jet_ctx {
   int32_t k = 0, kwp = 0;
   cudaStream_t stream = nullptr;
   int num_sms = 0;
+  int launch_sms = 0;  // SMs the grids are sized for (num_sms, or a share of it inside a batch)
 
   // balance constants (Section 2, Section 4.3)
   int64_t W = 0, A = 0, Lmax = 0, dz_min = 0;
@@ -144,8 +157,19 @@ struct jet_ctx {
   int graph_next = 0;
   int use_graphs = 1;
   int capturing = 0;
-  cudaStream_t cap_stream[2] = {nullptr, nullptr};
+  cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t graph_ev[2] = {nullptr, nullptr};  // idle targets of the graphs' event-record nodes
+
+  // CUDA graph of jet_refine (Algorithm 1 on the device), one cached argument set
+  struct RefineGraph {
+    std::vector<int32_t> tau;
+    int32_t limit = 0;
+    const void *part = nullptr, *phi = nullptr, *bw = nullptr, *res = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  };
+  RefineGraph refine_graph;
+  jet::RefineState *rstate = nullptr;      // device: loop state and summary of jet_refine
+  jet_refine_result *res_host = nullptr;   // pinned copy of the summary
 
   // profiling: kernel launches (always counted) and event pairs per family
   long long kernel_launches = 0;
@@ -160,6 +184,24 @@ struct jet_ctx {
 };
 
 namespace jet {
+
+// ---- shared host helpers (jet_abi.cu) ----
+int fail(jet_ctx *c, int code, const char *fmt, ...);
+int cuda_fail(jet_ctx *c, cudaError_t e, const char *where);
+int sync_counters(jet_ctx *c);
+cudaError_t reset_counters(jet_ctx *c);
+int check_ctx(jet_ctx *c);
+int check_tau(jet_ctx *c, int32_t tau_num, int32_t tau_den);
+cudaError_t ensure_capture_streams(jet_ctx *c);
+cudaError_t capture_iteration(jet_ctx *c, cudaStream_t s_main, cudaStream_t s_body, int32_t tn, int32_t td,
+                              int32_t *part, int32_t *phi, int64_t *bw, uint8_t *locked, jet_round_stats *stats,
+                              cudaEvent_t ev0, cudaEvent_t ev1);
+// ---- device-side Algorithm 1 and batches (jet_graph.cu) ----
+int refine_graph(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *part, int32_t *phi,
+                 int64_t *block_w, jet_refine_result *result);
+cudaError_t capture_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *part,
+                           int32_t *phi, int64_t *block_w, jet_refine_result *result_dst);
+void destroy_refine_graph(jet_ctx *c);
 
 // ---- launchers (one per kernel family); all enqueue on ctx->stream ----
 // state kernels (k_state.cu)
@@ -187,7 +229,7 @@ cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part);
 cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond = 0,
                            int use_cond = 0);
 cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *stats, int rebalance_only);
-cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best);
+cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best, const int *enable = nullptr);
 
 // Block-wide append to a global list: every thread of the block calls it (same
 // iteration); each thread with `sel` gets a distinct slot.  One atomicAdd per

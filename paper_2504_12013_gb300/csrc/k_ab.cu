@@ -351,21 +351,21 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
   if (c->n_tiny > 0) {
     a.elist = c->e_tiny;
     a.nlist = c->n_tiny;
-    k_ab_tiny<<<grid_for(c->n_tiny, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    k_ab_tiny<<<grid_for(c->n_tiny, 256, c->launch_sms), 256, 0, c->stream>>>(a);
     ++c->kernel_launches;
   }
   if (c->n_mid > 0) {
     a.elist = c->e_mid;
     a.nlist = c->n_mid;
     const size_t smem = (size_t)kAbWarps * 2 * c->k * sizeof(unsigned long long);
-    k_ab_warp<<<grid_for((int64_t)c->n_mid * 32, kAbWarps * 32, c->num_sms), kAbWarps * 32, smem, c->stream>>>(a);
+    k_ab_warp<<<grid_for((int64_t)c->n_mid * 32, kAbWarps * 32, c->launch_sms), kAbWarps * 32, smem, c->stream>>>(a);
     ++c->kernel_launches;
   }
   if (c->n_big > 0) {
     a.elist = c->e_big;
     a.nlist = c->n_big;
     const size_t smem = (size_t)c->k * (2 * sizeof(unsigned long long) + sizeof(int));
-    k_ab_block<<<c->num_sms * 2, 512, smem, c->stream>>>(a);
+    k_ab_block<<<c->launch_sms * 2, 512, smem, c->stream>>>(a);
     ++c->kernel_launches;
   }
   return cudaGetLastError();
@@ -384,14 +384,14 @@ cudaError_t launch_approve(jet_ctx *c, uint8_t *locked, int32_t *rg_out, uint8_t
   a.mv_v = c->mv_v;
   a.mv_st = c->mv_st;
   a.cnt = c->cnt;
-  k_approve<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(a);
+  k_approve<<<grid_for(c->n, 256, c->launch_sms), 256, 0, c->stream>>>(a);
   ++c->kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_export_candidates(jet_ctx *c, int32_t *target, int32_t *gain, uint8_t *in_m) {
   if (c->n == 0) return cudaSuccess;
-  k_export_cand<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(c->cand, c->n, target, gain, in_m);
+  k_export_cand<<<grid_for(c->n, 256, c->launch_sms), 256, 0, c->stream>>>(c->cand, c->n, target, gain, in_m);
   ++c->kernel_launches;
   return cudaGetLastError();
 }

@@ -694,7 +694,7 @@ cudaError_t launch_cand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_light > 0) {
     a.vlist = c->v_light;
     a.nlist = c->n_light;
-    const int g = grid_for(c->n, 256, c->num_sms, c->stage_bps[0]);
+    const int g = grid_for(c->n, 256, c->launch_sms, c->stage_bps[0]);
     if (c->unit_ewgt) k_cand_light<KWP, true><<<g, 256, 8 * Stage<KWP>::template bytes<true>(), c->stream>>>(a);
     else k_cand_light<KWP, false><<<g, 256, 8 * Stage<KWP>::template bytes<false>(), c->stream>>>(a);
     ++c->kernel_launches;
@@ -702,7 +702,7 @@ cudaError_t launch_cand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_heavy > 0) {
     a.vlist = c->v_heavy;
     a.nlist = c->n_heavy;
-    k_cand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    k_cand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->launch_sms), 256, 0, c->stream>>>(a);
     ++c->kernel_launches;
   }
   return cudaGetLastError();
@@ -714,7 +714,7 @@ cudaError_t launch_rbcand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_light > 0) {
     a.vlist = c->v_light;
     a.nlist = c->n_light;
-    const int g = grid_for(c->n, 256, c->num_sms, c->stage_bps[1]);
+    const int g = grid_for(c->n, 256, c->launch_sms, c->stage_bps[1]);
     if (c->unit_ewgt) k_rbcand_light<KWP, true><<<g, 256, 8 * Stage<KWP>::template bytes<true>(), c->stream>>>(a);
     else k_rbcand_light<KWP, false><<<g, 256, 8 * Stage<KWP>::template bytes<false>(), c->stream>>>(a);
     ++c->kernel_launches;
@@ -722,7 +722,7 @@ cudaError_t launch_rbcand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_heavy > 0) {
     a.vlist = c->v_heavy;
     a.nlist = c->n_heavy;
-    k_rbcand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->num_sms), 256, 0, c->stream>>>(a);
+    k_rbcand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->launch_sms), 256, 0, c->stream>>>(a);
     ++c->kernel_launches;
   }
   return cudaGetLastError();

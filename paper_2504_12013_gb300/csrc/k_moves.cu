@@ -312,9 +312,11 @@ __global__ void k_stats(const int64_t *bw, int32_t k, long long Lmax, const Coun
 
 // Moves that take part back to best (rollback at the end of a phase).
 __global__ void __launch_bounds__(256) k_rollback_moves(const int32_t *part, const int32_t *best, int32_t n,
-                                                        int32_t *mv_v, uint32_t *mv_st, Counters *cnt) {
+                                                        int32_t *mv_v, uint32_t *mv_st, Counters *cnt,
+                                                        const int *enable) {
   __shared__ unsigned s_wc[8];
   __shared__ unsigned long long s_base;
+  if (enable && !*enable) return;  // uniform: no snapshot to roll back to
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t v = base + threadIdx.x;
     int s = 0, t = 0;
@@ -377,7 +379,7 @@ RbArgs rb_args(jet_ctx *c, const int64_t *block_w, const int32_t *part) {
 cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   if (c->n == 0) return cudaSuccess;
   const MoveArgs a = move_args(c, part, phi, block_w);
-  k_apply<<<grid_for((int64_t)c->n * kMoveLanes, 256, c->num_sms, 8), 256, 0, c->stream>>>(a);
+  k_apply<<<grid_for((int64_t)c->n * kMoveLanes, 256, c->launch_sms, 8), 256, 0, c->stream>>>(a);
   ++c->kernel_launches;
   return cudaGetLastError();
 }
@@ -396,7 +398,7 @@ cudaError_t launch_rb_prep(jet_ctx *c, const int64_t *block_w) {
 
 template <class KT>
 void rb_select_levels(jet_ctx *c, const RbArgs &a) {
-  const int g = grid_for(c->n, 256, c->num_sms);
+  const int g = grid_for(c->n, 256, c->launch_sms);
   int first = 1;
   for (int hi = a.tbits; hi > 0; first = 0) {
     const int lo = hi - kRbDigitBits > 0 ? hi - kRbDigitBits : 0;
@@ -430,11 +432,11 @@ cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *st
   return cudaGetLastError();
 }
 
-cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best) {
+cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best, const int *enable) {
   cudaError_t e = cudaMemsetAsync(&c->cnt->n_moves, 0, sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess || c->n == 0) return e;
-  k_rollback_moves<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(part, best, c->n, c->mv_v, c->mv_st,
-                                                                         c->cnt);
+  k_rollback_moves<<<grid_for(c->n, 256, c->launch_sms), 256, 0, c->stream>>>(part, best, c->n, c->mv_v, c->mv_st,
+                                                                         c->cnt, enable);
   ++c->kernel_launches;
   return cudaGetLastError();
 }

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) k_objective_masks(const uint32_t *mask, c
 cudaError_t launch_validate(jet_ctx *c, int64_t *wdeg_tmp, int32_t *degcount_tmp, unsigned long long *scal) {
   // phases 1..3; the caller synchronizes and checks cnt->err between phases
   cudaStream_t s = c->stream;
-  int g = grid_for((int64_t)c->m + c->n + 2, 256, c->num_sms);
+  int g = grid_for((int64_t)c->m + c->n + 2, 256, c->launch_sms);
   k_validate_offsets<<<g, 256, 0, s>>>(c->eptr, c->vptr, c->vwgt, c->ewgt, c->n, c->m, c->P, c->cnt);
   ++c->kernel_launches;
   cudaError_t e = cudaGetLastError();
@@ -277,7 +277,7 @@ cudaError_t launch_validate(jet_ctx *c, int64_t *wdeg_tmp, int32_t *degcount_tmp
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   if (c->cnt_host->err) return cudaSuccess;  // offsets unusable: stop before indexing with them
   if (c->P > 0) {
-    k_validate_ids<<<grid_for(c->P, 256, c->num_sms), 256, 0, s>>>(c->pins, c->inc, c->n, c->m, c->P, degcount_tmp,
+    k_validate_ids<<<grid_for(c->P, 256, c->launch_sms), 256, 0, s>>>(c->pins, c->inc, c->n, c->m, c->P, degcount_tmp,
                                                                     c->cnt);
     ++c->kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -287,7 +287,7 @@ cudaError_t launch_validate(jet_ctx *c, int64_t *wdeg_tmp, int32_t *degcount_tmp
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
   if (c->cnt_host->err) return cudaSuccess;
   if (c->n > 0) {
-    k_validate_degrees<<<grid_for(c->n, 256, c->num_sms), 256, 0, s>>>(c->vptr, c->inc, c->vwgt, c->ewgt, c->n,
+    k_validate_degrees<<<grid_for(c->n, 256, c->launch_sms), 256, 0, s>>>(c->vptr, c->inc, c->vwgt, c->ewgt, c->n,
                                                                         degcount_tmp, wdeg_tmp, scal, c->cnt);
     ++c->kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -348,7 +348,7 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
   if (e != cudaSuccess) return e;
   int32_t t[kClasses];
   if (c->n > 0) {
-    k_vertex_codes<<<grid_for(c->n, 256, c->num_sms), 256, 0, c->stream>>>(wdeg, c->n, c->vheavy);
+    k_vertex_codes<<<grid_for(c->n, 256, c->launch_sms), 256, 0, c->stream>>>(wdeg, c->n, c->vheavy);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = stable_partition(c, c->vheavy, c->n, c->v_light, t);
@@ -357,7 +357,7 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
     c->n_heavy = t[1];
     c->v_heavy = c->v_light + t[0];
     if (c->m > 0) {
-      k_edge_codes<<<grid_for(c->m, 256, c->num_sms), 256, 0, c->stream>>>(c->eptr, c->m, code);
+      k_edge_codes<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->eptr, c->m, code);
       e = cudaGetLastError();
     }
   }
@@ -382,13 +382,13 @@ cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int6
   if (c->m > 0) {
     const int threads = 256;
     size_t smem = (size_t)(threads / 32) * c->k * sizeof(int);
-    k_pincounts<<<grid_for((int64_t)c->m * 32, threads, c->num_sms), threads, smem, s>>>(
+    k_pincounts<<<grid_for((int64_t)c->m * 32, threads, c->launch_sms), threads, smem, s>>>(
         c->eptr, c->pins, part, c->m, c->k, c->kwp, phi, c->mask, c->cnt);
     ++c->kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (c->n > 0) {
-    k_block_weights<<<grid_for(c->n, 256, c->num_sms, 2), 256, 0, s>>>(part, c->vwgt, c->n, c->k, block_w,
+    k_block_weights<<<grid_for(c->n, 256, c->launch_sms, 2), 256, 0, s>>>(part, c->vwgt, c->n, c->k, block_w,
                                                                         c->vcount, c->cnt);
     ++c->kernel_launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -399,7 +399,7 @@ cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int6
 
 cudaError_t launch_masks_from_phi(jet_ctx *c, const int32_t *phi) {
   if (c->m > 0) {
-    k_masks_from_phi<<<grid_for((int64_t)c->m * 32, 256, c->num_sms), 256, 0, c->stream>>>(phi, c->m, c->k, c->kwp,
+    k_masks_from_phi<<<grid_for((int64_t)c->m * 32, 256, c->launch_sms), 256, 0, c->stream>>>(phi, c->m, c->k, c->kwp,
                                                                                             c->mask);
     ++c->kernel_launches;
     cudaError_t e = cudaGetLastError();
@@ -412,7 +412,7 @@ cudaError_t launch_masks_from_phi(jet_ctx *c, const int32_t *phi) {
 cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *out) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), c->stream);
   if (e != cudaSuccess || c->m == 0) return e;
-  k_connectivity_dense<<<grid_for((int64_t)c->m * 32, 256, c->num_sms), 256, 0, c->stream>>>(
+  k_connectivity_dense<<<grid_for((int64_t)c->m * 32, 256, c->launch_sms), 256, 0, c->stream>>>(
       phi, c->ewgt, c->m, c->k, reinterpret_cast<long long *>(out));
   ++c->kernel_launches;
   return cudaGetLastError();
@@ -421,7 +421,7 @@ cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *o
 cudaError_t launch_objective_masks(jet_ctx *c) {
   cudaError_t e = cudaMemsetAsync(&c->cnt->objective, 0, sizeof(long long), c->stream);
   if (e != cudaSuccess || c->m == 0) return e;
-  k_objective_masks<<<grid_for(c->m, 256, c->num_sms), 256, 0, c->stream>>>(c->mask, c->ewgt, c->m, c->kwp, c->cnt);
+  k_objective_masks<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->mask, c->ewgt, c->m, c->kwp, c->cnt);
   ++c->kernel_launches;
   return cudaGetLastError();
 }

@@ -24,7 +24,8 @@ ERRORS = {-1: "JET_ERR_INVALID_ARG", -2: "JET_ERR_OOM", -3: "JET_ERR_CUDA", -4: 
 EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pincounts", "jet_connectivity",
            "jet_refine_round", "jet_rebalance", "jet_refine", "jet_candidates", "jet_afterburner",
            "jet_refine_host", "jet_profile_enable", "jet_profile_read", "jet_block_weights_noalloc",
-           "jet_set_graph_mode")
+           "jet_set_graph_mode", "jet_batch_create", "jet_batch_destroy", "jet_batch_last_error",
+           "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -99,8 +100,18 @@ def load_library():
             lib.jet_profile_read.argtypes = [_P, pp(ctypes.c_double), pp(i64), pp(i64), ctypes.c_int]
             lib.jet_block_weights_noalloc.argtypes = [_P, _P, i32, i32, _P, _P, _P]
             lib.jet_set_graph_mode.argtypes = [_P, ctypes.c_int]
+            lib.jet_batch_create.argtypes = [pp(_P), pp(_P), i32, _P]
+            lib.jet_batch_destroy.argtypes = [_P]
+            lib.jet_batch_destroy.restype = None
+            lib.jet_batch_last_error.argtypes = [_P]
+            lib.jet_batch_last_error.restype = ctypes.c_char_p
+            lib.jet_batch_refine.argtypes = [_P, pp(i32), i32, i32, pp(_P), pp(_P), pp(_P), pp(JetRefineResult)]
+            lib.jet_batch_set_split.argtypes = [_P, i32]
+            lib.jet_batch_get_split.argtypes = [_P]
+            lib.jet_batch_tune.argtypes = [_P, pp(i32), i32, i32, pp(_P), pp(_P), pp(_P), pp(i32), i32,
+                                           pp(ctypes.c_float)]
             for f in EXPORTS:
-                if f not in ("jet_ctx_destroy", "jet_last_error"):
+                if f not in ("jet_ctx_destroy", "jet_last_error", "jet_batch_destroy", "jet_batch_last_error"):
                     getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -291,6 +302,81 @@ def jet_block_weights_noalloc(part, vwgt, k, block_w, block_count=None, stream=N
                                                     n, int(k), _ptr(block_w, torch.int64, "block_w"),
                                                     _ptr(block_count, torch.int32, "block_count"),
                                                     _stream_ptr(stream)))
+
+
+class Batch:
+    """Owning handle of a jet_batch; keeps its contexts alive."""
+
+    def __init__(self, handle, ctxs):
+        self.handle = handle
+        self.ctxs = list(ctxs)
+
+    def close(self):
+        if self.handle:
+            load_library().jet_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch_check(rc, batch):
+    if rc != JET_OK:
+        raise JetError(rc, load_library().jet_batch_last_error(batch.handle if batch else None).decode())
+
+
+def jet_batch_create(ctxs, stream=None) -> Batch:
+    lib = load_library()
+    out = _P()
+    arr = (_P * len(ctxs))(*[c.handle for c in ctxs])
+    _batch_check(lib.jet_batch_create(ctypes.byref(out), arr, len(ctxs), _stream_ptr(stream)), None)
+    return Batch(out, ctxs)
+
+
+def jet_batch_destroy(batch: Batch):
+    batch.close()
+
+
+def _state_arrays(states):
+    import torch
+    part = (_P * len(states))(*[_ptr(s.part, torch.int32, "part") for s in states])
+    phi = (_P * len(states))(*[_ptr(s.phi, torch.int32, "phi") for s in states])
+    bw = (_P * len(states))(*[_ptr(s.block_w, torch.int64, "block_w") for s in states])
+    return part, phi, bw
+
+
+def _pairs(schedule):
+    return (ctypes.c_int32 * max(2 * len(schedule), 1))(*[int(x) for t in schedule for x in t])
+
+
+def jet_batch_refine(batch: Batch, schedule, limit, states) -> list:
+    """Refine every instance (states[i]: a JetState of batch.ctxs[i]) with one graph launch."""
+    part, phi, bw = _state_arrays(states)
+    res = (JetRefineResult * len(states))()
+    _batch_check(load_library().jet_batch_refine(batch.handle, _pairs(schedule), len(schedule), int(limit), part, phi,
+                                                  bw, res), batch)
+    return [r.as_dict() for r in res]
+
+
+def jet_batch_set_split(batch: Batch, split: int):
+    _batch_check(load_library().jet_batch_set_split(batch.handle, int(split)), batch)
+
+
+def jet_batch_get_split(batch: Batch) -> int:
+    return int(load_library().jet_batch_get_split(batch.handle))
+
+
+def jet_batch_tune(batch: Batch, schedule, limit, states, splits) -> tuple:
+    """Time the batch under each split; keep the fastest.  Returns (chosen split, {split: ms})."""
+    part, phi, bw = _state_arrays(states)
+    sp = (ctypes.c_int32 * len(splits))(*[int(x) for x in splits])
+    ms = (ctypes.c_float * len(splits))()
+    _batch_check(load_library().jet_batch_tune(batch.handle, _pairs(schedule), len(schedule), int(limit), part, phi,
+                                               bw, sp, len(splits), ms), batch)
+    return jet_batch_get_split(batch), {int(s): float(t) for s, t in zip(splits, ms)}
 
 
 # ---------------------------------------------------------------- state helper

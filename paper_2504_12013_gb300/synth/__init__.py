@@ -245,3 +245,20 @@ def config_rownet_4m(seed: int = 1):
     """4,000,000 columns x 4,000,000 rows, log-normal(2,1) lengths + 200 hubs of 50k-200k pins, k=128."""
     h = rownet(seed, 4_000_000, 4_000_000)
     return h, 128, part_perm(seed, h.n, 128)
+
+
+def config_batched(seed: int = 1, count: int = 256, n_lo: int = 1_000, n_hi: int = 200_000):
+    """Independent instances of the batched workload: n log-uniform in [n_lo, n_hi], m = round(1.1 n),
+    |e| = 2 + Geometric(2/5) failures capped at 256, unit weights, k uniform from {2, 8, 32},
+    hash partition with the instance's seed.  Returns a list of (hypergraph, k, partition)."""
+    import math
+    u = stream_u64(seed * 1_000_003 + 17, 2 * count)
+    out = []
+    for i in range(count):
+        frac = float(u[2 * i] >> np.uint64(11)) / float(1 << 53)
+        n = int(round(math.exp(math.log(n_lo) + frac * (math.log(n_hi) - math.log(n_lo)))))
+        k = (2, 8, 32)[int(u[2 * i + 1] % np.uint64(3))]
+        s = seed * 100_003 + i
+        h = uniform(s, n, int(round(1.1 * n)), base=2, geo=(2, 5), size_cap=256)
+        out.append((h, k, part_hash(s, h.n, k)))
+    return out

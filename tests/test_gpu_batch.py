@@ -1,0 +1,116 @@
+"""Batched refinement (one graph launch for many instances) vs the oracle.
+
+Every instance of a batch must come out exactly as the oracle's Algorithm 1
+on that instance alone: same partition, objective, iteration counts, pin
+counts and block weights, whatever the work split.  The device-side
+refinement graph (jet_refine in graph mode) is checked the same way.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_12013_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2504_12013_gb300 import jet  # noqa: E402
+
+
+def _instances():
+    inst = synth.config_batched(seed=5, count=9, n_lo=300, n_hi=6_000)
+    h = synth.uniform(41, 3_000, 3_300, base=2, geo=(1, 2), size_cap=64, c_max=4, w_max=3)
+    inst.append((h, 11, synth.part_perm(41, h.n, 11)))
+    h = synth.uniform(42, 2_000, 2_200, base=2, geo=(1, 2), size_cap=64, w_max=40)  # heavy vertices
+    inst.append((h, 128, synth.part_perm(42, h.n, 128)))
+    h = synth.rownet(43, 6_000, 6_000, n_hubs=3, hub_min=2_100, hub_max=3_000)  # block-path edges
+    inst.append((h, 32, synth.part_random(43, h.n, 32)))
+    return inst
+
+
+INST = _instances()
+
+
+def _oracle(hg, k, part):
+    orc = oracle.Oracle(hg)
+    p = part.copy()
+    iters, obj, phase = orc.refine(oracle.Params(k), p)
+    phi, bw = orc.pincounts(k, p)
+    return iters, obj, [int(x) for x in phase], p, phi, bw
+
+
+EXPECTED = [_oracle(*x) for x in INST]
+
+
+def _check(i, res, st):
+    hg, k, _ = INST[i]
+    iters, obj, phase, p, phi, bw = EXPECTED[i]
+    assert res["iterations"] == iters and res["objective"] == obj, f"instance {i}"
+    assert res["phase_iterations"][:3] == phase, f"instance {i}"
+    assert np.array_equal(st.part.cpu().numpy()[: hg.n], p), f"instance {i}: partition"
+    assert np.array_equal(st.phi.cpu().numpy()[: hg.m * k].reshape(hg.m, k), phi), f"instance {i}: phi"
+    assert np.array_equal(st.block_w.cpu().numpy(), bw), f"instance {i}: block weights"
+
+
+def _contexts():
+    return [jet.jet_ctx_create(jet.DeviceHypergraph(h), jet.params(k)) for h, k, _ in INST]
+
+
+@pytest.mark.parametrize("split", [0, 1, 4])
+def test_batch_matches_oracle(split):
+    ctxs = _contexts()
+    states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST)]
+    b = jet.jet_batch_create(ctxs)
+    jet.jet_batch_set_split(b, split)
+    res = jet.jet_batch_refine(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states)
+    for i, (r, st) in enumerate(zip(res, states)):
+        _check(i, r, st)
+    # a second launch of the cached graph from fresh partitions gives the same
+    for st, (_, _, p) in zip(states, INST):
+        st.part.copy_(torch.as_tensor(p))
+    res2 = jet.jet_batch_refine(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states)
+    for i, (r, st) in enumerate(zip(res2, states)):
+        _check(i, r, st)
+    b.close()
+
+
+def test_batch_tune_restores_partitions_and_picks_a_split():
+    ctxs = _contexts()
+    states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST)]
+    b = jet.jet_batch_create(ctxs)
+    chosen, ms = jet.jet_batch_tune(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states, [0, 1, 2])
+    assert chosen in (0, 1, 2) and set(ms) == {0, 1, 2} and all(t > 0 for t in ms.values())
+    for st, (hg, _, p) in zip(states, INST):
+        assert np.array_equal(st.part.cpu().numpy()[: hg.n], p)
+    res = jet.jet_batch_refine(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states)
+    for i, (r, st) in enumerate(zip(res, states)):
+        _check(i, r, st)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_refine_graph_and_host_loop_match_oracle(graph):
+    for i in (0, 9, 10, 11):
+        hg, k, part = INST[i]
+        ctx = jet.jet_ctx_create(jet.DeviceHypergraph(hg), jet.params(k))
+        jet.jet_set_graph_mode(ctx, graph)
+        st = jet.JetState(ctx, part)
+        res = jet.jet_refine(ctx, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, st.part, st.phi, st.block_w)
+        _check(i, res, st)
+
+
+def test_batch_argument_errors():
+    c = jet.jet_ctx_create(jet.DeviceHypergraph(INST[0][0]), jet.params(INST[0][1]))
+    with pytest.raises(jet.JetError) as ei:
+        jet.jet_batch_create([c, c])
+    assert ei.value.code == -1
+    b = jet.jet_batch_create([c])
+    with pytest.raises(jet.JetError) as ei:
+        jet.jet_batch_set_split(b, -1)
+    assert ei.value.code == -1
+    st = jet.JetState(c, INST[0][2])
+    with pytest.raises(jet.JetError) as ei:
+        jet.jet_batch_refine(b, [(1, 1)], 8, [st])
+    assert ei.value.code == -1

@@ -165,10 +165,12 @@ def test_rebalance_from_random_partition(name):
     assert np.array_equal(host(st.block_w), ost.bw)
 
 
+@pytest.mark.parametrize("graph", [True, False], ids=["device_loop", "host_loop"])
 @pytest.mark.parametrize("name", ["random10k_k8", "weighted_k11", "geo04_k2", "heavy_k128", "rownet_k32",
                                   "empty_edges_k4", "bigc_k16"])
-def test_refine_to_convergence(name):
+def test_refine_to_convergence(name, graph):
     hg, k, part, ctx = setup(name)
+    jet.jet_set_graph_mode(ctx, graph)
     st = jet.JetState(ctx, part)
     res = jet.jet_refine(ctx, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, st.part, st.phi, st.block_w)
     orc = oracle.Oracle(hg)
