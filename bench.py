@@ -361,6 +361,80 @@ def run_batched(args, dev):
                       "k from {2, 8, 32}, unit weights, eps = 3/100, hash partitions"}
 
 
+def run_served(args, dev):
+    """The served form: refinement requests (P log-uniform in [10k, 5M], n = P / 3.85, m = 1.1 n,
+    |e| = 2 + Geometric(0.4) <= 256, c in 1..8, k from {2, 4, ..., 256}, balanced random partitions, each
+    refined to convergence) arrive as a Poisson stream at 200/s.  The server admits them by device-memory
+    footprint into up to `serve_slots` concurrent slots (continuous batching); the serial arm is the same
+    queue with one slot (the plain path, one job after another).  Latency = arrival to refined partition back
+    in host memory."""
+    import threading
+
+    import torch
+
+    from paper_2504_12013_gb300 import jet
+    insts, jobs = synth.served_jobs(args.seed, args.serve_jobs)
+    pinned = []
+    for h in insts:
+        arrs = {}
+        for name in ("eptr", "pins", "vptr", "inc", "vwgt", "ewgt"):
+            a = getattr(h, name)
+            t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True)
+            t.numpy()[:] = a
+            arrs[name] = t.numpy()
+        pinned.append(synth.Hypergraph(h.n, h.m, **arrs))
+    budget = int(args.serve_budget_gb * (1 << 30))
+    out = {}
+    finals = {}
+    for arm, slots in (("served", args.serve_slots), ("serial", 1)):
+        server = jet.jet_server_create(budget, slots)
+        warm = [np.ascontiguousarray(jobs[i][3].copy()) for i in range(min(4, len(jobs)))]
+        for i, w in enumerate(warm):
+            jet.jet_server_submit(server, pinned[jobs[i][1]], jet.params(jobs[i][2]), SCHEDULE, LIMIT, w)
+        got = 0
+        while got < len(warm):
+            got += len(jet.jet_server_wait(server))
+        parts = [np.ascontiguousarray(j[3].copy()) for j in jobs]
+        ids = {}
+        t0 = time.perf_counter()
+
+        def submit():
+            for idx, (arr_s, pi, k, _) in enumerate(jobs):
+                delay = t0 + arr_s - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                ids[jet.jet_server_submit(server, pinned[pi], jet.params(k), SCHEDULE, LIMIT, parts[idx])] = idx
+
+        th = threading.Thread(target=submit)
+        th.start()
+        done = []
+        while len(done) < len(jobs):
+            done += jet.jet_server_wait(server, timeout_ms=1000)
+        wall = time.perf_counter() - t0
+        th.join()
+        server.close()
+        bad = [d for d in done if d["status"] != 0]
+        if bad:
+            raise RuntimeError(f"served job failed: {bad[0]}")
+        lat = sorted(d["latency_ms"] for d in done)
+        pr = sum(insts[jobs[ids[d["id"]]][1]].P * d["result"]["iterations"] for d in done)
+        out[arm] = {"slots": slots, "jobs": len(done), "seconds": wall, "jobs_per_s": len(done) / wall,
+                    "pin_rounds_per_s": pr / wall,
+                    "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, (99 * len(lat)) // 100)],
+                    "queue_ms_mean": sum(d["queue_ms"] for d in done) / len(done)}
+        finals[arm] = parts
+        torch.cuda.synchronize(dev)
+    same = all(np.array_equal(a, b) for a, b in zip(finals["served"], finals["serial"]))
+    return {"metric": "served refinement: throughput and p50/p99 latency, continuous batching vs serial queue",
+            "served": out["served"], "serial": out["serial"],
+            "p99_speedup": out["serial"]["latency_ms_p99"] / out["served"]["latency_ms_p99"],
+            "throughput_speedup": out["served"]["jobs_per_s"] / out["serial"]["jobs_per_s"],
+            "results_identical_alone_and_in_mix": bool(same),
+            "config": f"{len(jobs)} jobs, Poisson arrivals at 200/s, P log-uniform [10k, 5M] over a pool of "
+                      f"{len(insts)} seeded instances, k from {{2..256}} (powers of two), c in 1..8, balanced "
+                      f"random partitions, memory budget {args.serve_budget_gb} GB"}
+
+
 def cpu_baseline(hg, k, part0, budget_s):
     """The oracle as it stands (single thread), rounds at tau = 3/4 from the same start until budget_s."""
     import oracle
@@ -392,6 +466,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=48.0)
+    ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="time the kernel-by-kernel form instead of the CUDA graphs (same work and results; "
                          "ncu cannot profile kernels inside graphs with conditional nodes)")
@@ -417,6 +495,7 @@ def main():
         return
     e2e = None if args.no_e2e else run_e2e(args, hg, k, r["part0"], r["dev"])
     batched = None if args.no_batched else run_batched(args, r["dev"])
+    served = None if args.no_served else run_served(args, r["dev"])
     cpu = None if args.no_cpu_baseline else cpu_baseline(hg, k, r["part0"], args.cpu_budget)
 
     import json as _j
@@ -472,6 +551,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "batched": batched,
+        "served": served,
         "trace_first_steps": r["trace"][:3],
     }
     print(json.dumps(line), flush=True)

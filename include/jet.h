@@ -25,6 +25,7 @@
 #ifndef JET_H
 #define JET_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -237,6 +238,54 @@ int jet_batch_get_split(const jet_batch *batch);
 int jet_batch_tune(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
                    int32_t *const *phi, int64_t *const *block_w, const int32_t *splits, int32_t n_splits,
                    float *ms_out);
+
+/*
+ * Serving: a request loop that refines submitted jobs (each = jet_refine_host
+ * on the job's host buffers: upload, Algorithm 1 as one graph, download) with
+ * up to max_active jobs on the device at once, each on its own stream and
+ * worker thread.  Jobs are admitted in submission order while a slot is free
+ * and the sum of the admitted jobs' device footprints (jet_job_footprint)
+ * stays within hbm_budget bytes, so a job that arrives while others run
+ * starts as soon as a slot and enough memory are free, and its kernels
+ * overlap with theirs.  A job's result is the same as running it alone.
+ *
+ * jet_server_submit copies the job description (not the arrays): hg_host's
+ * arrays and part_host (HOST, n; refined in place) must stay valid and
+ * untouched until jet_server_wait reports the job.  Errors:
+ * JET_ERR_INVALID_ARG (bad arguments), JET_ERR_OOM (the footprint exceeds
+ * the whole budget).  *id_out gets the job id (1, 2, ...).
+ *
+ * jet_server_wait moves up to max_done finished jobs into done (HOST) and
+ * sets *n_done; it blocks until at least one job is done or timeout_ms
+ * passes (0: no wait, < 0: no limit).  A job's own failure is in its status.
+ * latency_ms runs from submission to the partition being back in host
+ * memory; queue_ms from submission to admission.
+ *
+ * jet_server_load reports the jobs waiting for admission, the jobs admitted
+ * or running, and the reserved bytes.  jet_server_destroy waits for every
+ * submitted job, then stops the workers; reports not yet collected are
+ * dropped.  The paper has no serving loop; this is the project's runtime
+ * around the refinement.
+ */
+typedef struct jet_server jet_server;
+
+typedef struct {
+  int64_t id;
+  int32_t status;            /* JET_OK or the job's error code       */
+  int32_t reserved;
+  double latency_ms;         /* submission -> result in host memory   */
+  double queue_ms;           /* submission -> admission               */
+  jet_refine_result result;  /* summary of the job's refinement       */
+} jet_job_done;
+
+size_t jet_job_footprint(int32_t n, int32_t m, int64_t P, int32_t k);
+int jet_server_create(jet_server **out, size_t hbm_budget, int32_t max_active);
+int jet_server_submit(jet_server *server, const jet_hypergraph *hg_host, const jet_params *params,
+                      const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *part_host, int64_t *id_out);
+int jet_server_wait(jet_server *server, jet_job_done *done, int32_t max_done, int32_t *n_done, int32_t timeout_ms);
+int jet_server_load(jet_server *server, int32_t *pending, int32_t *running, size_t *reserved_bytes);
+const char *jet_server_last_error(const jet_server *server);
+void jet_server_destroy(jet_server *server);
 
 /*
  * The candidate step of jet_refine_round alone (Section 4.1), for

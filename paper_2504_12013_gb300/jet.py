@@ -25,7 +25,9 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_refine_round", "jet_rebalance", "jet_refine", "jet_candidates", "jet_afterburner",
            "jet_refine_host", "jet_profile_enable", "jet_profile_read", "jet_block_weights_noalloc",
            "jet_set_graph_mode", "jet_batch_create", "jet_batch_destroy", "jet_batch_last_error",
-           "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune")
+           "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune",
+           "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
+           "jet_server_last_error", "jet_server_destroy")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -60,6 +62,11 @@ class JetRefineResult(ctypes.Structure):
         return {"iterations": self.iterations, "objective": self.objective,
                 "initial_objective": self.initial_objective, "balanced": self.balanced,
                 "phase_iterations": list(self.phase_iterations)}
+
+
+class JetJobDone(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("result", JetRefineResult)]
 
 
 class JetError(RuntimeError):
@@ -110,8 +117,20 @@ def load_library():
             lib.jet_batch_get_split.argtypes = [_P]
             lib.jet_batch_tune.argtypes = [_P, pp(i32), i32, i32, pp(_P), pp(_P), pp(_P), pp(i32), i32,
                                            pp(ctypes.c_float)]
+            sz = ctypes.c_size_t
+            lib.jet_job_footprint.argtypes = [i32, i32, i64, i32]
+            lib.jet_job_footprint.restype = sz
+            lib.jet_server_create.argtypes = [pp(_P), sz, i32]
+            lib.jet_server_submit.argtypes = [_P, pp(JetHypergraph), pp(JetParams), pp(i32), i32, i32, _P, pp(i64)]
+            lib.jet_server_wait.argtypes = [_P, pp(JetJobDone), i32, pp(i32), i32]
+            lib.jet_server_load.argtypes = [_P, pp(i32), pp(i32), pp(sz)]
+            lib.jet_server_last_error.argtypes = [_P]
+            lib.jet_server_last_error.restype = ctypes.c_char_p
+            lib.jet_server_destroy.argtypes = [_P]
+            lib.jet_server_destroy.restype = None
             for f in EXPORTS:
-                if f not in ("jet_ctx_destroy", "jet_last_error", "jet_batch_destroy", "jet_batch_last_error"):
+                if f not in ("jet_ctx_destroy", "jet_last_error", "jet_batch_destroy", "jet_batch_last_error",
+                             "jet_job_footprint", "jet_server_last_error", "jet_server_destroy"):
                     getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -377,6 +396,81 @@ def jet_batch_tune(batch: Batch, schedule, limit, states, splits) -> tuple:
     _batch_check(load_library().jet_batch_tune(batch.handle, _pairs(schedule), len(schedule), int(limit), part, phi,
                                                bw, sp, len(splits), ms), batch)
     return jet_batch_get_split(batch), {int(s): float(t) for s, t in zip(splits, ms)}
+
+
+def jet_job_footprint(n, m, P, k) -> int:
+    return int(load_library().jet_job_footprint(int(n), int(m), int(P), int(k)))
+
+
+class Server:
+    """Owning handle of a jet_server.  Keeps every submitted job's host arrays alive until it is reported."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.keep = {}
+
+    def close(self):
+        if self.handle:
+            load_library().jet_server_destroy(self.handle)
+            self.handle = None
+            self.keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _server_check(rc, server):
+    if rc != JET_OK:
+        raise JetError(rc, load_library().jet_server_last_error(server.handle if server else None).decode())
+
+
+def jet_server_create(hbm_budget: int, max_active: int) -> Server:
+    out = _P()
+    _server_check(load_library().jet_server_create(ctypes.byref(out), int(hbm_budget), int(max_active)), None)
+    return Server(out)
+
+
+def jet_server_destroy(server: Server):
+    server.close()
+
+
+def jet_server_submit(server: Server, hg, p: JetParams, schedule, limit, part: np.ndarray) -> int:
+    """Submit a job on host arrays (hg: synth.Hypergraph; part: int32[n], refined in place)."""
+    if part.dtype != np.int32 or not part.flags["C_CONTIGUOUS"] or part.shape[0] != hg.n:
+        raise ValueError("part must be a contiguous int32 array of n entries")
+    arrs = [np.ascontiguousarray(a) for a in (hg.eptr, hg.pins, hg.vptr, hg.inc, hg.vwgt, hg.ewgt)]
+    hh = JetHypergraph(hg.n, hg.m, hg.P, *[a.ctypes.data for a in arrs])
+    pairs = (ctypes.c_int32 * max(2 * len(schedule), 1))(*[int(x) for t in schedule for x in t])
+    jid = ctypes.c_int64()
+    _server_check(load_library().jet_server_submit(server.handle, ctypes.byref(hh), ctypes.byref(p), pairs,
+                                                   len(schedule), int(limit), part.ctypes.data, ctypes.byref(jid)),
+                  server)
+    server.keep[jid.value] = (arrs, part, hh, pairs)
+    return jid.value
+
+
+def jet_server_wait(server: Server, max_done: int = 64, timeout_ms: int = -1) -> list:
+    """Finished jobs as dicts (id, status, latency_ms, queue_ms, result)."""
+    buf = (JetJobDone * max_done)()
+    nd = ctypes.c_int32()
+    _server_check(load_library().jet_server_wait(server.handle, buf, max_done, ctypes.byref(nd), int(timeout_ms)),
+                  server)
+    out = []
+    for d in buf[: nd.value]:
+        server.keep.pop(d.id, None)
+        out.append({"id": d.id, "status": d.status, "latency_ms": d.latency_ms, "queue_ms": d.queue_ms,
+                    "result": d.result.as_dict()})
+    return out
+
+
+def jet_server_load(server: Server) -> dict:
+    pend, run, res = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    _server_check(load_library().jet_server_load(server.handle, ctypes.byref(pend), ctypes.byref(run),
+                                                 ctypes.byref(res)), server)
+    return {"pending": pend.value, "running": run.value, "reserved_bytes": res.value}
 
 
 # ---------------------------------------------------------------- state helper

@@ -262,3 +262,32 @@ def config_batched(seed: int = 1, count: int = 256, n_lo: int = 1_000, n_hi: int
         h = uniform(s, n, int(round(1.1 * n)), base=2, geo=(2, 5), size_cap=256)
         out.append((h, k, part_hash(s, h.n, k)))
     return out
+
+
+def served_instance(seed: int, P_lo: int = 10_000, P_hi: int = 5_000_000):
+    """One request of the served workload: pins P log-uniform in [P_lo, P_hi], n = round(P / 3.85),
+    m = round(1.1 n), |e| = 2 + Geometric(2/5) failures capped at 256, c in 1..8, unit edge weights."""
+    import math
+    u = stream_u64(seed * 7_919 + 3, 1)
+    frac = float(u[0] >> np.uint64(11)) / float(1 << 53)
+    P = math.exp(math.log(P_lo) + frac * (math.log(P_hi) - math.log(P_lo)))
+    n = max(int(round(P / 3.85)), 2)
+    return uniform(seed, n, int(round(1.1 * n)), base=2, geo=(2, 5), size_cap=256, c_max=8)
+
+
+def served_jobs(seed: int, count: int, rate_per_s: float = 200.0, pool: int = 32):
+    """The request stream of the served workload: Poisson arrivals (seeded exponential gaps) at rate_per_s;
+    job j refines instance j % pool of a pool of `pool` served_instance hypergraphs, with k from
+    {2, 4, ..., 256} and a balanced random partition (seeded permutation).  Returns (pool instances,
+    [(arrival_s, pool index, k, partition)])."""
+    import math
+    insts = [served_instance(seed * 1_000 + i) for i in range(pool)]
+    u = stream_u64(seed * 104_729 + 11, 2 * count)
+    t, jobs = 0.0, []
+    for j in range(count):
+        frac = (float(u[2 * j] >> np.uint64(11)) + 0.5) / float(1 << 53)
+        t += -math.log(frac) / rate_per_s
+        k = 2 << int(u[2 * j + 1] % np.uint64(8))
+        h = insts[j % pool]
+        jobs.append((t, j % pool, k, part_perm(seed * 31 + j, h.n, k)))
+    return insts, jobs
