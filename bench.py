@@ -117,7 +117,7 @@ def kernel_bytes(hg, k, deg, st_before, round_stats):
     kw = (k + 31) // 32
     unlocked = ~st_before
     Pu = int(deg[unlocked].sum())
-    b = 8 * (n + 1) + 4 * n + n + 4 * int(unlocked.sum())  # vptr, vertex list, locks, own block
+    b = 8 * (n + 1) + 4 * n + n + n                         # vptr, partition, heavy flags, locks
     b += 4 * Pu                                              # incidences of unlocked vertices
     b += min(4 * Pu, 4 * m)                                  # omega(e) gathers
     b += min(8 * kw * Pu, 8 * kw * m)                        # bitmask rows (phi >= 1, phi >= 2) gathers
