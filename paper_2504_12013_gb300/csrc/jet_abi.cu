@@ -1,6 +1,7 @@
 // C ABI of libjet: argument checks, context and workspace, and the host-side
 // order of the kernels of one Jet iteration (Algorithm 1) and of the
 // temperature schedule (Section 7.2).
+#include <algorithm>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
@@ -421,6 +422,13 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
       int vb = 1;
       while (vb < 31 && (1ll << vb) < (long long)c->n) ++vb;  // vertex ids need vb bits
       c->rb_vbits = vb;
+      // fewest levels of <= 16 bits, but histograms (k rows of 2^digit) no larger than max(4n, 2048k) bins
+      const int tb = c->rb_hbits + c->rb_vbits;
+      int levels = (tb + kRbMaxDigit - 1) / kRbMaxDigit;
+      int digit = (tb + levels - 1) / levels;
+      const long long cap = std::max(4ll * c->n, 2048ll * c->k);
+      while (digit > 11 && ((long long)c->k << digit) > cap) digit = (tb + ++levels - 1) / levels;
+      c->rb_digit = digit;
     }
     // class lists, workspace
     if ((e = dalloc(c, &c->v_light, c->n)) != cudaSuccess || (e = dalloc(c, &c->e_tiny, (size_t)c->m)) != cudaSuccess ||
@@ -429,7 +437,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
         (e = dalloc(c, &c->mv_st, c->n)) != cudaSuccess || (e = dalloc(c, &c->vcount, c->k)) != cudaSuccess ||
         (e = dalloc(c, &c->rbb, c->k)) != cudaSuccess || (e = dalloc(c, &c->rb_hi, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_v, c->n)) != cudaSuccess ||
-        (e = dalloc(c, &c->rb_hist, (size_t)c->k * kRbBins)) != cudaSuccess ||
+        (e = dalloc(c, &c->rb_hist, (size_t)c->k << c->rb_digit)) != cudaSuccess ||
         (e = dalloc(c, &c->rb_ct, c->n)) != cudaSuccess || (e = dalloc(c, &c->best_part, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->locked_ws, c->n)) != cudaSuccess || (e = dalloc(c, &c->vheavy, c->n)) != cudaSuccess ||
         (e = dalloc(c, &c->stats_scratch, 1)) != cudaSuccess ||
@@ -440,7 +448,8 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     if ((e = cudaMemsetAsync(c->rg, 0, sizeof(int32_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->cand, 0, sizeof(uint64_t) * (c->n > 0 ? c->n : 1), c->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->rb_hist, 0, sizeof(unsigned long long) * c->k * kRbBins, c->stream)) != cudaSuccess) {
+        (e = cudaMemsetAsync(c->rb_hist, 0, sizeof(unsigned long long) * ((size_t)c->k << c->rb_digit), c->stream)) !=
+            cudaSuccess) {
       rc = cuda_fail(c, e, "workspace init");
       break;
     }

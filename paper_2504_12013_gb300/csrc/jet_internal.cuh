@@ -86,8 +86,7 @@ struct RefineState {
   jet_refine_result res;  // the summary returned to the caller
 };
 
-constexpr int kRbDigitBits = 11;  // radix-select digit width
-constexpr int kRbBins = 1 << kRbDigitBits;
+constexpr int kRbMaxDigit = 16;  // widest radix-select digit (bins per block row <= 65536)
 
 }  // namespace jet
 
@@ -134,8 +133,9 @@ struct jet_ctx {
   uint64_t *rb_hi = nullptr;          // per record: priority part of the rebalancing key
   int32_t *rb_v = nullptr;            // per record: vertex
   int32_t *rb_ct = nullptr;           // per record: c(v) << 16 | block << 8 | target
-  unsigned long long *rb_hist = nullptr;  // k x kRbBins weighted digit histograms (zero between uses)
+  unsigned long long *rb_hist = nullptr;  // k x 2^rb_digit weighted digit histograms (zero between uses)
   int rb_hbits = 0, rb_vbits = 1;     // key = rb_hi << rb_vbits | v, rb_hbits + rb_vbits significant bits
+  int rb_digit = 1;                   // radix-select digit width: the key in as few levels of <= 16 bits
   int32_t *best_part = nullptr;       // best balanced partition of jet_refine
   uint8_t *locked_ws = nullptr;       // locks of jet_refine
   jet_round_stats *stats_scratch = nullptr;

@@ -119,7 +119,7 @@ size_t jet_job_footprint(int32_t n, int32_t m, int64_t P, int32_t k) {
   b += 8 * M * kwp;                                               // edge bitmasks
   b += N * (8 + 4 + 4 + 4 + 8 + 4 + 4 + 4 + 1 + 1 + 4) + 4 * M;   // per-vertex workspace, class lists
   b += 16 * N + 4 * M;                                            // set-up temporaries of the context
-  b += 24 * K + 16 * K * 2048 + 4096;                             // per-block state, histograms, counters
+  b += 64 * K + 4096 + 8 * std::max((size_t)4 * N, 2048 * K);      // per-block state, counters, histograms
   return b + b / 16;                                              // allocator rounding
 }
 

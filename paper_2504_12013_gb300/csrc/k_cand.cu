@@ -41,6 +41,8 @@ struct CandArgs {
   Counters *cnt;
   int rb_compact;
   long long rb_L, rb_Pmax;
+  unsigned long long *rb_hist;  // first-level histogram of the rebalancing selection
+  int rb_vbits, rb_tbits, rb_digit;
 };
 
 // One edge's mask row: KWP words of Lambda(e) then KWP words of the blocks
@@ -253,6 +255,29 @@ __device__ __forceinline__ uint64_t rb_hi_of(const CandArgs &a, int32_t g, int32
     return (uint64_t)(a.rb_Pmax - P);
   }
   return rb_order_key(g, c);
+}
+
+// Top digit of the selection key K(v) = hi << vbits | v (the first radix
+// level), added with c(v) into the (block, digit) histogram: one atomic per
+// distinct (block, digit) in the warp.  Every lane of the warp calls it.
+__device__ __forceinline__ void rb_first_level(const CandArgs &a, bool rec, int s, uint64_t hi, int v, int32_t c) {
+  const int lane = threadIdx.x & 31;
+  const int lo = a.rb_tbits - a.rb_digit > 0 ? a.rb_tbits - a.rb_digit : 0;
+  int d = 0;
+  if (rec) {
+    if (a.rb_tbits <= 64) {
+      const uint64_t K = (hi << a.rb_vbits) | (uint32_t)v;
+      d = (int)((K >> lo) & ((1ull << (a.rb_tbits - lo)) - 1));
+    } else {
+      const unsigned __int128 K = ((unsigned __int128)hi << a.rb_vbits) | (uint32_t)v;
+      d = (int)((K >> lo) & ((1ull << (a.rb_tbits - lo)) - 1));
+    }
+  }
+  const int code = rec ? (s << 16) | d : -1 - lane;
+  const unsigned grp = __match_any_sync(kFull, code);
+  const unsigned sum = __reduce_add_sync(grp, rec ? (unsigned)c : 0u);
+  if (rec && lane == __ffs(grp) - 1)
+    atomicAdd(&a.rb_hist[((int64_t)s << a.rb_digit) + d], (unsigned long long)sum);
 }
 
 template <int KWP>
@@ -559,6 +584,7 @@ __device__ __forceinline__ void rb_batch(const CandArgs &a, uint8_t *stage, cons
     hi = rb_hi_of(a, conn - A, c);
     ct = (c << 16) | (s << 8) | t;
   }
+  rb_first_level(a, mine, s, hi, v, c);
   const unsigned bal = __ballot_sync(kFull, mine);
   unsigned long long pos0 = 0;
   if (lane == 0) pos0 = atomicAdd(&a.cnt->n_rec, (unsigned long long)__popc(bal));
@@ -679,9 +705,11 @@ __global__ void __launch_bounds__(256) k_rbcand_heavy(CandArgs a) {
       if (b < a.k && s_cap[b] >= c && (bb < 0 || conn[q] > bc)) { bb = b; bc = conn[q]; }
     }
     warp_argmax(bc, bb);
+    const uint64_t hi = rb_hi_of(a, bc - A, c);
+    rb_first_level(a, lane == 0, s, hi, v, c);
     if (lane == 0) {
       const unsigned long long pos = atomicAdd(&a.cnt->n_rec, 1ull);
-      a.rb_hi[pos] = rb_hi_of(a, bc - A, c);
+      a.rb_hi[pos] = hi;
       a.rb_v[pos] = v;
       a.rb_ct[pos] = (c << 16) | (s << 8) | bb;
     }
@@ -750,6 +778,10 @@ CandArgs make_args(jet_ctx *c, const int32_t *part, const int32_t *phi) {
   a.rb_compact = c->rb_compact;
   a.rb_L = c->rb_L;
   a.rb_Pmax = c->rb_Pmax;
+  a.rb_hist = c->rb_hist;
+  a.rb_vbits = c->rb_vbits;
+  a.rb_tbits = c->rb_hbits + c->rb_vbits;
+  a.rb_digit = c->rb_digit;
   return a;
 }
 

@@ -87,12 +87,15 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 // block with a valid target has a record with the key
 // K(v) = hi(v) << vb | v  (priority descending, then id ascending, as one
 // ascending number of hb + vb bits; 64-bit when it fits, else 128-bit).
-// Per level (kRbDigitBits bits, from the top) one grid-wide kernel adds c(v)
-// of every record that matches its block's fixed prefix into the (block,
-// digit) histogram, and one small kernel per overloaded block picks the
-// digit at which the cumulative weight reaches the excess.  After the last
-// level the prefix is the threshold key, and every record up to it moves.
+// Per level (rb_digit <= 16 bits, from the top; two levels cover keys of up
+// to 32 bits) a grid-wide pass adds c(v) of every record that matches its
+// block's fixed prefix into the (block, digit) histogram -- for the first
+// level the target kernels do this while they write the records -- and one
+// small kernel per overloaded block picks the digit at which the cumulative
+// weight reaches the excess.  After the last level the prefix is the
+// threshold key, and every record up to it moves.
 typedef unsigned __int128 u128;
+constexpr int kPickThreads = 1024;
 
 struct RbArgs {
   const int64_t *bw;
@@ -104,6 +107,7 @@ struct RbArgs {
   uint32_t *mv_st;
   int32_t n, k;
   int vbits, tbits;
+  int digit, bins;               // radix-select digit width and bins per block row
   long long Lmax, dz_min;
   int32_t max_rounds;
   Counters *cnt;
@@ -180,67 +184,72 @@ __global__ void __launch_bounds__(256) k_rb_level(RbArgs a, int lo, int w) {
         c = (unsigned)(ct >> 16);
       }
     }
-    const int code = m ? (b << kRbDigitBits) | d : -1 - lane;
+    const int code = m ? (b << 16) | d : -1 - lane;
     const unsigned grp = __match_any_sync(kFull, code);
     const unsigned sum = __reduce_add_sync(grp, c);
-    if (m && lane == __ffs(grp) - 1) atomicAdd(&a.hist[(int64_t)b * kRbBins + d], (unsigned long long)sum);
+    if (m && lane == __ffs(grp) - 1) atomicAdd(&a.hist[(int64_t)b * a.bins + d], (unsigned long long)sum);
   }
 }
 
 // Per overloaded block: the digit at which the cumulative weight first reaches
 // the excess; at the first level a total below the excess selects everything.
+// Warp w owns a contiguous segment of bins and reads it 32 bins at a time
+// (coalesced); the warp whose segment holds the threshold walks it again.
 // Leaves the histogram row zeroed.
-__global__ void __launch_bounds__(256) k_rb_pick(RbArgs a, int lo, int first) {
+__global__ void __launch_bounds__(kPickThreads) k_rb_pick(RbArgs a, int lo, int first) {
+  constexpr int kWarps = kPickThreads / 32;
   const int b = blockIdx.x;
   RbBlock *r = &a.rbb[b];
   if (!r->over || r->all) return;
-  constexpr int kPer = kRbBins / 256;
-  unsigned long long *row = a.hist + (int64_t)b * kRbBins;
-  __shared__ long long s_warp[8];
-  __shared__ long long s_total;
+  __shared__ long long s_warp[kWarps];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  long long loc[kPer];
-  long long sum = 0;
+  const int seg = (a.bins + kWarps - 1) / kWarps;
+  const int x0 = wid * seg < a.bins ? wid * seg : a.bins;
+  const int x1 = x0 + seg < a.bins ? x0 + seg : a.bins;
+  unsigned long long *row = a.hist + (int64_t)b * a.bins;
+  long long part = 0;
+#pragma unroll 8
+  for (int x = x0 + lane; x < x1; x += 32) part += (long long)row[x];
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) {
-    loc[q] = (long long)row[threadIdx.x * kPer + q];
-    sum += loc[q];
-  }
-  long long incl = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const long long y = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) s_warp[wid] = incl;
-  __syncthreads();
-  long long wbase = 0;
-  for (int i = 0; i < wid; ++i) wbase += s_warp[i];
-  if (threadIdx.x == 0) {
-    long long t = 0;
-    for (int i = 0; i < 8; ++i) t += s_warp[i];
-    s_total = t;
-  }
-  const long long excl = wbase + incl - sum;
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+  if (lane == 0) s_warp[wid] = part;
+  // read before the barrier: the threshold warp rewrites r->before below
   const long long before = r->before, need = r->excess;
   __syncthreads();
-  if (first && s_total < need) {
-    if (threadIdx.x == 0) r->all = 1;
-  } else if (before + excl < need && before + excl + sum >= need) {
-    long long run = before + excl;
-    int d = threadIdx.x * kPer;
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      if (run + loc[q] >= need) { d = threadIdx.x * kPer + q; break; }
-      run += loc[q];
-    }
-    r->before = run;
-    const u128 pre = (((u128)r->pre_hi << 64) | r->pre_lo) | ((u128)(unsigned)d << lo);
-    r->pre_hi = (unsigned long long)(pre >> 64);
-    r->pre_lo = (unsigned long long)pre;
+  long long excl = 0, total = 0;
+  for (int i = 0; i < kWarps; ++i) {
+    if (i < wid) excl += s_warp[i];
+    total += s_warp[i];
   }
+  if (first && total < need) {
+    if (threadIdx.x == 0) r->all = 1;
+  } else if (before + excl < need && before + excl + part >= need) {  // warp-uniform
+    long long run = before + excl;
+    for (int x = x0; x < x1; x += 32) {
+      const long long w = x + lane < x1 ? (long long)row[x + lane] : 0;
+      long long incl = w;
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) row[threadIdx.x * kPer + q] = 0ull;
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned hit = __ballot_sync(kFull, run + incl >= need);
+      if (hit) {
+        const int l = __ffs(hit) - 1;
+        const long long prev = __shfl_sync(kFull, incl - w, l);
+        if (lane == 0) {
+          r->before = run + prev;
+          const u128 pre = (((u128)r->pre_hi << 64) | r->pre_lo) | ((u128)(unsigned)(x + l) << lo);
+          r->pre_hi = (unsigned long long)(pre >> 64);
+          r->pre_lo = (unsigned long long)pre;
+        }
+        break;
+      }
+      run += __shfl_sync(kFull, incl, 31);
+    }
+  }
+  __syncthreads();  // the threshold walk above reads the row
+  for (int x = x0 + lane; x < x1; x += 32) row[x] = 0ull;
 }
 
 // Every record with K(v) <= its block's threshold (or of an `all` block) moves.
@@ -367,6 +376,8 @@ RbArgs rb_args(jet_ctx *c, const int64_t *block_w, const int32_t *part) {
   a.k = c->k;
   a.vbits = c->rb_vbits;
   a.tbits = c->rb_hbits + c->rb_vbits;
+  a.digit = c->rb_digit;
+  a.bins = 1 << c->rb_digit;
   a.Lmax = c->Lmax;
   a.dz_min = c->dz_min;
   a.max_rounds = c->params.max_rebalance_rounds;
@@ -401,10 +412,12 @@ void rb_select_levels(jet_ctx *c, const RbArgs &a) {
   const int g = grid_for(c->n, 256, c->launch_sms);
   int first = 1;
   for (int hi = a.tbits; hi > 0; first = 0) {
-    const int lo = hi - kRbDigitBits > 0 ? hi - kRbDigitBits : 0;
-    k_rb_level<KT><<<g, 256, 0, c->stream>>>(a, lo, hi - lo);
-    ++c->kernel_launches;
-    k_rb_pick<<<c->k, 256, 0, c->stream>>>(a, lo, first);
+    const int lo = hi - a.digit > 0 ? hi - a.digit : 0;
+    if (!first) {  // the first level's histogram comes from the target kernels
+      k_rb_level<KT><<<g, 256, 0, c->stream>>>(a, lo, hi - lo);
+      ++c->kernel_launches;
+    }
+    k_rb_pick<<<c->k, kPickThreads, 0, c->stream>>>(a, lo, first);
     ++c->kernel_launches;
     hi = lo;
   }
