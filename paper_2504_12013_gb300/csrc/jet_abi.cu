@@ -454,6 +454,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
       break;
     }
     if ((e = launch_classify(c, wdeg)) != cudaSuccess) { rc = cuda_fail(c, e, "size classes"); break; }
+    if ((e = prepare_afterburner(c)) != cudaSuccess) { rc = cuda_fail(c, e, "edge segments"); break; }
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) { rc = cuda_fail(c, e, "context setup"); break; }
   } while (0);
   dfree(c, wdeg);
@@ -472,7 +473,8 @@ void jet_ctx_destroy(jet_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
-                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->vheavy, c->stats_scratch};
+                 c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->vheavy, c->stats_scratch,
+                 c->ab_seg, c->ab_slot_edge, c->ab_tab, c->ab_nm};
   for (void *p : dev) dfree(c, p);
   cudaStreamSynchronize(c->stream);
   for (auto &g : c->graphs) {

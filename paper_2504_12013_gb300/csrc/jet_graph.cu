@@ -245,7 +245,7 @@ struct jet_batch {
 namespace {
 
 int bfail(jet_batch *b, int code, const char *msg, cudaError_t e = cudaSuccess) {
-  if (b) snprintf(b->err, sizeof(b->err), "%s%s%s", msg, e != cudaSuccess ? ": " : "",
+  if (b) snprintf(b->err, sizeof(b->err), "%.160s%s%.80s", msg, e != cudaSuccess ? ": " : "",
                   e != cudaSuccess ? cudaGetErrorString(e) : "");
   jet::set_global_error("%s%s%s", msg, e != cudaSuccess ? ": " : "", e != cudaSuccess ? cudaGetErrorString(e) : "");
   return code;

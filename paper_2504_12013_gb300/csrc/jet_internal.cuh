@@ -28,8 +28,9 @@ namespace jet {
 constexpr int kMaxK = 256;
 constexpr int kLightPlanes = 6;      // thread-per-vertex gain path: weighted degree < 2^6
 constexpr int kTinyEdge = 8;         // thread-per-edge afterburner: |e| <= 8
-constexpr int kWarpEdge = 2048;      // warp-per-edge afterburner: 8 < |e| <= 2048
-constexpr int kWarpEdgeSlots = 32;   // a warp-class edge with more candidates is deferred
+constexpr int kWarpEdge = 128;       // warp-per-edge afterburner: 8 < |e| <= 128
+constexpr int kSegPins = 2048;       // block-class edges are cut into segments of at most this many pins
+constexpr int kSmallMidEdge = 32;    // warp-class edges of at most 32 pins: one pin per lane, pipelined
 constexpr int kPrioShift = 30;       // exact rebalancing priority encoding (needs c(v) <= 2^15)
 constexpr int kMaxVertexWeight = 32767;
 
@@ -50,7 +51,7 @@ struct Counters {
   unsigned long long n_moves;     // entries in the move list
   unsigned long long n_cand;      // |M|
   unsigned long long approved;    // afterburner-approved moves
-  unsigned long long n_deferred;  // warp-class edges handed to the block path
+  unsigned long long unused0;
   long long objective;            // (lambda-1), accumulated
   long long rb_rounds;
   long long rb_moves;
@@ -117,8 +118,16 @@ struct jet_ctx {
   int32_t *v_light = nullptr, *v_heavy = nullptr;
   int32_t n_light = 0, n_heavy = 0;
   uint8_t *vheavy = nullptr;  // per vertex: 1 if heavy (weighted degree >= 2^kLightPlanes)
-  int32_t *e_tiny = nullptr, *e_mid = nullptr, *e_big = nullptr;  // one array of m ids: [tiny | mid | big]
-  int32_t n_tiny = 0, n_mid = 0, n_big = 0;
+  // one array of m edge ids: [tiny by size | mid <= 32 pins | mid > 32 pins, largest first | big]
+  int32_t *e_tiny = nullptr, *e_mid_small = nullptr, *e_mid = nullptr, *e_big = nullptr;
+  int32_t n_tiny = 0, n_mid_small = 0, n_mid = 0, n_big = 0;
+  // block-class edges as segments (largest first): edge, first pin, pins, table slot (-1: the whole edge)
+  int4 *ab_seg = nullptr;
+  int32_t n_seg = 0;
+  int32_t n_slots = 0;                       // edges longer than one segment
+  int32_t *ab_slot_edge = nullptr;           // edge of each slot
+  unsigned long long *ab_tab = nullptr;      // per slot and block: max departure key, min arrival key
+  uint32_t *ab_nm = nullptr;                 // per slot: blocks holding a non-candidate pin (8 words)
 
   // workspace
   uint32_t *mask = nullptr;
@@ -217,6 +226,7 @@ cudaError_t launch_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, cons
                               const uint8_t *locked);
 cudaError_t launch_rebalance_candidates(jet_ctx *c, const int32_t *part, const int32_t *phi);
 // afterburner (k_ab.cu)
+cudaError_t prepare_afterburner(jet_ctx *c);
 cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi);
 cudaError_t launch_approve(jet_ctx *c, uint8_t *locked, int32_t *rg_out, uint8_t *approved_out, bool build_moves);
 cudaError_t launch_export_candidates(jet_ctx *c, int32_t *target, int32_t *gain, uint8_t *in_m);

@@ -22,9 +22,13 @@
 // (gathered from the partition), so the afterburner reads no phi entry.
 //
 // Size classes: |e| <= 8 one thread per edge (pairwise tests in registers);
-// 8 < |e| <= 2048 one warp per edge and > 2048 one thread block per edge,
-// both with a per-block max / min table and a non-candidate bitmask in
-// shared memory.
+// 8 < |e| <= 128 one warp per edge (<= 32 pins: software-pipelined over the
+// warp's edges; larger: largest edges first) and > 128 one thread block per
+// segment of <= 2048 pins, each with a per-block max / min table and a
+// non-candidate bitmask in shared memory.
+#include <algorithm>
+#include <vector>
+
 #include "jet_internal.cuh"
 
 namespace jet {
@@ -208,51 +212,215 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
   }
 }
 
-// Block per edge: the big class (|e| > 2048).
-__global__ void __launch_bounds__(512) k_ab_block(AbArgs a) {
+// Warp per edge for 8 < |e| <= 32 (one pin per lane), software-pipelined
+// over the warp's edges: while edge j is evaluated, the candidate records and
+// blocks of edge j+1, the pins of edge j+2, the offsets of edge j+3 and the
+// id of edge j+4 are in flight, so the chain list -> offsets -> pins ->
+// records costs one memory latency per edge instead of four.  The evaluation
+// is the same three passes as in k_ab_warp.
+__global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp_small(AbArgs a) {
+  extern __shared__ unsigned long long s_tab[];  // per warp: maxd[k], mina[k]
+  __shared__ uint32_t s_nm[kAbWarps][kMaxK / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long *maxd = s_tab + (size_t)w * 2 * a.k;
+  unsigned long long *mina = maxd + a.k;
+  uint32_t *nm = s_nm[w];
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
+  auto edge_at = [&](long long i) -> int { return i < a.nlist ? a.elist[i] : -1; };
+  // stage registers, named by how many edges ahead of the evaluated one they are
+  int e4 = edge_at(gw + 4 * nw);
+  int e3 = edge_at(gw + 3 * nw);
+  int64_t p3 = e3 >= 0 ? a.eptr[e3] : 0;
+  int sz3 = e3 >= 0 ? (int)(a.eptr[e3 + 1] - p3) : 0;
+  int e2 = edge_at(gw + 2 * nw);
+  int v2 = -1;
+  if (e2 >= 0) {
+    const int64_t q = a.eptr[e2];
+    if (lane < a.eptr[e2 + 1] - q) v2 = a.pins[q + lane];
+  }
+  int e1 = edge_at(gw + nw), v1 = -1;
+  uint64_t r1 = 0;
+  int b1 = 0;
+  if (e1 >= 0) {
+    const int64_t q = a.eptr[e1];
+    if (lane < a.eptr[e1 + 1] - q) {
+      v1 = a.pins[q + lane];
+      r1 = a.cand[v1];
+      b1 = a.part[v1];
+    }
+  }
+  int e0 = edge_at(gw), v0 = -1;
+  uint64_t r0 = 0;
+  int b0 = 0;
+  if (e0 >= 0) {
+    const int64_t q = a.eptr[e0];
+    if (lane < a.eptr[e0 + 1] - q) {
+      v0 = a.pins[q + lane];
+      r0 = a.cand[v0];
+      b0 = a.part[v0];
+    }
+  }
+  for (long long i = gw; i < a.nlist; i += nw) {
+    // advance the pipeline: every load below is first used one iteration later
+    const int e5 = edge_at(i + 5 * nw);
+    const int64_t p4 = e4 >= 0 ? a.eptr[e4] : 0;
+    const int sz4 = e4 >= 0 ? (int)(a.eptr[e4 + 1] - p4) : 0;
+    const int v3 = lane < sz3 ? a.pins[p3 + lane] : -1;
+    const uint64_t r2 = v2 >= 0 ? a.cand[v2] : 0ull;
+    const int b2 = v2 >= 0 ? a.part[v2] : 0;
+    // evaluate edge e0 with v0 / r0 / b0
+    const uint64_t r = r0;
+    const int s = cand_s(r), t = cand_t(r);
+    if (r) {
+      maxd[s] = 0ull;
+      mina[s] = ~0ull;
+      maxd[t] = 0ull;
+      mina[t] = ~0ull;
+      nm[s >> 5] = 0u;
+      nm[t >> 5] = 0u;
+    }
+    if (__any_sync(kFull, r != 0)) {
+      __syncwarp();
+      const uint64_t K = cand_key(r, v0);
+      if (r) {
+        atomicMax(&maxd[s], (unsigned long long)K);
+        atomicMin(&mina[t], (unsigned long long)K);
+      } else if (v0 >= 0) {
+        const int b = b0 & 255;
+        atomicOr(&nm[b >> 5], 1u << (b & 31));
+      }
+      __syncwarp();
+      if (r) {
+        const int wt = a.ewgt[e0];
+        int delta = 0;
+        if (maxd[s] == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina[s] == ~0ull || K < mina[s])) delta += wt;
+        if (mina[t] == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd[t] < K) delta -= wt;
+        if (delta) atomicAdd(&a.rg[v0], delta);
+      }
+      __syncwarp();
+    }
+    e0 = e1; v0 = v1; r0 = r1; b0 = b1;
+    e1 = e2; v1 = v2; r1 = r2; b1 = b2;
+    e2 = e3; v2 = v3;
+    e3 = e4; p3 = p4; sz3 = sz4;
+    e4 = e5;
+  }
+}
+
+// Block-class edges (|e| > kWarpEdge) in segments of at most kSegPins pins,
+// one thread block per segment, so a hub edge of 200,000 pins is spread over
+// ~100 blocks instead of serialising one.  A block builds the per-block
+// max-departure / min-arrival table and the non-candidate mask of its
+// segment in shared memory.  An edge that is a single segment is decided
+// right there; the segments of a longer edge merge their tables into the
+// edge's slot of a global table (atomic max / min / or), and k_ab_slots
+// decides those edges afterwards and resets the slots.
+constexpr int kSegThreads = 256;
+
+struct SegArgs {
+  AbArgs ab;
+  const int4 *seg;                 // edge, first pin (offset in pins), pins, slot or -1
+  int32_t nseg;
+  const int32_t *slot_edge;
+  unsigned long long *tab;         // slot * 2k: maxd[k] then mina[k]
+  uint32_t *nmw;                   // slot * 8 words
+  int32_t nslots;
+};
+
+__device__ __forceinline__ void ab_decide(const AbArgs &a, int b, unsigned long long md, unsigned long long ma,
+                                          bool nm, int w) {
+  const bool has_d = md != 0ull, has_a = ma != ~0ull;
+  if ((!has_d && !has_a) || nm) return;        // nothing moves here, or a pin of e in b stays
+  if (has_d && has_a && !(md < ma)) return;     // an arrival precedes the last departure
+  if (has_d) atomicAdd(&a.rg[(int)(md & 0xffffffffu)], w);
+  if (has_a) atomicAdd(&a.rg[(int)(ma & 0xffffffffu)], -w);
+  (void)b;
+}
+
+__global__ void __launch_bounds__(kSegThreads) k_ab_block(SegArgs sa) {
+  const AbArgs &a = sa.ab;
   extern __shared__ unsigned long long s_mem[];
-  unsigned long long *s_maxd = s_mem;            // k: max key among departures
-  unsigned long long *s_mina = s_mem + a.k;      // k: min key among arrivals
-  int *s_cntd = reinterpret_cast<int *>(s_mem + 2 * a.k);  // k: number of departures
-  __shared__ uint32_t s_nm[kMaxK / 32];          // blocks holding a non-candidate pin
-  for (int i = blockIdx.x; i < a.nlist; i += gridDim.x) {
-    const int e = a.elist[i];
+  unsigned long long *s_maxd = s_mem;        // k: max key among departures
+  unsigned long long *s_mina = s_mem + a.k;  // k: min key among arrivals
+  __shared__ uint32_t s_nm[kMaxK / 32];      // blocks holding a non-candidate pin
+  constexpr int kPer = kSegPins / kSegThreads;
+  for (int i = blockIdx.x; i < sa.nseg; i += gridDim.x) {
+    const int4 sg = sa.seg[i];
     for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
       s_maxd[b] = 0ull;
       s_mina[b] = ~0ull;
-      s_cntd[b] = 0;
     }
     if (threadIdx.x < kMaxK / 32) s_nm[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t p1 = a.eptr[e + 1];
-    for (int64_t p = a.eptr[e] + threadIdx.x; p < p1; p += blockDim.x) {
-      const int v = a.pins[p];
-      const uint64_t r = a.cand[v];
-      if (r) {
-        const uint64_t K = cand_key(r, v);
-        const int s = cand_s(r), t = cand_t(r);
-        atomicAdd(&s_cntd[s], 1);
-        atomicMax(&s_maxd[s], (unsigned long long)K);
-        atomicMin(&s_mina[t], (unsigned long long)K);
+    const int64_t p0 = a.eptr[sg.x] + sg.y;
+    int v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int j = q * kSegThreads + threadIdx.x;
+      v[q] = j < sg.z ? a.pins[p0 + j] : -1;
+    }
+    uint64_t r[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) r[q] = v[q] >= 0 ? a.cand[v[q]] : 0ull;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      if (v[q] < 0) continue;
+      if (r[q]) {
+        const uint64_t K = cand_key(r[q], v[q]);
+        atomicMax(&s_maxd[cand_s(r[q])], (unsigned long long)K);
+        atomicMin(&s_mina[cand_t(r[q])], (unsigned long long)K);
       } else {
-        const int b = a.part[v] & 255;
+        const int b = a.part[v[q]] & 255;
         const uint32_t bit = 1u << (b & 31);
         if (!(s_nm[b >> 5] & bit)) atomicOr(&s_nm[b >> 5], bit);
       }
     }
     __syncthreads();
-    const int w = a.ewgt[e];
-    for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
-      const int nd = s_cntd[b];
-      const bool has_a = s_mina[b] != ~0ull;
-      if (nd == 0 && !has_a) continue;
-      if ((s_nm[b >> 5] >> (b & 31)) & 1u) continue;  // a pin of e in b stays
-      if (nd > 0 && has_a && !(s_maxd[b] < s_mina[b])) continue;
-      if (nd > 0) atomicAdd(&a.rg[(int)(s_maxd[b] & 0xffffffffu)], w);
-      if (has_a) atomicAdd(&a.rg[(int)(s_mina[b] & 0xffffffffu)], -w);
+    if (sg.w < 0) {  // the whole edge: decide here
+      const int w = a.ewgt[sg.x];
+      for (int b = threadIdx.x; b < a.k; b += blockDim.x)
+        ab_decide(a, b, s_maxd[b], s_mina[b], (s_nm[b >> 5] >> (b & 31)) & 1u, w);
+    } else {  // one segment of a longer edge: merge into its slot
+      unsigned long long *tmax = sa.tab + (size_t)sg.w * 2 * a.k, *tmin = tmax + a.k;
+      for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
+        if (s_maxd[b] != 0ull) atomicMax(&tmax[b], s_maxd[b]);
+        if (s_mina[b] != ~0ull) atomicMin(&tmin[b], s_mina[b]);
+      }
+      if (threadIdx.x < kMaxK / 32 && s_nm[threadIdx.x]) atomicOr(&sa.nmw[sg.w * 8 + threadIdx.x], s_nm[threadIdx.x]);
     }
     __syncthreads();
   }
+}
+
+// The edges longer than one segment: decide every (edge, block) from the
+// merged tables, then reset the slot for the next call.
+__global__ void __launch_bounds__(256) k_ab_slots(SegArgs sa) {
+  const AbArgs &a = sa.ab;
+  const int64_t total = (int64_t)sa.nslots * a.k;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(x / a.k), b = (int)(x % a.k);
+    unsigned long long *tmax = sa.tab + (size_t)slot * 2 * a.k, *tmin = tmax + a.k;
+    const bool nm = (sa.nmw[slot * 8 + (b >> 5)] >> (b & 31)) & 1u;
+    ab_decide(a, b, tmax[b], tmin[b], nm, a.ewgt[sa.slot_edge[slot]]);
+    tmax[b] = 0ull;
+    tmin[b] = ~0ull;
+  }
+}
+
+__global__ void k_ab_slots_clear_nm(uint32_t *nmw, int32_t words) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < words; x += gridDim.x * blockDim.x) nmw[x] = 0u;
+}
+
+__global__ void k_edge_sizes(const int64_t *eptr, const int32_t *ids, int32_t n, int64_t *out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = eptr[ids[i] + 1] - eptr[ids[i]];
+}
+
+__global__ void k_ab_slots_init(unsigned long long *tab, int32_t nslots, int32_t k) {
+  const int64_t total = (int64_t)nslots * 2 * k;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x)
+    tab[x] = ((x / k) & 1) ? ~0ull : 0ull;
 }
 
 // Approval: v in M and recomputed gain > 0.  Resets rg, counts |M|; with
@@ -354,6 +522,14 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
     k_ab_tiny<<<grid_for(c->n_tiny, 256, c->launch_sms), 256, 0, c->stream>>>(a);
     ++c->kernel_launches;
   }
+  if (c->n_mid_small > 0) {
+    a.elist = c->e_mid_small;
+    a.nlist = c->n_mid_small;
+    const size_t smem = (size_t)kAbWarps * 2 * c->k * sizeof(unsigned long long);
+    k_ab_warp_small<<<grid_for((int64_t)c->n_mid_small * 32, kAbWarps * 32, c->launch_sms), kAbWarps * 32, smem,
+                      c->stream>>>(a);
+    ++c->kernel_launches;
+  }
   if (c->n_mid > 0) {
     a.elist = c->e_mid;
     a.nlist = c->n_mid;
@@ -361,14 +537,83 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
     k_ab_warp<<<grid_for((int64_t)c->n_mid * 32, kAbWarps * 32, c->launch_sms), kAbWarps * 32, smem, c->stream>>>(a);
     ++c->kernel_launches;
   }
-  if (c->n_big > 0) {
-    a.elist = c->e_big;
-    a.nlist = c->n_big;
-    const size_t smem = (size_t)c->k * (2 * sizeof(unsigned long long) + sizeof(int));
-    k_ab_block<<<c->launch_sms * 2, 512, smem, c->stream>>>(a);
+  if (c->n_seg > 0) {
+    SegArgs sa{};
+    sa.ab = a;
+    sa.seg = c->ab_seg;
+    sa.nseg = c->n_seg;
+    sa.slot_edge = c->ab_slot_edge;
+    sa.tab = c->ab_tab;
+    sa.nmw = c->ab_nm;
+    sa.nslots = c->n_slots;
+    const size_t smem = (size_t)c->k * 2 * sizeof(unsigned long long);
+    k_ab_block<<<grid_for(c->n_seg, 1, c->launch_sms, 8), kSegThreads, smem, c->stream>>>(sa);
     ++c->kernel_launches;
+    if (c->n_slots > 0) {
+      k_ab_slots<<<grid_for((int64_t)c->n_slots * c->k, 256, c->launch_sms), 256, 0, c->stream>>>(sa);
+      k_ab_slots_clear_nm<<<grid_for((int64_t)c->n_slots * 8, 256, c->launch_sms), 256, 0, c->stream>>>(
+          c->ab_nm, c->n_slots * 8);
+      c->kernel_launches += 2;
+    }
   }
   return cudaGetLastError();
+}
+
+// Cuts the block-class edges into segments (largest first) and sets up the
+// merge table of the edges longer than one segment.  Host work, once per
+// context (synchronizes the stream).
+cudaError_t prepare_afterburner(jet_ctx *c) {
+  if (c->n_big == 0) return cudaSuccess;
+  std::vector<int32_t> ids(c->n_big);
+  cudaError_t e = cudaMemcpyAsync(ids.data(), c->e_big, sizeof(int32_t) * c->n_big, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+  std::vector<int64_t> sz(c->n_big);
+  int64_t *dsz = nullptr;
+  if ((e = cudaMallocAsync(reinterpret_cast<void **>(&dsz), sizeof(int64_t) * c->n_big, c->stream)) != cudaSuccess)
+    return e;
+  k_edge_sizes<<<grid_for(c->n_big, 256, c->launch_sms), 256, 0, c->stream>>>(c->eptr, c->e_big, c->n_big, dsz);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sz.data(), dsz, sizeof(int64_t) * c->n_big, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFreeAsync(dsz, c->stream);
+  if (e != cudaSuccess) return e;
+  std::vector<int4> seg;
+  std::vector<int32_t> slot_edge;
+  for (int32_t i = 0; i < c->n_big; ++i) {
+    const int slot = sz[i] > kSegPins ? (int)slot_edge.size() : -1;
+    if (slot >= 0) slot_edge.push_back(ids[i]);
+    for (int64_t off = 0; off < sz[i]; off += kSegPins)
+      seg.push_back(make_int4(ids[i], (int)off, (int)std::min<int64_t>(kSegPins, sz[i] - off), slot));
+  }
+  std::stable_sort(seg.begin(), seg.end(), [](const int4 &x, const int4 &y) { return x.z > y.z; });
+  c->n_seg = (int32_t)seg.size();
+  c->n_slots = (int32_t)slot_edge.size();
+  if ((e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_seg), sizeof(int4) * seg.size(), c->stream)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(c->ab_seg, seg.data(), sizeof(int4) * seg.size(), cudaMemcpyHostToDevice, c->stream)) !=
+      cudaSuccess)
+    return e;
+  if (c->n_slots > 0) {
+    const size_t ns = (size_t)c->n_slots;
+    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_slot_edge), sizeof(int32_t) * ns, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_tab), sizeof(unsigned long long) * ns * 2 * c->k,
+                             c->stream)) != cudaSuccess ||
+        (e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_nm), sizeof(uint32_t) * ns * 8, c->stream)) !=
+            cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(c->ab_slot_edge, slot_edge.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+      return e;
+    k_ab_slots_init<<<grid_for((int64_t)ns * 2 * c->k, 256, c->launch_sms), 256, 0, c->stream>>>(c->ab_tab,
+                                                                                                   c->n_slots, c->k);
+    k_ab_slots_clear_nm<<<grid_for((int64_t)ns * 8, 256, c->launch_sms), 256, 0, c->stream>>>(c->ab_nm,
+                                                                                              c->n_slots * 8);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaStreamSynchronize(c->stream);
 }
 
 cudaError_t launch_approve(jet_ctx *c, uint8_t *locked, int32_t *rg_out, uint8_t *approved_out, bool build_moves) {

@@ -103,7 +103,7 @@ __global__ void k_validate_degrees(const int64_t *vptr, const int32_t *inc, cons
 
 // ---------------------------------------------------------------- classes
 // Stable partition of ids [0, count) by class code (0 .. kClasses-1).
-constexpr int kClasses = 16;
+constexpr int kClasses = 24;
 
 __global__ void k_class_count(const uint8_t *code, int32_t count, int32_t *blk_counts) {
   __shared__ int s_c[kClasses];
@@ -141,11 +141,19 @@ __global__ void k_vertex_codes(const int64_t *wdeg, int32_t n, uint8_t *code) {
 }
 
 // Edge classes: code = |e| for |e| <= kTinyEdge (so the tiny list comes out
-// ordered by size and a warp's edges tend to share one size), then mid, big.
+// ordered by size and a warp's edges tend to share one size); then the warp
+// class split into kSmallMidEdge-pin edges (one code) and larger ones by
+// size bucket, largest first, so the warps that get the longest edges start
+// first; then the block class.
 __global__ void k_edge_codes(const int64_t *eptr, int32_t m, uint8_t *code) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t sz = eptr[e + 1] - eptr[e];
-    code[e] = sz <= kTinyEdge ? (uint8_t)sz : (sz <= kWarpEdge ? kTinyEdge + 1 : kTinyEdge + 2);
+    const int64_t sz = eptr[e + 1] - eptr[e];
+    int c;
+    if (sz <= kTinyEdge) c = (int)sz;
+    else if (sz <= kSmallMidEdge) c = kTinyEdge + 1;
+    else if (sz <= kWarpEdge) c = sz > 64 ? kTinyEdge + 2 : kTinyEdge + 3;  // 65..128 first, then 33..64
+    else c = kTinyEdge + 4;
+    code[e] = (uint8_t)c;
   }
 }
 
@@ -365,9 +373,11 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
   if (e == cudaSuccess) {
     c->n_tiny = 0;
     for (int cl = 0; cl <= kTinyEdge; ++cl) c->n_tiny += t[cl];
-    c->n_mid = t[kTinyEdge + 1];
-    c->n_big = t[kTinyEdge + 2];
-    c->e_mid = c->e_tiny + c->n_tiny;
+    c->n_mid_small = t[kTinyEdge + 1];
+    c->n_mid = t[kTinyEdge + 2] + t[kTinyEdge + 3];
+    c->n_big = t[kTinyEdge + 4];
+    c->e_mid_small = c->e_tiny + c->n_tiny;
+    c->e_mid = c->e_mid_small + c->n_mid_small;
     c->e_big = c->e_mid + c->n_mid;
   }
   cudaFreeAsync(code, c->stream);
