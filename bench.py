@@ -125,12 +125,32 @@ def kernel_bytes(hg, k, deg, st_before, round_stats):
     return b
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the candidate kernel from the committed ncu summary, or None if the
-    kernel source changed since that capture (or no capture exists for this workload)."""
+def ctx_unit_weights(hg):
+    return bool(hg.m == 0 or int(hg.ewgt.max()) <= 1)
+
+
+def rebalance_target_bytes(hg, k, stats, work, unit):
+    """Algorithmic bytes of the rebalancing target kernels over one iteration (all its rounds), gathers
+    counted at their element size: per round a scan of the partition and heavy flags; per vertex of an
+    overloaded block its weight; per evaluated vertex its offsets and its record (16 B key, vertex,
+    weight/target) and first-level histogram update (8 B); per incidence of an evaluated vertex the edge id,
+    the edge's bitmask row (2 ceil(k/32) words, rounded to 8/16/32/64 B) and omega(e) unless unit."""
+    kw = (k + 31) // 32
+    row = 4 * 2 * (1 if kw <= 1 else 2 if kw <= 2 else 4 if kw <= 4 else 8)
+    rounds = stats["rebalance_rounds"]
+    b = rounds * (4 * hg.n + hg.n)
+    b += 4 * work["rebalance_over"]
+    b += (8 + 16 + 8) * work["rebalance_evaluated"]
+    b += (4 + row + (0 if unit else 4)) * work["rebalance_evaluated_pins"]
+    return b
+
+
+def ncu_traffic(workload, kernel="k_cand_light"):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, or None if the kernel source
+    changed since that capture (or no capture exists for this workload)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "k_cand_light.md")
+    path = os.path.join(ROOT, "profiles", kernel + ".md")
     src = os.path.join(ROOT, "paper_2504_12013_gb300", "csrc", "k_cand.cu")
     if not os.path.exists(path):
         return None
@@ -207,6 +227,7 @@ def run_gpu(args, rank, world):
     jet.jet_profile_read(ctx, reset=True)
     deg = np.diff(hg.vptr)
     model_bytes = 0
+    rb_bytes = 0
     trace = []
     for _ in range(args.steps):
         locked_before = st.locked.cpu().numpy()[: hg.n].astype(bool)
@@ -214,13 +235,15 @@ def run_gpu(args, rank, world):
         s = st.stats_dict()
         trace.append(s)
         model_bytes += kernel_bytes(hg, k, deg, locked_before, s)
+        rb_bytes += rebalance_target_bytes(hg, k, s, jet.jet_profile_work(ctx), ctx_unit_weights(hg))
     prof = jet.jet_profile_read(ctx, reset=True)
     if args.eager:
         prof = prof_eager_timed
     jet.jet_profile_enable(ctx, False)
     assert trace[-1] == final_stats, "replay diverged from the timed run"
 
-    result = {"ms": ms, "prof": prof, "prof_timed": prof_timed, "model_bytes": model_bytes, "trace": trace,
+    result = {"ms": ms, "prof": prof, "prof_timed": prof_timed, "model_bytes": model_bytes, "rb_bytes": rb_bytes,
+              "trace": trace,
               "clocks": clk.summary(), "hg": hg, "k": k, "part0": part0, "desc": desc, "dev": dev}
     ctx.close()
     return result
@@ -514,6 +537,9 @@ def main():
     dom = max(fam_ms, key=fam_ms.get)
     cand_ms = r["prof_timed"]["candidates"]["ms"]  # measured inside the timed region
     achieved = r["model_bytes"] / (cand_ms / 1e3) / 1e9 if cand_ms > 0 else None
+    tgt_ms = prof["rebalance_targets"]["ms"]
+    tgt_launches = prof["rebalance_targets"]["launches"]
+    tgt_achieved = r["rb_bytes"] / (tgt_ms / 1e3) / 1e9 if tgt_ms > 0 else None
     launches = sum(v["launches"] for v in prof.values())
     line = {
         "metric": "Jet-round pins/s (bit-exact vs oracle)",
@@ -534,18 +560,29 @@ def main():
                                                                           "rebalancing loop)",
                    "l2": "inputs larger than L2 (phi %d MB)" % (hg.m * k * 4 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "candidates (k_cand_light/k_cand_heavy)",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None,
-                     "traffic": ncu_traffic(args.workload),
-                     "traffic_note": "DRAM bytes of the first timed launch (profiles/k_cand_light.md)",
+        "roofline": {"bound": "hbm", "kernel": "rebalancing targets (k_rbcand_light/k_rbcand_heavy)",
+                     "achieved": tgt_achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (tgt_achieved / hbm) if tgt_achieved else None,
+                     "traffic": ncu_traffic(args.workload, "k_rbcand_light"),
+                     "traffic_note": "mean DRAM bytes per launch, first 24 launches, cold L2 "
+                                     "(profiles/k_rbcand_light.md)",
+                     "bytes_per_step": r["rb_bytes"] / args.steps,
+                     "ms_per_step": tgt_ms / args.steps,
+                     "launches_per_step": tgt_launches / args.steps,
+                     "timing": "CUDA events around each launch in the kernel-by-kernel replay of the timed steps "
+                               "(the kernels sit in a conditional graph body, which cannot hold event nodes)",
                      "peak_source": peak_src,
+                     "candidates": {"kernel": "k_cand_light/k_cand_heavy", "achieved": achieved,
+                                    "frac": (achieved / hbm) if achieved else None,
+                                    "traffic": ncu_traffic(args.workload),
+                                    "traffic_note": "DRAM bytes of the first timed launch (profiles/k_cand_light.md)",
+                                    "timing": "event-record nodes around the kernels inside the timed graphs",
+                                    "ms_per_step": cand_ms / args.steps,
+                                    "bytes_per_step": r["model_bytes"] / args.steps},
                      "dominant_family": dom, "family_share": {f: round(v / total_fam, 4) for f, v in fam_ms.items()}
                      if total_fam > 0 else {},
                      "family_ms_per_step_replay": {f: round(v / args.steps, 4) for f, v in fam_ms.items()},
-                     "family_times": "kernel-by-kernel replay of the timed steps (identical work)",
-                     "candidates_ms_per_step": cand_ms / args.steps,
-                     "model_bytes_per_step": r["model_bytes"] / args.steps},
+                     "family_times": "kernel-by-kernel replay of the timed steps (identical work)"},
         "clocks": r["clocks"],
         "gpu_launches": launches,
         "e2e": e2e,

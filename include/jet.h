@@ -334,6 +334,16 @@ int jet_profile_enable(jet_ctx *ctx, int enable);
 int jet_profile_read(jet_ctx *ctx, double *ms_out, int64_t *calls_out, int64_t *launches_out, int reset);
 
 /*
+ * Work counts of the last jet_refine_round or jet_rebalance call (for byte
+ * models of the kernels; always counted, no events).  Synchronizes.  Writes
+ * up to n (<= 4) entries of out (HOST): [0] vertices of overloaded blocks
+ * met by the rebalancing target passes, summed over the rounds; [1] vertices
+ * they evaluated (one record each); [2] the incidences of those vertices;
+ * [3] incidences of all moved vertices (Jet and rebalancing moves).
+ */
+int jet_profile_work(jet_ctx *ctx, int64_t *out, int32_t n);
+
+/*
  * Block weights without any device allocation (the paper has no counterpart;
  * this is a deployment variant of the block-weight pass of
  * jet_build_pincounts).  For callers that must not allocate device memory:

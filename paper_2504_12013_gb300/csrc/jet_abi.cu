@@ -673,6 +673,17 @@ int jet_profile_read(jet_ctx *c, double *ms_out, int64_t *calls_out, int64_t *la
   return JET_OK;
 }
 
+int jet_profile_work(jet_ctx *c, int64_t *out, int32_t n) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (n < 0 || n > 4 || (n > 0 && !out)) return fail(c, JET_ERR_INVALID_ARG, "n must be in [0, 4]");
+  unsigned long long w[4];
+  CK(cudaMemcpyAsync(w, &c->cnt->w_over, sizeof(w), cudaMemcpyDeviceToHost, c->stream), "work counts");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  for (int i = 0; i < n; ++i) out[i] = (int64_t)w[i];
+  return JET_OK;
+}
+
 int jet_refine_host(const jet_hypergraph *hh, const jet_params *p, const int32_t *tau_pairs, int32_t n_tau,
                     int32_t limit, int32_t *part, jet_refine_result *result) {
   if (!hh || !p || !part) return fail(nullptr, JET_ERR_INVALID_ARG, "NULL argument");

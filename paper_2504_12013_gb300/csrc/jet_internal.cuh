@@ -55,6 +55,9 @@ struct Counters {
   long long objective;            // (lambda-1), accumulated
   long long rb_rounds;
   long long rb_moves;
+  // work counts of the current call (jet_profile_work): vertices of overloaded blocks met by the
+  // rebalancing target passes, vertices they evaluated, the incidences of those, incidences moved
+  unsigned long long w_over, w_eval, w_eval_pins, w_apply_pins;
   unsigned long long n_rec;       // rebalancing records of the current round
   int rb_done;                    // rebalancing loop may stop
   int rb_any;                     // an overloaded block exists

@@ -257,6 +257,32 @@ __device__ __forceinline__ uint64_t rb_hi_of(const CandArgs &a, int32_t g, int32
   return rb_order_key(g, c);
 }
 
+// Adds the thread's work counts to the call's totals: one atomic per thread
+// block and counter (every thread of the block calls it).
+__device__ __forceinline__ void count_work(Counters *cnt, unsigned long long over, unsigned long long eval,
+                                           unsigned long long pins) {
+  __shared__ unsigned long long s_w[3];
+  if (threadIdx.x < 3) s_w[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    over += __shfl_xor_sync(kFull, over, o);
+    eval += __shfl_xor_sync(kFull, eval, o);
+    pins += __shfl_xor_sync(kFull, pins, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (over) atomicAdd(&s_w[0], over);
+    if (eval) atomicAdd(&s_w[1], eval);
+    if (pins) atomicAdd(&s_w[2], pins);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_w[0]) atomicAdd(&cnt->w_over, s_w[0]);
+    if (s_w[1]) atomicAdd(&cnt->w_eval, s_w[1]);
+    if (s_w[2]) atomicAdd(&cnt->w_eval_pins, s_w[2]);
+  }
+}
+
 // Top digit of the selection key K(v) = hi << vbits | v (the first radix
 // level), added with c(v) into the (block, digit) histogram: one atomic per
 // distinct (block, digit) in the warp.  Every lane of the warp calls it.
@@ -630,6 +656,7 @@ __global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_rbcand_light(CandArgs
   int64_t base = ((int64_t)blockIdx.x * warps + w) * 32;
   GroupRaw cur = fetch_group(a, base + lane, false);
   int qn = 0;
+  unsigned long long w_over = 0, w_eval = 0, w_pins = 0;
   for (; base < a.n; base += stride) {
     const GroupRaw nxt = fetch_group(a, base + stride + lane, false);
     const int64_t v = base + lane;
@@ -639,6 +666,7 @@ __global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_rbcand_light(CandArgs
     int64_t j0 = 0;
     int deg = 0;
     if (v < a.n && !cur.hv && (unsigned)s < (unsigned)a.k && s_over[s]) {
+      ++w_over;
       c = a.vwgt[v];
       if (2ll * c <= 3ll * (s_bw[s] - a.A)) {  // heavy vertices (Section 4.3) are never moved
         uint32_t nz = 0;
@@ -655,6 +683,8 @@ __global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_rbcand_light(CandArgs
           act = true;
           j0 = a.vptr[v];
           deg = (int)(a.vptr[v + 1] - j0);
+          ++w_eval;
+          w_pins += deg;
         }
       }
     }
@@ -666,6 +696,7 @@ __global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_rbcand_light(CandArgs
     cur = nxt;
   }
   if (qn > 0) rb_batch<KWP, UNIT, kTab>(a, stage, q, qn, s_cap, s_elig);
+  count_work(a.cnt, w_over, w_eval, w_pins);
 }
 
 template <int KWP>
@@ -681,11 +712,13 @@ __global__ void __launch_bounds__(256) k_rbcand_heavy(CandArgs a) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long w_over = 0, w_eval = 0, w_pins = 0;
   for (int i = gw; i < a.nlist; i += nw) {
     const int v = a.vlist[i];
     const int s = a.part[v];
     const int32_t c = a.vwgt[v];
     bool any_elig = false;
+    if (lane == 0 && (unsigned)s < (unsigned)a.k && s_over[s]) ++w_over;
     if ((unsigned)s < (unsigned)a.k && s_over[s] && 2ll * c <= 3ll * (s_bw[s] - a.A)) {
 #pragma unroll
       for (int q = 0; q < KWP; ++q) {
@@ -694,6 +727,10 @@ __global__ void __launch_bounds__(256) k_rbcand_heavy(CandArgs a) {
       }
     }
     if (!__any_sync(kFull, any_elig)) continue;  // no record (warp-uniform: one vertex per warp)
+    if (lane == 0) {
+      ++w_eval;
+      w_pins += (unsigned long long)(a.vptr[v + 1] - a.vptr[v]);
+    }
     int32_t conn[KWP];
     uint32_t adj;
     const int32_t A = accumulate_heavy<KWP>(a, v, s, conn, adj);
@@ -714,6 +751,7 @@ __global__ void __launch_bounds__(256) k_rbcand_heavy(CandArgs a) {
       a.rb_ct[pos] = (c << 16) | (s << 8) | bb;
     }
   }
+  count_work(a.cnt, w_over, w_eval, w_pins);
 }
 
 template <int KWP>

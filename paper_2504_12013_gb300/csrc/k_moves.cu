@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) { s_dw[b] = 0; s_dc[b] = 0; }
   __syncthreads();
   const long long nm = (long long)a.cnt->n_moves;
+  unsigned long long pins = 0;  // incidences moved by this thread's moves (work count)
   const int sub = threadIdx.x % kMoveLanes;
   const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
   const long long ng = ((long long)gridDim.x * blockDim.x) / kMoveLanes;
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
     }
     const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
     const int64_t j1 = a.vptr[v + 1];
+    if (sub == 0) pins += (unsigned long long)(j1 - a.vptr[v]);
     for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
       const int64_t e = a.inc[j];
       const int os = atomicSub(&a.phi[e * a.k + s], 1);  // os -> os - 1
@@ -74,7 +76,14 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
       if (ot == 1) atomicXor(&row[a.kwp + (t >> 5)], tbit);  // 1 -> 2
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pins += __shfl_xor_sync(kFull, pins, o);
+  __shared__ unsigned long long s_pins;
+  if (threadIdx.x == 0) s_pins = 0;
   __syncthreads();
+  if ((threadIdx.x & 31) == 0 && pins) atomicAdd(&s_pins, pins);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_pins) atomicAdd(&a.cnt->w_apply_pins, s_pins);
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
     if (s_dw[b]) add_i64(reinterpret_cast<long long *>(&a.bw[b]), s_dw[b]);
     if (s_dc[b]) atomicAdd(&a.vcount[b], s_dc[b]);

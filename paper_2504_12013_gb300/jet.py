@@ -27,7 +27,7 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_set_graph_mode", "jet_batch_create", "jet_batch_destroy", "jet_batch_last_error",
            "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune",
            "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
-           "jet_server_last_error", "jet_server_destroy")
+           "jet_server_last_error", "jet_server_destroy", "jet_profile_work")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -107,6 +107,7 @@ def load_library():
             lib.jet_profile_read.argtypes = [_P, pp(ctypes.c_double), pp(i64), pp(i64), ctypes.c_int]
             lib.jet_block_weights_noalloc.argtypes = [_P, _P, i32, i32, _P, _P, _P]
             lib.jet_set_graph_mode.argtypes = [_P, ctypes.c_int]
+            lib.jet_profile_work.argtypes = [_P, pp(i64), i32]
             lib.jet_batch_create.argtypes = [pp(_P), pp(_P), i32, _P]
             lib.jet_batch_destroy.argtypes = [_P]
             lib.jet_batch_destroy.restype = None
@@ -311,6 +312,15 @@ def jet_profile_read(ctx: Ctx, reset: bool = True) -> dict:
     launches = (ctypes.c_int64 * n)()
     _check(load_library().jet_profile_read(ctx.handle, ms, calls, launches, 1 if reset else 0), ctx)
     return {f: {"ms": ms[i], "calls": calls[i], "launches": launches[i]} for i, f in enumerate(PROF_FAMILIES)}
+
+
+WORK_FIELDS = ("rebalance_over", "rebalance_evaluated", "rebalance_evaluated_pins", "moved_pins")
+
+
+def jet_profile_work(ctx: Ctx) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    _check(load_library().jet_profile_work(ctx.handle, out, 4), ctx)
+    return dict(zip(WORK_FIELDS, [int(x) for x in out]))
 
 
 def jet_block_weights_noalloc(part, vwgt, k, block_w, block_count=None, stream=None):
