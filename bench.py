@@ -145,13 +145,22 @@ def rebalance_target_bytes(hg, k, stats, work, unit):
     return b
 
 
+def apply_move_bytes(stats, work):
+    """Algorithmic bytes of the apply kernel over one iteration (the Jet moves and every rebalancing
+    round's moves): per move its list entry (vertex, source/target), the partition write, c(v) and the
+    offsets; per incidence of a moved vertex the edge id and two phi read-modify-writes (4 B each way).
+    The bitmask toggles at phi crossings are not counted."""
+    moves = stats["approved"] + stats["rebalance_moves"]
+    return moves * (4 + 4 + 4 + 4 + 16) + work["moved_pins"] * (4 + 2 * 8)
+
+
 def ncu_traffic(workload, kernel="k_cand_light"):
     """DRAM bytes per launch of a kernel from its committed ncu summary, or None if the kernel source
     changed since that capture (or no capture exists for this workload)."""
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", kernel + ".md")
-    src = os.path.join(ROOT, "paper_2504_12013_gb300", "csrc", "k_cand.cu")
+    src = os.path.join(ROOT, "paper_2504_12013_gb300", "csrc", "k_moves.cu" if kernel == "k_apply" else "k_cand.cu")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -228,6 +237,7 @@ def run_gpu(args, rank, world):
     deg = np.diff(hg.vptr)
     model_bytes = 0
     rb_bytes = 0
+    apply_bytes = 0
     trace = []
     for _ in range(args.steps):
         locked_before = st.locked.cpu().numpy()[: hg.n].astype(bool)
@@ -235,7 +245,9 @@ def run_gpu(args, rank, world):
         s = st.stats_dict()
         trace.append(s)
         model_bytes += kernel_bytes(hg, k, deg, locked_before, s)
-        rb_bytes += rebalance_target_bytes(hg, k, s, jet.jet_profile_work(ctx), ctx_unit_weights(hg))
+        work = jet.jet_profile_work(ctx)
+        rb_bytes += rebalance_target_bytes(hg, k, s, work, ctx_unit_weights(hg))
+        apply_bytes += apply_move_bytes(s, work)
     prof = jet.jet_profile_read(ctx, reset=True)
     if args.eager:
         prof = prof_eager_timed
@@ -243,6 +255,7 @@ def run_gpu(args, rank, world):
     assert trace[-1] == final_stats, "replay diverged from the timed run"
 
     result = {"ms": ms, "prof": prof, "prof_timed": prof_timed, "model_bytes": model_bytes, "rb_bytes": rb_bytes,
+              "apply_bytes": apply_bytes,
               "trace": trace,
               "clocks": clk.summary(), "hg": hg, "k": k, "part0": part0, "desc": desc, "dev": dev}
     ctx.close()
@@ -537,9 +550,25 @@ def main():
     dom = max(fam_ms, key=fam_ms.get)
     cand_ms = r["prof_timed"]["candidates"]["ms"]  # measured inside the timed region
     achieved = r["model_bytes"] / (cand_ms / 1e3) / 1e9 if cand_ms > 0 else None
-    tgt_ms = prof["rebalance_targets"]["ms"]
-    tgt_launches = prof["rebalance_targets"]["launches"]
-    tgt_achieved = r["rb_bytes"] / (tgt_ms / 1e3) / 1e9 if tgt_ms > 0 else None
+    replay_note = ("CUDA events around each launch in the kernel-by-kernel replay of the timed steps (these kernels "
+                   "also run inside conditional graph bodies, which cannot hold event nodes)")
+
+    def family_roofline(fam, kernel, nbytes, traffic_kernel):
+        fms, fl = prof[fam]["ms"], prof[fam]["launches"]
+        ach = nbytes / (fms / 1e3) / 1e9 if fms > 0 else None
+        return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": (ach / hbm) if ach else None,
+                "traffic": ncu_traffic(args.workload, traffic_kernel) if traffic_kernel else None,
+                "traffic_note": (f"mean DRAM bytes per launch, cold L2 (profiles/{traffic_kernel}.md)"
+                                 if traffic_kernel else "no capture for this kernel"),
+                "bytes_per_step": nbytes / args.steps, "ms_per_step": fms / args.steps,
+                "launches_per_step": fl / args.steps, "timing": replay_note, "peak_source": peak_src}
+
+    fam_roof = {"rebalance_targets": family_roofline("rebalance_targets",
+                                                     "rebalancing targets (k_rbcand_light/k_rbcand_heavy)",
+                                                     r["rb_bytes"], "k_rbcand_light"),
+                "apply": family_roofline("apply", "apply moves (k_apply)", r["apply_bytes"], "k_apply")}
+    dom_kernel = max(fam_roof, key=lambda f: prof[f]["ms"])  # the kernel with the most device time per step
     launches = sum(v["launches"] for v in prof.values())
     line = {
         "metric": "Jet-round pins/s (bit-exact vs oracle)",
@@ -560,18 +589,8 @@ def main():
                                                                           "rebalancing loop)",
                    "l2": "inputs larger than L2 (phi %d MB)" % (hg.m * k * 4 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "rebalancing targets (k_rbcand_light/k_rbcand_heavy)",
-                     "achieved": tgt_achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (tgt_achieved / hbm) if tgt_achieved else None,
-                     "traffic": ncu_traffic(args.workload, "k_rbcand_light"),
-                     "traffic_note": "mean DRAM bytes per launch, first 24 launches, cold L2 "
-                                     "(profiles/k_rbcand_light.md)",
-                     "bytes_per_step": r["rb_bytes"] / args.steps,
-                     "ms_per_step": tgt_ms / args.steps,
-                     "launches_per_step": tgt_launches / args.steps,
-                     "timing": "CUDA events around each launch in the kernel-by-kernel replay of the timed steps "
-                               "(the kernels sit in a conditional graph body, which cannot hold event nodes)",
-                     "peak_source": peak_src,
+        "roofline": dict(fam_roof[dom_kernel], **{
+                     "others": {f: v for f, v in fam_roof.items() if f != dom_kernel},
                      "candidates": {"kernel": "k_cand_light/k_cand_heavy", "achieved": achieved,
                                     "frac": (achieved / hbm) if achieved else None,
                                     "traffic": ncu_traffic(args.workload),
@@ -582,7 +601,7 @@ def main():
                      "dominant_family": dom, "family_share": {f: round(v / total_fam, 4) for f, v in fam_ms.items()}
                      if total_fam > 0 else {},
                      "family_ms_per_step_replay": {f: round(v / args.steps, 4) for f, v in fam_ms.items()},
-                     "family_times": "kernel-by-kernel replay of the timed steps (identical work)"},
+                     "family_times": "kernel-by-kernel replay of the timed steps (identical work)"}),
         "clocks": r["clocks"],
         "gpu_launches": launches,
         "e2e": e2e,
