@@ -171,6 +171,23 @@ def ncu_traffic(workload, kernel="k_cand_light"):
     return int(m.group(1)) if m else None
 
 
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's time (every rank runs its own replica; the job takes as long as the slowest)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world):
     import torch
@@ -220,11 +237,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     prof_timed = jet.jet_profile_read(ctx, reset=True)  # graph mode: the candidate kernels, timed in the graphs
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     final_stats = st.stats_dict()
 
     # untimed replay of the same K steps, kernel by kernel (results are bit-identical): per-family device
@@ -543,7 +556,7 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     ms = r["ms"]
-    value = hg.P * args.steps * world / (ms / 1e3)
+    value = job_throughput(hg.P * args.steps, world, ms)
     prof = r["prof"]
     fam_ms = {f: v["ms"] for f, v in prof.items()}
     total_fam = sum(fam_ms.values())
