@@ -146,12 +146,13 @@ def rebalance_target_bytes(hg, k, stats, work, unit):
 
 
 def apply_move_bytes(stats, work):
-    """Algorithmic bytes of the apply kernel over one iteration (the Jet moves and every rebalancing
-    round's moves): per move its list entry (vertex, source/target), the partition write, c(v) and the
-    offsets; per incidence of a moved vertex the edge id and two phi read-modify-writes (4 B each way).
-    The bitmask toggles at phi crossings are not counted."""
-    moves = stats["approved"] + stats["rebalance_moves"]
-    return moves * (4 + 4 + 4 + 4 + 16) + work["moved_pins"] * (4 + 2 * 8)
+    """Algorithmic bytes of the apply kernels over one iteration: per Jet move its list entry (vertex,
+    source/target), the partition write, c(v) and the offsets; per rebalancing record (the rebalancing
+    apply reads every record and moves the selected ones) the record, and per rebalancing move the
+    partition write and the offsets; per incidence of a moved vertex the edge id and two phi
+    read-modify-writes (4 B each way).  The bitmask toggles at phi crossings are not counted."""
+    return (stats["approved"] * (4 + 4 + 4 + 4 + 16) + work["rebalance_evaluated"] * 16
+            + stats["rebalance_moves"] * (4 + 16) + work["moved_pins"] * (4 + 2 * 8))
 
 
 def ncu_traffic(workload, kernel="k_cand_light"):
@@ -580,7 +581,7 @@ def main():
     fam_roof = {"rebalance_targets": family_roofline("rebalance_targets",
                                                      "rebalancing targets (k_rbcand_light/k_rbcand_heavy)",
                                                      r["rb_bytes"], "k_rbcand_light"),
-                "apply": family_roofline("apply", "apply moves (k_apply)", r["apply_bytes"], "k_apply")}
+                "apply": family_roofline("apply", "apply moves (k_apply, k_rb_apply)", r["apply_bytes"], "k_apply")}
     dom_kernel = max(fam_roof, key=lambda f: prof[f]["ms"])  # the kernel with the most device time per step
     launches = sum(v["launches"] for v in prof.values())
     line = {

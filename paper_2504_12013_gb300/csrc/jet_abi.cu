@@ -136,10 +136,9 @@ int rebalance_loop(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   if (rc) return rc;
   if (!c->cnt_host->rb_any || c->params.max_rebalance_rounds <= 0) return JET_OK;
   for (;;) {
-    CKP(F_RB_CTL, launch_rb_prep(c, block_w), "rebalance prep");
     CKP(F_RB_TGT, launch_rebalance_candidates(c, part, phi), "rebalance targets");
     CKP(F_RB_SEL, launch_rb_select(c, part), "rebalance select");
-    CKP(F_APPLY, launch_apply(c, part, phi, block_w), "rebalance apply");
+    CKP(F_APPLY, launch_rb_apply(c, part, phi, block_w), "rebalance apply");
     CKP(F_RB_CTL, launch_rb_post(c, block_w), "rebalance post");
     rc = sync_counters(c);
     if (rc) return rc;
@@ -215,10 +214,9 @@ cudaError_t capture_iteration(jet_ctx *c, cudaStream_t s_main, cudaStream_t s_bo
         cudaSuccess)
       return e;
     c->stream = s_body;
-    cudaError_t eb = launch_rb_prep(c, bw);
-    if (eb == cudaSuccess) eb = launch_rebalance_candidates(c, part, phi);
+    cudaError_t eb = launch_rebalance_candidates(c, part, phi);
     if (eb == cudaSuccess) eb = launch_rb_select(c, part);
-    if (eb == cudaSuccess) eb = launch_apply(c, part, phi, bw);
+    if (eb == cudaSuccess) eb = launch_rb_apply(c, part, phi, bw);
     if (eb == cudaSuccess) eb = launch_rb_post(c, bw, h, 1);
     cudaGraph_t tmp = nullptr;
     e = cudaStreamEndCapture(s_body, &tmp);

@@ -237,8 +237,8 @@ cudaError_t launch_export_candidates(jet_ctx *c, int32_t *target, int32_t *gain,
 cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w);  // applies the move list
 cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond = 0,
                             int use_cond = 0);
-cudaError_t launch_rb_prep(jet_ctx *c, const int64_t *block_w);
 cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part);
+cudaError_t launch_rb_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w);  // applies the selection
 cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond = 0,
                            int use_cond = 0);
 cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *stats, int rebalance_only);

@@ -122,22 +122,10 @@ struct RbArgs {
   Counters *cnt;
 };
 
-// Any block above L_max?  One block of 256 threads (k <= 256).  In a CUDA
-// graph (use_cond) it also sets the condition of the rebalancing WHILE node.
-__global__ void k_rb_check(RbArgs a, cudaGraphConditionalHandle cond, int use_cond) {
-  const int b = threadIdx.x;
-  const bool over = b < a.k && a.bw[b] > a.Lmax;
-  const int any = __syncthreads_or(over);
-  if (b == 0) {
-    a.cnt->rb_any = any;
-    a.cnt->rb_done = !any;
-    if (use_cond) cudaGraphSetConditional(cond, (any && a.max_rounds > 0) ? 1u : 0u);
-  }
-}
-
-// Per-block state of the round: overloaded flag, excess, target capacity
-// (deadzone and L_max), cleared selection state.
-__global__ void k_rb_prep(RbArgs a) {
+// Per-block state of the next round: overloaded flag, excess, target
+// capacity (deadzone and L_max), cleared selection state and counters.  One
+// block of kMaxK threads, thread b for block b.
+__device__ __forceinline__ void rb_prep_blocks(const RbArgs &a) {
   const int b = threadIdx.x;
   if (b < a.k) {
     const long long bwb = a.bw[b];
@@ -156,6 +144,20 @@ __global__ void k_rb_prep(RbArgs a) {
     a.cnt->n_moves = 0;
     a.cnt->n_rec = 0;
   }
+}
+
+// Any block above L_max?  If so, the state of the first round.  In a CUDA
+// graph (use_cond) it also sets the condition of the rebalancing WHILE node.
+__global__ void k_rb_check(RbArgs a, cudaGraphConditionalHandle cond, int use_cond) {
+  const int b = threadIdx.x;
+  const bool over = b < a.k && a.bw[b] > a.Lmax;
+  const int any = __syncthreads_or(over);
+  if (b == 0) {
+    a.cnt->rb_any = any;
+    a.cnt->rb_done = !any;
+    if (use_cond) cudaGraphSetConditional(cond, (any && a.max_rounds > 0) ? 1u : 0u);
+  }
+  if (any) rb_prep_blocks(a);
 }
 
 template <class KT>
@@ -261,35 +263,97 @@ __global__ void __launch_bounds__(kPickThreads) k_rb_pick(RbArgs a, int lo, int 
   for (int x = x0 + lane; x < x1; x += 32) row[x] = 0ull;
 }
 
-// Every record with K(v) <= its block's threshold (or of an `all` block) moves.
+// Apply the selection: every record with K(v) <= its block's threshold (or of
+// an `all` block) moves v to its target.  A warp tests 32 records (one per
+// lane) and then applies the selected ones four at a time, kMoveLanes lanes
+// per move striding over I(v) as k_apply does; the moves are counted for the
+// round's statistics.
 template <class KT>
-__global__ void __launch_bounds__(256) k_rb_mark(RbArgs a) {
-  __shared__ unsigned s_wc[8];
-  __shared__ unsigned long long s_base;
-  const long long nrec = (long long)a.cnt->n_rec;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < nrec; base += (long long)gridDim.x * blockDim.x) {
-    const long long i = base + threadIdx.x;
+__global__ void __launch_bounds__(256) k_rb_apply(RbArgs r, MoveArgs a) {
+  __shared__ long long s_dw[kMaxK];
+  __shared__ int s_dc[kMaxK];
+  __shared__ unsigned long long s_moves, s_pins;
+  for (int b = threadIdx.x; b < a.k; b += blockDim.x) { s_dw[b] = 0; s_dc[b] = 0; }
+  if (threadIdx.x == 0) { s_moves = 0; s_pins = 0; }
+  __syncthreads();
+  const long long nrec = (long long)r.cnt->n_rec;
+  unsigned long long moves = 0, pins = 0;
+  const int lane = threadIdx.x & 31, grp = lane / kMoveLanes, sub = lane % kMoveLanes;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = w0 * 32; base < nrec; base += nw * 32) {
+    const long long i = base + lane;
     bool sel = false;
-    int v = 0, b = 0, t = 0;
+    int v = 0;
+    int32_t ct = 0;
     if (i < nrec) {
-      const int32_t ct = a.rb_ct[i];
-      b = (ct >> 8) & 255;
-      t = ct & 255;
-      v = a.rb_v[i];
-      const RbBlock &r = a.rbb[b];
-      sel = r.all || rb_full_key<KT>(a.rb_hi[i], v, a.vbits) <= rb_prefix<KT>(r);
+      ct = r.rb_ct[i];
+      v = r.rb_v[i];
+      const RbBlock &rb = r.rbb[(ct >> 8) & 255];
+      KT pre;
+      if constexpr (sizeof(KT) > 8) pre = ((KT)rb.pre_hi << 64) | (KT)rb.pre_lo;
+      else pre = (KT)rb.pre_lo;
+      sel = rb.all || rb_full_key<KT>(r.rb_hi[i], v, r.vbits) <= pre;
     }
-    const unsigned long long pos = block_append(sel, &a.cnt->n_moves, s_wc, &s_base);
-    if (sel) {
-      a.mv_v[pos] = v;
-      a.mv_st[pos] = (uint32_t)b | ((uint32_t)t << 16);
+    unsigned bal = __ballot_sync(kFull, sel);
+    while (bal) {
+      const int nsel = __popc(bal);
+      const int src = grp < nsel ? (int)__fns(bal, 0, grp + 1) : -1;  // this group's record lane
+      const int mv = __shfl_sync(kFull, v, src < 0 ? 0 : src);
+      const int32_t mct = __shfl_sync(kFull, ct, src < 0 ? 0 : src);
+      if (src >= 0) {
+        const int s = (mct >> 8) & 255, t = mct & 255;
+        const int64_t j0 = a.vptr[mv], j1 = a.vptr[mv + 1];
+        if (sub == 0) {
+          a.part[mv] = t;
+          const int c = (mct >> 16) & 0xffff;
+          atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[s]), (unsigned long long)(-(long long)c));
+          atomicAdd(reinterpret_cast<unsigned long long *>(&s_dw[t]), (unsigned long long)c);
+          atomicSub(&s_dc[s], 1);
+          atomicAdd(&s_dc[t], 1);
+          ++moves;
+          pins += (unsigned long long)(j1 - j0);
+        }
+        const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
+        for (int64_t j = j0 + sub; j < j1; j += kMoveLanes) {
+          const int64_t e = a.inc[j];
+          const int os = atomicSub(&a.phi[e * a.k + s], 1);  // os -> os - 1
+          const int ot = atomicAdd(&a.phi[e * a.k + t], 1);  // ot -> ot + 1
+          uint32_t *row = a.mask + e * 2 * a.kwp;
+          if (os == 1) atomicXor(&row[s >> 5], sbit);           // 1 -> 0
+          if (os == 2) atomicXor(&row[a.kwp + (s >> 5)], sbit);  // 2 -> 1
+          if (ot == 0) atomicXor(&row[t >> 5], tbit);           // 0 -> 1
+          if (ot == 1) atomicXor(&row[a.kwp + (t >> 5)], tbit);  // 1 -> 2
+        }
+      }
+      // drop the (up to) 32 / kMoveLanes records just applied
+      for (int q = 0; q < 32 / kMoveLanes && bal; ++q) bal &= bal - 1;
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    moves += __shfl_xor_sync(kFull, moves, o);
+    pins += __shfl_xor_sync(kFull, pins, o);
+  }
+  if (lane == 0) {
+    if (moves) atomicAdd(&s_moves, moves);
+    if (pins) atomicAdd(&s_pins, pins);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_moves) atomicAdd(&r.cnt->n_moves, s_moves);
+    if (s_pins) atomicAdd(&r.cnt->w_apply_pins, s_pins);
+  }
+  for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
+    if (s_dw[b]) add_i64(reinterpret_cast<long long *>(&a.bw[b]), s_dw[b]);
+    if (s_dc[b]) atomicAdd(&a.vcount[b], s_dc[b]);
   }
 }
 
 // End of a round: count it, and stop if nothing moved, nothing is overloaded
-// any more, or the round cap is reached.
+// any more, or the round cap is reached; otherwise the state of the next round.
 __global__ void k_rb_post(RbArgs a, cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ int s_done;
   const int b = threadIdx.x;
   const bool over = b < a.k && a.bw[b] > a.Lmax;
   const int any = __syncthreads_or(over);
@@ -300,8 +364,11 @@ __global__ void k_rb_post(RbArgs a, cudaGraphConditionalHandle cond, int use_con
     a.cnt->rb_any = any;
     const int done = (moved == 0) || !any || (a.cnt->rb_rounds >= a.max_rounds);
     a.cnt->rb_done = done;
+    s_done = done;
     if (use_cond) cudaGraphSetConditional(cond, done ? 0u : 1u);
   }
+  __syncthreads();
+  if (!s_done) rb_prep_blocks(a);
 }
 
 __global__ void k_stats(const int64_t *bw, int32_t k, long long Lmax, const Counters *cnt, jet_round_stats *out,
@@ -410,12 +477,6 @@ cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w, cudaGraphConditi
   return cudaGetLastError();
 }
 
-cudaError_t launch_rb_prep(jet_ctx *c, const int64_t *block_w) {
-  k_rb_prep<<<1, kMaxK, 0, c->stream>>>(rb_args(c, block_w, nullptr));
-  ++c->kernel_launches;
-  return cudaGetLastError();
-}
-
 template <class KT>
 void rb_select_levels(jet_ctx *c, const RbArgs &a) {
   const int g = grid_for(c->n, 256, c->launch_sms);
@@ -430,8 +491,6 @@ void rb_select_levels(jet_ctx *c, const RbArgs &a) {
     ++c->kernel_launches;
     hi = lo;
   }
-  k_rb_mark<KT><<<g, 256, 0, c->stream>>>(a);
-  ++c->kernel_launches;
 }
 
 cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part) {
@@ -439,6 +498,17 @@ cudaError_t launch_rb_select(jet_ctx *c, const int32_t *part) {
   const RbArgs a = rb_args(c, nullptr, part);
   if (a.tbits <= 64) rb_select_levels<unsigned long long>(c, a);
   else rb_select_levels<u128>(c, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rb_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
+  if (c->n == 0) return cudaSuccess;
+  const RbArgs r = rb_args(c, block_w, part);
+  const MoveArgs a = move_args(c, part, phi, block_w);
+  const int g = grid_for(c->n, 256, c->launch_sms, 8);
+  if (r.tbits <= 64) k_rb_apply<unsigned long long><<<g, 256, 0, c->stream>>>(r, a);
+  else k_rb_apply<u128><<<g, 256, 0, c->stream>>>(r, a);
+  ++c->kernel_launches;
   return cudaGetLastError();
 }
 
