@@ -47,11 +47,39 @@ struct AbArgs {
   Counters *cnt;
 };
 
+// Thread per edge (|e| <= 8), software-pipelined over the thread's edges:
+// while edge j is decided, the pins of edge j+1, the offsets of edge j+2 and
+// the id of edge j+3 are in flight.
 __global__ void __launch_bounds__(256) k_ab_tiny(AbArgs a) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nlist; i += gridDim.x * blockDim.x) {
-    const int e = a.elist[i];
-    const int64_t p0 = a.eptr[e];
-    const int sz = (int)(a.eptr[e + 1] - p0);
+  const int stride = gridDim.x * blockDim.x;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  auto edge_at = [&](long long i) -> int { return i < a.nlist ? a.elist[i] : -1; };
+  int e3 = edge_at(i0 + 2ll * stride);
+  int e2 = edge_at(i0 + (long long)stride);
+  int64_t p2 = e2 >= 0 ? a.eptr[e2] : 0;
+  int sz2 = e2 >= 0 ? (int)(a.eptr[e2 + 1] - p2) : 0;
+  int e1 = edge_at(i0), sz1 = 0;
+  int pins1[kTinyEdge];
+  {
+    const int64_t p1 = e1 >= 0 ? a.eptr[e1] : 0;
+    sz1 = e1 >= 0 ? (int)(a.eptr[e1 + 1] - p1) : 0;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q) pins1[q] = q < sz1 ? a.pins[p1 + q] : 0;
+  }
+  for (long long i = i0; i < a.nlist; i += stride) {
+    const int e = e1, sz = sz1;
+    int pin[kTinyEdge];
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q) pin[q] = pins1[q];
+    // advance the pipeline: first used in the next iteration
+    const int e4 = edge_at(i + 3ll * stride);
+    const int64_t p3 = e3 >= 0 ? a.eptr[e3] : 0;
+    const int sz3 = e3 >= 0 ? (int)(a.eptr[e3 + 1] - p3) : 0;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q) pins1[q] = q < sz2 ? a.pins[p2 + q] : 0;
+    e1 = e2; sz1 = sz2;
+    e2 = e3; p2 = p3; sz2 = sz3;
+    e3 = e4;
     uint64_t key[kTinyEdge];
     uint32_t st[kTinyEdge];  // s | t << 8 | 1 << 16 for a candidate; block | 1 << 17 for another pin
     int vid[kTinyEdge];
@@ -62,7 +90,7 @@ __global__ void __launch_bounds__(256) k_ab_tiny(AbArgs a) {
       st[q] = 0;
       vid[q] = 0;
       if (q < sz) {
-        const int v = a.pins[p0 + q];
+        const int v = pin[q];
         const uint64_t r = a.cand[v];
         vid[q] = v;
         if (r) {
@@ -110,7 +138,7 @@ __global__ void __launch_bounds__(256) k_ab_tiny(AbArgs a) {
 
 constexpr int kAbWarps = 8;
 
-// Warp per edge (8 < |e| <= 2048): the per-block form of the replay in
+// Warp per edge (32 < |e| <= 128): the per-block form of the replay in
 // shared memory, one table per warp: max key of the departures and min key
 // of the arrivals of every block, and the blocks holding a non-candidate pin.
 // A key is never 0 (its high word is INT32_MAX - gain >= 1), so max = 0 means
