@@ -95,6 +95,8 @@ def load(source=None):
             lib.ojet_refine_round.argtypes = [H, Pp, i32, i32, I32P, I32P, I64P, U8P, S]
             lib.ojet_refine_round.restype = None
             lib.ojet_refine.argtypes = [H, Pp, I32P, i32, i32, I32P, I64P, I64P]; lib.ojet_refine.restype = i64
+            lib.ojet_quotient.argtypes = [H, i32, I32P, U8P]; lib.ojet_quotient.restype = None
+            lib.ojet_schedule.argtypes = [i32, U8P, I32P, I32P, I32P]; lib.ojet_schedule.restype = i64
             _libs[key] = lib
     return _libs[key]
 
@@ -210,6 +212,18 @@ class Oracle:
                                          _p(phi, I32P), _p(bw, I64P), ctypes.byref(moves))
         return rounds, moves.value
 
+    # Section 5 (matching schedule)
+    def quotient(self, k, phi):
+        """Quotient graph adjacency (k x k uint8) of the partition whose pin counts are phi."""
+        phi = np.ascontiguousarray(phi, dtype=np.int32)
+        q = np.zeros((k, k), np.uint8)
+        self.lib.ojet_quotient(ctypes.byref(self.h), k, _p(phi, I32P), _p(q, U8P))
+        return q
+
+    def schedule(self, qadj):
+        """Rounds of maximal matchings covering the quotient edges: (pairs int32[p, 2], round int32[p], rounds)."""
+        return schedule(qadj, self.lib)
+
     # Algorithm 1
     def refine_round(self, params: Params, tau, part, phi, bw, locked):
         st = OStats()
@@ -235,3 +249,16 @@ class State:
         self.phi = np.ascontiguousarray(phi)
         self.bw = bw
         self.locked = np.zeros(orc.hg.n, dtype=np.uint8)
+
+
+def schedule(qadj, lib=None):
+    """The matching schedule (Section 5) of a quotient graph given as a k x k 0/1 matrix."""
+    lib = lib or load()
+    q = np.ascontiguousarray(qadj, dtype=np.uint8)
+    k = q.shape[0]
+    cap = max(k * (k - 1) // 2, 1)
+    pairs = np.zeros(2 * cap, np.int32)
+    rnd = np.zeros(cap, np.int32)
+    nr = ctypes.c_int32(0)
+    npairs = lib.ojet_schedule(k, _p(q, U8P), _p(pairs, I32P), _p(rnd, I32P), ctypes.byref(nr))
+    return pairs[: 2 * npairs].reshape(-1, 2), rnd[:npairs], nr.value

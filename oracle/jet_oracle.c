@@ -13,6 +13,7 @@
  *   Section 4.2, Algorithm 2            hypergraph afterburner (sort + replay)
  *   Section 4.3                         deterministic rebalancing, deadzone, heavy vertices
  *   Section 7.2                         three temperatures 0.75 -> 0, 8 iterations
+ *   Section 5 (matching schedule)       quotient graph, rounds of maximal matchings
  * Readings where the paper is silent or ambiguous (each marked READING below):
  *   R1  blocks are 0-based, [k] = {0..k-1}.
  *   R2  L_max = floor((1+eps) * ceil(c(V)/k)), eps = eps_num/eps_den exactly.
@@ -45,6 +46,8 @@
  *       the best balanced partition seen so far; at the end of each temperature
  *       phase the best balanced partition is restored (rollback).
  *   R12 an empty hyperedge contributes 0 to (lambda-1).
+ *   R17 the matching schedule of the quotient graph (Section 5): see
+ *       ojet_schedule.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -458,4 +461,86 @@ int64_t ojet_refine(const ojet_hg *h, const ojet_params *p, const int32_t *tau_p
   if (objective_out) *objective_out = ojet_connectivity(h, k, phi);
   free(phi); free(bw); free(locked); free(best);
   return iterations;
+}
+
+/*
+ * Section 5 ("K-Way Refinement: Matching Schedule").  The quotient graph Q
+ * has the k blocks as vertices and an edge {i, j} (i != j) when some
+ * hyperedge has pins in both V_i and V_j, i.e. phi_e(i) >= 1 and
+ * phi_e(j) >= 1.  qadj[i*k + j] = qadj[j*k + i] = 1 for those pairs, by
+ * definition from phi.
+ */
+void ojet_quotient(const ojet_hg *h, int32_t k, const int32_t *phi, uint8_t *qadj) {
+  memset(qadj, 0, (size_t)k * (size_t)k);
+  for (int32_t e = 0; e < h->m; ++e) {
+    const int32_t *row = phi + (size_t)e * (size_t)k;
+    for (int32_t i = 0; i < k; ++i) {
+      if (row[i] < 1) continue;
+      for (int32_t j = 0; j < k; ++j)
+        if (j != i && row[j] >= 1) qadj[(size_t)i * k + j] = 1;
+    }
+  }
+}
+
+/*
+ * Section 5 ("K-Way Refinement: Matching Schedule"): block pairs are
+ * scheduled in rounds; each round is a maximal matching in the quotient
+ * edges not scheduled yet, and rounds repeat until every quotient edge is
+ * scheduled.  Edges of high-degree blocks go first.
+ * READING R17: each round takes the blocks in order of their degree in the
+ * remaining quotient graph at the start of the round (descending, ties to
+ * the smaller id); a block that is still unmatched is paired with its
+ * unmatched remaining neighbour of the largest such degree (ties to the
+ * smaller id).  Output in selection order: pairs[2p] = the visited block,
+ * pairs[2p+1] = its partner, round_of[p] = the round.  Returns the number of
+ * pairs; *n_rounds gets the number of rounds.
+ */
+int64_t ojet_schedule(int32_t k, const uint8_t *qadj, int32_t *pairs, int32_t *round_of, int32_t *n_rounds) {
+  uint8_t *rem = (uint8_t *)malloc((size_t)k * (size_t)k + 1);
+  int32_t *deg = (int32_t *)malloc(sizeof(int32_t) * (size_t)k + 4);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)k + 4);
+  uint8_t *matched = (uint8_t *)malloc((size_t)k + 1);
+  memcpy(rem, qadj, (size_t)k * (size_t)k);
+  for (int32_t i = 0; i < k; ++i) rem[(size_t)i * k + i] = 0;
+  int64_t np = 0;
+  int32_t round = 0;
+  for (;;) {
+    int64_t left = 0;
+    for (int32_t i = 0; i < k; ++i) {
+      deg[i] = 0;
+      for (int32_t j = 0; j < k; ++j) deg[i] += rem[(size_t)i * k + j];
+      left += deg[i];
+      order[i] = i;
+    }
+    if (left == 0) break;
+    /* insertion sort by (degree desc, id asc) */
+    for (int32_t x = 1; x < k; ++x) {
+      const int32_t b = order[x];
+      int32_t y = x - 1;
+      while (y >= 0 && (deg[order[y]] < deg[b] || (deg[order[y]] == deg[b] && order[y] > b))) {
+        order[y + 1] = order[y];
+        --y;
+      }
+      order[y + 1] = b;
+    }
+    memset(matched, 0, (size_t)k);
+    for (int32_t x = 0; x < k; ++x) {
+      const int32_t i = order[x];
+      if (deg[i] == 0 || matched[i]) continue;
+      int32_t best = -1;
+      for (int32_t j = 0; j < k; ++j)
+        if (rem[(size_t)i * k + j] && !matched[j] && (best < 0 || deg[j] > deg[best])) best = j;
+      if (best < 0) continue;
+      matched[i] = matched[best] = 1;
+      rem[(size_t)i * k + best] = rem[(size_t)best * k + i] = 0;
+      pairs[2 * np] = i;
+      pairs[2 * np + 1] = best;
+      round_of[np] = round;
+      ++np;
+    }
+    ++round;
+  }
+  if (n_rounds) *n_rounds = round;
+  free(rem); free(deg); free(order); free(matched);
+  return np;
 }

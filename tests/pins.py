@@ -496,6 +496,86 @@ def medium_instances():
 
 # ------------------------------------------------------------------ suite
 
+# ---------------------------------------------------------------- Section 5: matching schedule
+def schedule_hand_example():
+    """Quotient graph on 4 blocks with edges {0,1}, {1,2}, {2,3}, {1,3}; expected schedule by hand.
+
+    Round 0: degrees 0:1, 1:3, 2:2, 3:2, so block 1 goes first; its unmatched neighbours of the
+    largest degree are 2 and 3 (both 2), the smaller id wins: (1, 2).  Blocks 3 and 0 then find no
+    unmatched neighbour.  Round 1: remaining {0,1}, {2,3}, {1,3}; degrees 0:1, 1:2, 2:1, 3:2; block 1
+    first, its neighbours 0 (degree 1) and 3 (degree 2): (1, 3); 0 and 2 find nothing.  Round 2:
+    {0,1} and {2,3}, all degrees 1: (0, 1) then (2, 3).
+    """
+    q = np.zeros((4, 4), np.uint8)
+    for i, j in ((0, 1), (1, 2), (2, 3), (1, 3)):
+        q[i, j] = q[j, i] = 1
+    return q, [(1, 2), (1, 3), (0, 1), (2, 3)], [0, 1, 2, 2], 3
+
+
+def check_schedule_hand(orc):
+    q, want_pairs, want_rounds, want_n = schedule_hand_example()
+    pairs, rnd, nr = orc.schedule(q)
+    assert [tuple(int(x) for x in p) for p in pairs] == want_pairs, pairs
+    assert list(rnd) == want_rounds and nr == want_n, (rnd, nr)
+
+
+def check_quotient(orc, hg, k, part):
+    """Q from phi equals the block pairs that share a hyperedge, counted from the partition."""
+    phi, _ = orc.pincounts(k, part)
+    q = orc.quotient(k, phi)
+    want = np.zeros((k, k), np.uint8)
+    for e in range(hg.m):
+        bl = sorted({int(part[v]) for v in hg.edge(e)})
+        for i in bl:
+            for j in bl:
+                if i != j:
+                    want[i, j] = 1
+    assert np.array_equal(q, want)
+    return q
+
+
+def check_schedule_invariants(orc, q):
+    """Every quotient edge exactly once; each round a matching that is maximal in the edges left at its
+    start; each round opens with a block of the largest remaining degree (smallest such id)."""
+    k = q.shape[0]
+    pairs, rnd, nr = orc.schedule(q)
+    edges = {(i, j) for i in range(k) for j in range(i + 1, k) if q[i, j]}
+    got = [tuple(sorted((int(a), int(b)))) for a, b in pairs]
+    assert len(got) == len(set(got)) and set(got) == edges
+    assert list(rnd) == sorted(rnd) and (nr == (int(rnd[-1]) + 1 if len(rnd) else 0))
+    remaining = set(edges)
+    for r in range(nr):
+        this = [got[x] for x in range(len(got)) if rnd[x] == r]
+        used = [b for p in this for b in p]
+        assert len(used) == len(set(used)), "a block in two pairs of one round"
+        deg = np.zeros(k, np.int64)
+        for i, j in remaining:
+            deg[i] += 1
+            deg[j] += 1
+        first = int(pairs[list(rnd).index(r)][0])
+        assert deg[first] == deg.max() and first == int(np.argmax(deg)), (r, first)
+        free = set(range(k)) - set(used)
+        assert not any(i in free and j in free for i, j in remaining - set(this)), "round not maximal"
+        remaining -= set(this)
+    assert not remaining
+
+
+def random_quotients(count=8, seed=71):
+    u = synth.stream_u64(seed, 4096)
+    out = []
+    for t in range(count):
+        k = 2 + int(u[t] % np.uint64(39))
+        dens = 1 + int(u[100 + t] % np.uint64(9))  # percent-in-ten of edges present
+        bits = synth.stream_u64(seed + 17 * t + 1, k * k)
+        q = np.zeros((k, k), np.uint8)
+        for i in range(k):
+            for j in range(i + 1, k):
+                if int(bits[i * k + j] % np.uint64(10)) < dens:
+                    q[i, j] = q[j, i] = 1
+        out.append(q)
+    return out
+
+
 def run_all(orc_cls, params_cls, source=None):
     """Every pin; raises AssertionError on the first failure."""
     def O(hg):
@@ -525,3 +605,8 @@ def run_all(orc_cls, params_cls, source=None):
         check_rebalance_loop(o, params, hg, part)
         check_refine_round_stats(o, params, hg, part, (3, 4))
         check_refine_loop(o, params, hg, part, ((3, 4), (3, 8), (0, 1)), 3)
+        check_schedule_invariants(o, check_quotient(o, hg, k, part))
+    o = O(hand_example()[0])
+    check_schedule_hand(o)
+    for q in random_quotients():
+        check_schedule_invariants(o, q)

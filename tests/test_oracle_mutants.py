@@ -60,6 +60,12 @@ MUTANTS = {
     "loop_no_locking": ("for (int32_t v = 0; v < n; ++v) locked[v] = approved[v];", ""),
     "loop_locks_kept_across_phases": ("    memset(locked, 0, nn);\n    int32_t it = 0;", "    int32_t it = 0;"),
     "loop_counter_not_reset": ("        memcpy(best, part, sizeof(int32_t) * (size_t)n);\n        it = 0;", "        memcpy(best, part, sizeof(int32_t) * (size_t)n);"),
+    # Section 5 (matching schedule)
+    "quotient_needs_two_pins": ("if (j != i && row[j] >= 1) qadj[(size_t)i * k + j] = 1;", "if (j != i && row[j] >= 2) qadj[(size_t)i * k + j] = 1;"),
+    "schedule_degree_ascending": ("while (y >= 0 && (deg[order[y]] < deg[b] ||", "while (y >= 0 && (deg[order[y]] > deg[b] ||"),
+    "schedule_tie_larger_id": ("(deg[order[y]] == deg[b] && order[y] > b))) {", "(deg[order[y]] == deg[b] && order[y] < b))) {"),
+    "schedule_partner_lowest_degree": ("(best < 0 || deg[j] > deg[best])) best = j;", "(best < 0 || deg[j] < deg[best])) best = j;"),
+    "schedule_one_pair_per_round": ("      round_of[np] = round;\n      ++np;\n    }", "      round_of[np] = round;\n      ++np;\n      break;\n    }"),
     "round_always_rebalances_once": ("  if (over) st->rebalance_rounds = ojet_rebalance(h, p, part, phi, bw, &st->rebalance_moves);",
                                      "  if (over) { st->rebalance_rounds = 1; ojet_rebalance_round(h, p, part, phi, bw, NULL, NULL); }"),
 }

@@ -164,3 +164,31 @@ def test_refine_random_10k_invariants():
     assert all(int(x) >= oracle.ITERATION_LIMIT for x in phase)
     p2 = part.copy()
     assert o.refine(params, p2)[:2] == (iters, obj) and np.array_equal(p, p2)
+
+
+# ---------------------------------------------------------------- Section 5: matching schedule
+def test_schedule_hand_example():
+    pins.check_schedule_hand(make(pins.hand_example()[0]))
+
+
+@pytest.mark.parametrize("idx", range(len(INSTANCES)))
+def test_quotient_and_schedule_of_partitions(idx):
+    hg, k, part = INSTANCES[idx]
+    o = make(hg)
+    pins.check_schedule_invariants(o, pins.check_quotient(o, hg, k, part))
+
+
+@pytest.mark.parametrize("q_idx", range(8))
+def test_schedule_invariants_random_quotients(q_idx):
+    q = pins.random_quotients()[q_idx]
+    pins.check_schedule_invariants(make(pins.hand_example()[0]), q)
+
+
+def test_schedule_of_a_complete_quotient():
+    """K_k: all k(k-1)/2 pairs are scheduled, in at least k - 1 rounds (every block has k - 1 quotient
+    edges and meets at most one per round)."""
+    for k in (2, 4, 8, 16):
+        q = np.ones((k, k), np.uint8) - np.eye(k, dtype=np.uint8)
+        pairs, rnd, nr = oracle.schedule(q)
+        assert len(pairs) == k * (k - 1) // 2
+        assert nr >= k - 1
