@@ -267,13 +267,31 @@ def run_gpu(args, rank, world):
         prof = prof_eager_timed
     jet.jet_profile_enable(ctx, False)
     assert trace[-1] == final_stats, "replay diverged from the timed run"
+    sched = schedule_timing(jet, ctx, st, stream, dev)
 
     result = {"ms": ms, "prof": prof, "prof_timed": prof_timed, "model_bytes": model_bytes, "rb_bytes": rb_bytes,
               "apply_bytes": apply_bytes,
-              "trace": trace,
+              "trace": trace, "schedule": sched,
               "clocks": clk.summary(), "hg": hg, "k": k, "part0": part0, "desc": desc, "dev": dev}
     ctx.close()
     return result
+
+
+def schedule_timing(jet, ctx, st, stream, dev):
+    """Matching schedule of the quotient graph (Section 5) of the partition after the timed steps: the
+    quotient kernel over every edge bitmask row plus the one-block schedule kernel, device time."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(3):
+        ev0.record(stream)
+        pairs, rnd, nr = jet.jet_quotient_schedule(ctx, st.phi)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(ev0.elapsed_time(ev1))
+    return {"ms": min(times), "pairs": int(len(pairs)), "rounds": int(nr),
+            "what": "quotient graph of the partition after the timed steps and its rounds of maximal matchings "
+                    "(jet_quotient_schedule, Section 5)"}
 
 
 def run_e2e(args, hg, k, part0, dev):
@@ -622,6 +640,7 @@ def main():
         "cpu_baseline": cpu,
         "batched": batched,
         "served": served,
+        "matching_schedule": r["schedule"],
         "trace_first_steps": r["trace"][:3],
     }
     print(json.dumps(line), flush=True)

@@ -334,6 +334,25 @@ int jet_profile_enable(jet_ctx *ctx, int enable);
 int jet_profile_read(jet_ctx *ctx, double *ms_out, int64_t *calls_out, int64_t *launches_out, int reset);
 
 /*
+ * Matching schedule of k-way refinement (Section 5, "K-Way Refinement:
+ * Matching Schedule"): the quotient graph Q of the partition whose pin
+ * counts are phi (device, m*k) has the blocks as vertices and an edge {i, j}
+ * when some hyperedge has pins in both V_i and V_j.  The block pairs of Q are
+ * scheduled in rounds; each round is a maximal matching in the pairs not
+ * scheduled yet, so a block takes part in one two-way refinement at a time.
+ * Per round the blocks go in order of their degree among the unscheduled
+ * pairs (descending, ties to the smaller id), and a block still unmatched
+ * takes its unmatched neighbour of the largest such degree (ties to the
+ * smaller id).  Writes, in selection order, pairs[2p], pairs[2p+1] (device
+ * int32, room for k(k-1) entries) = the block whose turn it was and its
+ * partner, and round_of[p] (device int32, room for k(k-1)/2 entries);
+ * *n_pairs and *n_rounds (HOST) get the counts.  Synchronizes.  The two-way
+ * flow refinements themselves are not part of this library.
+ */
+int jet_quotient_schedule(jet_ctx *ctx, const int32_t *phi, int32_t *pairs, int32_t *round_of, int32_t *n_pairs,
+                          int32_t *n_rounds);
+
+/*
  * Work counts of the last jet_refine_round or jet_rebalance call (for byte
  * models of the kernels; always counted, no events).  Synchronizes.  Writes
  * up to n (<= 4) entries of out (HOST): [0] vertices of overloaded blocks

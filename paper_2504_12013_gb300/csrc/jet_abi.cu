@@ -472,7 +472,7 @@ void jet_ctx_destroy(jet_ctx *c) {
   cudaStreamSynchronize(c->stream);
   void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
                  c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->vheavy, c->stats_scratch,
-                 c->ab_seg, c->ab_slot_edge, c->ab_tab, c->ab_nm};
+                 c->ab_seg, c->ab_slot_edge, c->ab_tab, c->ab_nm, c->sched_q, c->sched_counts};
   for (void *p : dev) dfree(c, p);
   cudaStreamSynchronize(c->stream);
   for (auto &g : c->graphs) {
@@ -668,6 +668,26 @@ int jet_profile_read(jet_ctx *c, double *ms_out, int64_t *calls_out, int64_t *la
       c->fam_launches[f] = 0;
     }
   }
+  return JET_OK;
+}
+
+int jet_quotient_schedule(jet_ctx *c, const int32_t *phi, int32_t *pairs, int32_t *round_of, int32_t *n_pairs,
+                          int32_t *n_rounds) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (c->m > 0 && !phi) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
+  if (!pairs || !round_of || !n_pairs || !n_rounds) return fail(c, JET_ERR_INVALID_ARG, "NULL output");
+  if (!c->sched_q) {
+    CK(dalloc(c, &c->sched_q, (size_t)c->k * c->kwp), "schedule workspace");
+    CK(dalloc(c, &c->sched_counts, 2), "schedule workspace");
+  }
+  CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
+  CKP(F_OTHER, launch_quotient_schedule(c, c->sched_q, pairs, round_of, c->sched_counts), "matching schedule");
+  int32_t cnt[2];
+  CK(cudaMemcpyAsync(cnt, c->sched_counts, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream), "schedule counts");
+  CK(cudaStreamSynchronize(c->stream), "synchronize");
+  *n_pairs = cnt[0];
+  *n_rounds = cnt[1];
   return JET_OK;
 }
 

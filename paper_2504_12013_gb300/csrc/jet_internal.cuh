@@ -181,6 +181,8 @@ struct jet_ctx {
   };
   RefineGraph refine_graph;
   jet::RefineState *rstate = nullptr;      // device: loop state and summary of jet_refine
+  uint32_t *sched_q = nullptr;             // quotient graph bits (k x KWP) of jet_quotient_schedule
+  int32_t *sched_counts = nullptr;         // its pair and round counts (device)
   jet_refine_result *res_host = nullptr;   // pinned copy of the summary
 
   // profiling: kernel launches (always counted) and event pairs per family
@@ -243,6 +245,8 @@ cudaError_t launch_rb_post(jet_ctx *c, const int64_t *block_w, cudaGraphConditio
                            int use_cond = 0);
 cudaError_t launch_stats(jet_ctx *c, const int64_t *block_w, jet_round_stats *stats, int rebalance_only);
 cudaError_t launch_rollback_moves(jet_ctx *c, const int32_t *part, const int32_t *best, const int *enable = nullptr);
+// matching schedule of k-way refinement (k_sched.cu)
+cudaError_t launch_quotient_schedule(jet_ctx *c, uint32_t *qbits, int32_t *pairs, int32_t *round_of, int32_t *counts);
 
 // Block-wide append to a global list: every thread of the block calls it (same
 // iteration); each thread with `sel` gets a distinct slot.  One atomicAdd per

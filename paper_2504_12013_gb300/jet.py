@@ -27,7 +27,7 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_set_graph_mode", "jet_batch_create", "jet_batch_destroy", "jet_batch_last_error",
            "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune",
            "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
-           "jet_server_last_error", "jet_server_destroy", "jet_profile_work")
+           "jet_server_last_error", "jet_server_destroy", "jet_profile_work", "jet_quotient_schedule")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -108,6 +108,7 @@ def load_library():
             lib.jet_block_weights_noalloc.argtypes = [_P, _P, i32, i32, _P, _P, _P]
             lib.jet_set_graph_mode.argtypes = [_P, ctypes.c_int]
             lib.jet_profile_work.argtypes = [_P, pp(i64), i32]
+            lib.jet_quotient_schedule.argtypes = [_P, _P, _P, _P, pp(i32), pp(i32)]
             lib.jet_batch_create.argtypes = [pp(_P), pp(_P), i32, _P]
             lib.jet_batch_destroy.argtypes = [_P]
             lib.jet_batch_destroy.restype = None
@@ -312,6 +313,21 @@ def jet_profile_read(ctx: Ctx, reset: bool = True) -> dict:
     launches = (ctypes.c_int64 * n)()
     _check(load_library().jet_profile_read(ctx.handle, ms, calls, launches, 1 if reset else 0), ctx)
     return {f: {"ms": ms[i], "calls": calls[i], "launches": launches[i]} for i, f in enumerate(PROF_FAMILIES)}
+
+
+def jet_quotient_schedule(ctx: Ctx, phi):
+    """Matching schedule of the quotient graph: (pairs int32[p, 2], round int32[p], rounds) on the host."""
+    import torch
+    k = ctx.k
+    cap = max(k * (k - 1) // 2, 1)
+    dev = phi.device
+    pairs = torch.zeros(2 * cap, dtype=torch.int32, device=dev)
+    rnd = torch.zeros(cap, dtype=torch.int32, device=dev)
+    npairs, nr = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().jet_quotient_schedule(ctx.handle, _ptr(phi, torch.int32, "phi"), _ptr(pairs), _ptr(rnd),
+                                                ctypes.byref(npairs), ctypes.byref(nr)), ctx)
+    p = npairs.value
+    return pairs[: 2 * p].cpu().numpy().reshape(-1, 2), rnd[:p].cpu().numpy(), nr.value
 
 
 WORK_FIELDS = ("rebalance_over", "rebalance_evaluated", "rebalance_evaluated_pins", "moved_pins")
