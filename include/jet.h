@@ -240,6 +240,25 @@ int jet_batch_tune(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, in
                    float *ms_out);
 
 /*
+ * Uncoarsening (the refinement phase of the multilevel scheme, §7.2: the
+ * partition of the coarsest level is projected level by level to the input
+ * and refined with Algorithm 1 at every level) as ONE CUDA graph.
+ * levels[0..n_levels) are contexts of the hierarchy's hypergraphs from the
+ * coarsest (0) to the finest, all with the same k; maps[l] (device int32, one
+ * entry per vertex of level l+1) gives each vertex of level l+1 its vertex of
+ * level l.  part[0] (device) holds the coarsest level's initial partition;
+ * part[l] for l >= 1 receive the projections; every part[l], phi[l],
+ * block_w[l] (HOST arrays of DEVICE pointers, sized as for jet_refine) end
+ * refined.  results (HOST, n_levels entries, may be NULL) receive the
+ * per-level summaries.  `stream` runs the graph.  Synchronizes.  A map value
+ * outside [0, n of level l) is JET_ERR_DATA; other errors as jet_refine.
+ * The hierarchy itself (coarsening, Section 6) is the caller's.
+ */
+int jet_uncoarsen(jet_ctx *const *levels, int32_t n_levels, const int32_t *const *maps, const int32_t *tau_pairs,
+                  int32_t n_tau, int32_t limit, int32_t *const *part, int32_t *const *phi, int64_t *const *block_w,
+                  jet_refine_result *results, void *stream);
+
+/*
  * Serving: a request loop that refines submitted jobs (each = jet_refine_host
  * on the job's host buffers: upload, Algorithm 1 as one graph, download) with
  * up to max_active jobs on the device at once, each on its own stream and

@@ -59,6 +59,7 @@ const char *data_error_text(int err) {
   if (err & kErrIncRange) return "an incidence (edge id) is outside [0, m)";
   if (err & kErrTranspose) return "vptr/inc is not the transpose of eptr/pins (degree mismatch)";
   if (err & kErrPartRange) return "a partition value is outside [0, k)";
+  if (err & kErrMapRange) return "a hierarchy map value is outside the coarser level's vertex range";
   return "data error";
 }
 

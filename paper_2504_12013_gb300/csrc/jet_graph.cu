@@ -77,6 +77,22 @@ __global__ void k_refine_end(const jet_round_stats *st, RefineState *rs) {
   rs->res.balanced = st->imbalanced ? 0 : 1;
 }
 
+// Projection of a partition to the next finer level of a hierarchy:
+// part_fine[v] = part_coarse[map[v]]; a map value outside [0, n_coarse) is
+// reported as a data error and gives block 0.
+__global__ void k_project(const int32_t *part_coarse, const int32_t *map, int32_t n_fine, int32_t n_coarse,
+                          int32_t *part_fine, Counters *cnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_fine; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = map[v];
+    if ((unsigned)u < (unsigned)n_coarse) {
+      part_fine[v] = part_coarse[u];
+    } else {
+      part_fine[v] = 0;
+      atomicOr(&cnt->err, kErrMapRange);
+    }
+  }
+}
+
 bool same_key(const jet_ctx::RefineGraph &g, const int32_t *tau, int32_t n_tau, int32_t limit, const void *part,
               const void *phi, const void *bw, const void *res) {
   if (!g.exec || g.limit != limit || g.part != part || g.phi != phi || g.bw != bw || g.res != res) return false;
@@ -479,6 +495,84 @@ int jet_batch_tune(jet_batch *b, const int32_t *tau_pairs, int32_t n_tau, int32_
   if (e != cudaSuccess) return bfail(b, JET_ERR_CUDA, "batch tuning", e);
   b->split = splits[best];
   return JET_OK;
+}
+
+int jet_uncoarsen(jet_ctx *const *levels, int32_t n_levels, const int32_t *const *maps, const int32_t *tau_pairs,
+                  int32_t n_tau, int32_t limit, int32_t *const *part, int32_t *const *phi, int64_t *const *block_w,
+                  jet_refine_result *results, void *stream) {
+  if (!levels || n_levels < 1) return bfail(nullptr, JET_ERR_INVALID_ARG, "no levels");
+  if (n_levels > 1 && !maps) return bfail(nullptr, JET_ERR_INVALID_ARG, "maps is NULL");
+  if (!part || !phi || !block_w) return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL state array list");
+  if (n_tau < 0 || (n_tau > 0 && !tau_pairs) || limit < 1) return bfail(nullptr, JET_ERR_INVALID_ARG, "bad schedule");
+  for (int i = 0; i < n_tau; ++i)
+    if (tau_pairs[2 * i + 1] <= 0 || tau_pairs[2 * i] < 0 || tau_pairs[2 * i] >= tau_pairs[2 * i + 1])
+      return bfail(nullptr, JET_ERR_INVALID_ARG, "a temperature is outside [0, 1)");
+  for (int l = 0; l < n_levels; ++l) {
+    const jet_ctx *c = levels[l];
+    if (!c) return bfail(nullptr, JET_ERR_INVALID_ARG, "a level's context is NULL");
+    if (c->k != levels[0]->k) return bfail(nullptr, JET_ERR_INVALID_ARG, "the levels have different k");
+    if ((c->n > 0 && !part[l]) || (c->m > 0 && !phi[l]) || !block_w[l])
+      return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL state array of a level");
+    if (l > 0 && c->n > 0 && !maps[l - 1]) return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL map of a level");
+    for (int j = 0; j < l; ++j)
+      if (levels[j] == c) return bfail(nullptr, JET_ERR_INVALID_ARG, "a context appears twice");
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t origin = nullptr;
+  cudaEvent_t ev = nullptr;
+  jet_refine_result *res = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&res), sizeof(jet_refine_result) * n_levels);
+  for (int l = 0; l < n_levels && e == cudaSuccess; ++l) {
+    cudaStreamSynchronize(levels[l]->stream);
+    e = jet::ensure_capture_streams(levels[l]);
+    if (e == cudaSuccess && !levels[l]->rstate)
+      e = cudaMalloc(reinterpret_cast<void **>(&levels[l]->rstate), sizeof(jet::RefineState));
+  }
+  if (e == cudaSuccess) e = cudaGraphCreate(&g, 0);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(origin, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t ec = cudaEventRecord(ev, origin);
+    // a chain: level l waits for level l-1, projects its partition, refines
+    for (int l = 0; l < n_levels && ec == cudaSuccess; ++l) {
+      jet_ctx *c = levels[l];
+      cudaStream_t s0 = c->cap_stream[0];
+      ec = cudaStreamWaitEvent(s0, ev, 0);
+      if (ec == cudaSuccess && l > 0 && c->n > 0) {
+        jet::k_project<<<jet::grid_for(c->n, 256, c->launch_sms), 256, 0, s0>>>(part[l - 1], maps[l - 1], c->n,
+                                                                                  levels[l - 1]->n, part[l], c->cnt);
+        ec = cudaGetLastError();
+      }
+      if (ec == cudaSuccess) {
+        c->capturing = 1;
+        ec = jet::capture_refine(c, tau_pairs, n_tau, limit, part[l], phi[l], block_w[l], &res[l]);
+        c->capturing = 0;
+      }
+      if (ec == cudaSuccess) ec = cudaEventRecord(ev, s0);
+    }
+    if (ec == cudaSuccess) ec = cudaStreamWaitEvent(origin, ev, 0);
+    cudaGraph_t done = nullptr;
+    e = cudaStreamEndCapture(origin, &done);
+    if (ec != cudaSuccess) e = ec;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int rc = e == cudaSuccess ? JET_OK : bfail(nullptr, JET_ERR_CUDA, "uncoarsening graph", e);
+  for (int l = 0; l < n_levels && rc == JET_OK; ++l) {
+    const int r = jet::sync_counters(levels[l]);
+    if (r) rc = bfail(nullptr, r, levels[l]->err);
+  }
+  if (rc == JET_OK && results) memcpy(results, res, sizeof(jet_refine_result) * n_levels);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (g) cudaGraphDestroy(g);
+  if (res) cudaFreeHost(res);
+  if (ev) cudaEventDestroy(ev);
+  if (origin) cudaStreamDestroy(origin);
+  return rc;
 }
 
 }  // extern "C"

@@ -66,7 +66,7 @@ struct Counters {
 };
 
 enum : int { kErrPartRange = 1, kErrPinRange = 2, kErrIncRange = 4, kErrOffsets = 8, kErrWeight = 16,
-             kErrTranspose = 32 };
+             kErrTranspose = 32, kErrMapRange = 64 };
 
 // Per-block state of one rebalancing round (Section 4.3).
 struct RbBlock {

@@ -27,7 +27,8 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_set_graph_mode", "jet_batch_create", "jet_batch_destroy", "jet_batch_last_error",
            "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune",
            "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
-           "jet_server_last_error", "jet_server_destroy", "jet_profile_work", "jet_quotient_schedule")
+           "jet_server_last_error", "jet_server_destroy", "jet_profile_work", "jet_quotient_schedule",
+           "jet_uncoarsen")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -109,6 +110,8 @@ def load_library():
             lib.jet_set_graph_mode.argtypes = [_P, ctypes.c_int]
             lib.jet_profile_work.argtypes = [_P, pp(i64), i32]
             lib.jet_quotient_schedule.argtypes = [_P, _P, _P, _P, pp(i32), pp(i32)]
+            lib.jet_uncoarsen.argtypes = [pp(_P), i32, pp(_P), pp(i32), i32, i32, pp(_P), pp(_P), pp(_P),
+                                          pp(JetRefineResult), _P]
             lib.jet_batch_create.argtypes = [pp(_P), pp(_P), i32, _P]
             lib.jet_batch_destroy.argtypes = [_P]
             lib.jet_batch_destroy.restype = None
@@ -313,6 +316,22 @@ def jet_profile_read(ctx: Ctx, reset: bool = True) -> dict:
     launches = (ctypes.c_int64 * n)()
     _check(load_library().jet_profile_read(ctx.handle, ms, calls, launches, 1 if reset else 0), ctx)
     return {f: {"ms": ms[i], "calls": calls[i], "launches": launches[i]} for i, f in enumerate(PROF_FAMILIES)}
+
+
+def jet_uncoarsen(ctxs, maps, schedule, limit, states, stream=None) -> list:
+    """Project and refine level by level, coarsest first (states[0].part holds the coarsest partition);
+    maps[l] (int32 tensor) maps the vertices of level l+1 to level l.  One graph launch."""
+    import torch
+    n = len(ctxs)
+    hs = (_P * n)(*[c.handle for c in ctxs])
+    mp = (_P * max(n - 1, 1))(*([_ptr(m, torch.int32, "map") for m in maps] or [None]))
+    part, phi, bw = _state_arrays(states)
+    res = (JetRefineResult * n)()
+    rc = load_library().jet_uncoarsen(hs, n, mp, _pairs(schedule), len(schedule), int(limit), part, phi, bw, res,
+                                      _stream_ptr(stream))
+    if rc != JET_OK:
+        raise JetError(rc, jet_last_error(None))
+    return [r.as_dict() for r in res]
 
 
 def jet_quotient_schedule(ctx: Ctx, phi):

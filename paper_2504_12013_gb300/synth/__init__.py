@@ -291,3 +291,49 @@ def served_jobs(seed: int, count: int, rate_per_s: float = 200.0, pool: int = 32
         h = insts[j % pool]
         jobs.append((t, j % pool, k, part_perm(seed * 31 + j, h.n, k)))
     return insts, jobs
+
+
+def contract_pairs(h: Hypergraph) -> tuple[Hypergraph, np.ndarray]:
+    """One level of a fixed test hierarchy (an input builder, not the paper's coarsening): vertex v of h
+    becomes vertex v // 2; every edge keeps its distinct mapped pins (in increasing order) and is dropped
+    when fewer than two remain; coarse vertex weights are the sums, edge weights are kept.  Returns
+    (coarse hypergraph, map int32[h.n] from h's vertices to the coarse ones)."""
+    nc = (h.n + 1) // 2
+    mp = (np.arange(h.n, dtype=np.int64) // 2).astype(np.int32)
+    sizes = np.diff(h.eptr)
+    eid = np.repeat(np.arange(h.m, dtype=np.int64), sizes)
+    cp = mp[h.pins].astype(np.int64)
+    order = np.lexsort((cp, eid))
+    eid, cp = eid[order], cp[order]
+    keep = np.ones(len(cp), bool)
+    if len(cp):
+        keep[1:] = (eid[1:] != eid[:-1]) | (cp[1:] != cp[:-1])
+    eid, cp = eid[keep], cp[keep]
+    cnt = np.bincount(eid, minlength=h.m)
+    big = cnt >= 2
+    sel = big[eid]
+    eid, cp = eid[sel], cp[sel]
+    newid = np.cumsum(big) - 1
+    eid = newid[eid]
+    mc = int(big.sum())
+    eptr = np.zeros(mc + 1, np.int64)
+    np.cumsum(np.bincount(eid, minlength=mc), out=eptr[1:])
+    pins = cp.astype(np.int32)
+    o2 = np.lexsort((eid, cp))  # incidences by vertex, then edge id
+    inc = eid[o2].astype(np.int32)
+    vptr = np.zeros(nc + 1, np.int64)
+    np.cumsum(np.bincount(cp, minlength=nc), out=vptr[1:])
+    vw = np.zeros(nc, np.int64)
+    np.add.at(vw, mp, h.vwgt.astype(np.int64))
+    return Hypergraph(n=nc, m=mc, eptr=eptr, pins=pins, vptr=vptr, inc=inc, vwgt=vw.astype(np.int32),
+                      ewgt=h.ewgt[big].astype(np.int32)), mp
+
+
+def hierarchy(h: Hypergraph, levels: int) -> tuple[list, list]:
+    """levels hypergraphs from the coarsest to h, and the maps between consecutive ones (contract_pairs)."""
+    hs, maps = [h], []
+    for _ in range(levels - 1):
+        c, mp = contract_pairs(hs[0])
+        hs.insert(0, c)
+        maps.insert(0, mp)
+    return hs, maps
