@@ -8,7 +8,9 @@ library never calls it, and the two share no code.
 (arXiv 2504.12013) step by step: Section 2 (definitions), Algorithm 1 (Jet
 loop), Algorithm 2 (hypergraph afterburner), Section 4.3 (deterministic
 rebalancing) and the schedule of Section 7.2.  Its readings of points the
-paper leaves open are listed in the C file's header (R1..R12).
+paper leaves open are listed in the C file's header (R1..R25).  Section 5's
+matching schedule and Section 6's coarsening (Algorithm 4, contraction) are
+here too.
 
 Parity pins: every oracle function is checked by ``tests/test_oracle_pins.py``
 against brute force, closed forms, invariants and hand-worked fixtures.
@@ -97,6 +99,10 @@ def load(source=None):
             lib.ojet_refine.argtypes = [H, Pp, I32P, i32, i32, I32P, I64P, I64P]; lib.ojet_refine.restype = i64
             lib.ojet_quotient.argtypes = [H, i32, I32P, U8P]; lib.ojet_quotient.restype = None
             lib.ojet_schedule.argtypes = [i32, U8P, I32P, I32P, I32P]; lib.ojet_schedule.restype = i64
+            lib.ojet_subrounds.argtypes = [i32, i32, i32, I32P]; lib.ojet_subrounds.restype = i64
+            lib.ojet_cluster.argtypes = [H, i64, i32, i32, i32, I32P, I32P]; lib.ojet_cluster.restype = i64
+            lib.ojet_contract.argtypes = [H, I32P, I32P, I64P, I32P, I64P, I32P, I32P, I32P, I32P, I32P, I64P]
+            lib.ojet_contract.restype = i64
             _libs[key] = lib
     return _libs[key]
 
@@ -118,6 +124,9 @@ class Params:
 
 TAU_SCHEDULE = ((3, 4), (3, 8), (0, 1))  # three temperatures 0.75 -> 0, equidistant (Section 7.2)
 ITERATION_LIMIT = 8                      # iterations without improvement (Section 7.2)
+SINGLE_SUBROUNDS = 100                   # one-vertex sub-rounds at the start of clustering (Section 6)
+SUBROUND_CAP_DIV = 100                   # sub-rounds grow to 1% of the vertices (Section 6)
+RATING_MAX_EDGE = 1000                   # larger edges add nothing to the rating (reading R19)
 
 
 class Oracle:
@@ -224,6 +233,47 @@ class Oracle:
         """Rounds of maximal matchings covering the quotient edges: (pairs int32[p, 2], round int32[p], rounds)."""
         return schedule(qadj, self.lib)
 
+    # Section 6, Algorithm 4 (coarsening)
+    def cluster(self, cmax, order, rmax=RATING_MAX_EDGE, n_single=SINGLE_SUBROUNDS, cap_div=SUBROUND_CAP_DIV):
+        """Cluster labels (int32[n]) of one level of synchronous clustering; order is the vertex split."""
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        label = np.zeros(self.hg.n, np.int32)
+        rc = self.lib.ojet_cluster(ctypes.byref(self.h), int(cmax), int(rmax), int(n_single), int(cap_div),
+                                   _p(order, I32P), _p(label, I32P))
+        if rc != 0:
+            raise OverflowError("rating sum overflow")
+        return label
+
+    def contract(self, label):
+        """(coarse Hypergraph, map int32[n]) of the label classes."""
+        hg = self.hg
+        label = np.ascontiguousarray(label, dtype=np.int32)
+        P = int(hg.eptr[-1]) if hg.m else 0
+        mp = np.zeros(hg.n, np.int32)
+        ce, cp = np.zeros(hg.m + 1, np.int64), np.zeros(max(P, 1), np.int32)
+        cv, ci = np.zeros(hg.n + 1, np.int64), np.zeros(max(P, 1), np.int32)
+        cvw, cew = np.zeros(max(hg.n, 1), np.int32), np.zeros(max(hg.m, 1), np.int32)
+        nc, mc, pc = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+        rc = self.lib.ojet_contract(ctypes.byref(self.h), _p(label, I32P), _p(mp, I32P), _p(ce, I64P),
+                                    _p(cp, I32P), _p(cv, I64P), _p(ci, I32P), _p(cvw, I32P), _p(cew, I32P),
+                                    ctypes.byref(nc), ctypes.byref(mc), ctypes.byref(pc))
+        if rc != 0:
+            raise OverflowError("coarse weight overflow")
+        nc, mc, pc = nc.value, mc.value, pc.value
+        from paper_2504_12013_gb300.synth import Hypergraph
+        coarse = Hypergraph(n=nc, m=mc, eptr=ce[: mc + 1].copy(), pins=cp[:pc].copy(), vptr=cv[: nc + 1].copy(),
+                            inc=ci[:pc].copy(), vwgt=cvw[:nc].copy(), ewgt=cew[:mc].copy())
+        return coarse, mp
+
+    def subrounds(self, n, n_single=SINGLE_SUBROUNDS, cap_div=SUBROUND_CAP_DIV):
+        return subrounds(n, n_single, cap_div, self.lib)
+
+    def coarsen(self, cmax, order, **kw):
+        """One coarsening level: (coarse Hypergraph, map, labels)."""
+        label = self.cluster(cmax, order, **kw)
+        coarse, mp = self.contract(label)
+        return coarse, mp, label
+
     # Algorithm 1
     def refine_round(self, params: Params, tau, part, phi, bw, locked):
         st = OStats()
@@ -249,6 +299,15 @@ class State:
         self.phi = np.ascontiguousarray(phi)
         self.bw = bw
         self.locked = np.zeros(orc.hg.n, dtype=np.uint8)
+
+
+def subrounds(n, n_single=SINGLE_SUBROUNDS, cap_div=SUBROUND_CAP_DIV, lib=None):
+    """Sub-round bounds of the prefix-doubling schedule (Section 6): int32[r + 1], starts and n at the end."""
+    lib = lib or load()
+    r = lib.ojet_subrounds(int(n), int(n_single), int(cap_div), None)
+    b = np.zeros(r + 1, np.int32)
+    lib.ojet_subrounds(int(n), int(n_single), int(cap_div), _p(b, I32P))
+    return b
 
 
 def schedule(qadj, lib=None):

@@ -14,6 +14,7 @@
  *   Section 4.3                         deterministic rebalancing, deadzone, heavy vertices
  *   Section 7.2                         three temperatures 0.75 -> 0, 8 iterations
  *   Section 5 (matching schedule)       quotient graph, rounds of maximal matchings
+ *   Section 6, Algorithm 4              synchronous clustering, contraction
  * Readings where the paper is silent or ambiguous (each marked READING below):
  *   R1  blocks are 0-based, [k] = {0..k-1}.
  *   R2  L_max = floor((1+eps) * ceil(c(V)/k)), eps = eps_num/eps_den exactly.
@@ -48,6 +49,8 @@
  *   R12 an empty hyperedge contributes 0 to (lambda-1).
  *   R17 the matching schedule of the quotient graph (Section 5): see
  *       ojet_schedule.
+ *   R19..R25 coarsening (Section 6, Algorithm 4) and contraction: see
+ *       ojet_subrounds, ojet_cluster and ojet_contract.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -543,4 +546,297 @@ int64_t ojet_schedule(int32_t k, const uint8_t *qadj, int32_t *pairs, int32_t *r
   if (n_rounds) *n_rounds = round;
   free(rem); free(deg); free(order); free(matched);
   return np;
+}
+
+/*
+ * Section 6 ("Improving Deterministic Coarsening"), Algorithm 4: the sizes
+ * of the synchronous sub-rounds (prefix doubling).  READING R21: n_single
+ * sub-rounds of one vertex, then sizes 2, 4, 8, ... up to
+ * cap = max(1, floor(n / cap_div)) (cap_div = 100: one percent of the
+ * vertices), the last sub-round ragged.  bounds (may be NULL) receives the
+ * start of every sub-round and n at the end.  Returns the number of
+ * sub-rounds.
+ */
+int64_t ojet_subrounds(int32_t n, int32_t n_single, int32_t cap_div, int32_t *bounds) {
+  int64_t cap = n / (cap_div > 0 ? cap_div : 1);
+  if (cap < 1) cap = 1;
+  int64_t pos = 0, r = 0, size = 1;
+  while (pos < n) {
+    if (r < n_single) size = 1;
+    else if (r == n_single) size = 2;
+    else size *= 2;
+    if (size > cap) size = cap;
+    if (bounds) bounds[r] = (int32_t)pos;
+    pos += size > n - pos ? n - pos : size;
+    ++r;
+  }
+  if (bounds) bounds[r] = n;
+  return r;
+}
+
+/* The heavy-edge rating term of one hyperedge (READING R19): omega(e)/(|e|-1)
+ * in fixed point with 32 fraction bits, rounded down. */
+static uint64_t rating_term(int32_t w, int64_t size) { return ((uint64_t)(uint32_t)w << 32) / (uint64_t)(size - 1); }
+
+static const int32_t *g_cw_vwgt;
+static const int32_t *g_cw_target;
+static int approve_order(const void *a, const void *b) {
+  const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  if (g_cw_target[x] != g_cw_target[y]) return g_cw_target[x] < g_cw_target[y] ? -1 : 1;
+  if (g_cw_vwgt[x] != g_cw_vwgt[y]) return g_cw_vwgt[x] < g_cw_vwgt[y] ? -1 : 1;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Section 6, Algorithm 4: one level of synchronous clustering with the
+ * heavy-edge rating (corrected: an edge counts once per cluster), prefix-
+ * doubling sub-rounds and swap prevention.  Clusters are label classes;
+ * label[v] starts as v.  Per sub-round, from the state at its start:
+ *   1. every vertex u of the sub-round that is still a singleton cluster
+ *      (READING R22: no vertex joined it; it has not moved) rates the
+ *      clusters C of its neighbours: r(C) = sum over e in I(u) with
+ *      2 <= |e| <= rmax that have a pin other than u in C of the term of e
+ *      (READING R19), over clusters with c(C) + c(u) <= cmax (READING R20);
+ *      T[u] = argmax, ties to the smaller label, none if no cluster qualifies;
+ *   2. swap prevention (READING R23): for u, v of the sub-round with
+ *      T[u] = v and T[v] = u, the vertex whose cluster would be heavier (its
+ *      weight plus that of the other proposers to it) stays and the other
+ *      joins it; equal weights: the smaller id stays;
+ *   3. approval (READING R24): the proposers of each target label j, in
+ *      order of (c(u) asc, u asc), move while their weight sum stays within
+ *      cmax - c(C_j);
+ *   4. all approved vertices move at once.
+ * order (n entries, a permutation) is the random split of the vertices.
+ * Returns 0, or -1 when a vertex's rating sum could reach 2^63 (overflow).
+ */
+int64_t ojet_cluster(const ojet_hg *h, int64_t cmax, int32_t rmax, int32_t n_single, int32_t cap_div,
+                     const int32_t *order, int32_t *label) {
+  const int32_t n = h->n;
+  const size_t nn = (size_t)n + 1;
+  for (int32_t u = 0; u < n; ++u) {
+    uint64_t s = 0;
+    for (int64_t i = h->vptr[u]; i < h->vptr[u + 1]; ++i) {
+      const int32_t e = h->inc[i];
+      const int64_t size = h->eptr[e + 1] - h->eptr[e];
+      if (size < 2 || size > rmax) continue;
+      s += rating_term(h->ewgt[e], size);
+      if (s >= ((uint64_t)1 << 63)) return -1;
+    }
+  }
+  int64_t *cw = (int64_t *)malloc(sizeof(int64_t) * nn);
+  int32_t *csize = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *T = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *T2 = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int64_t *pw = (int64_t *)calloc(nn, sizeof(int64_t));
+  uint64_t *acc = (uint64_t *)calloc(nn, sizeof(uint64_t));
+  int32_t *last = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * nn);
+  int32_t *members = (int32_t *)malloc(sizeof(int32_t) * nn);
+  const int64_t rounds = ojet_subrounds(n, n_single, cap_div, NULL);
+  int32_t *bounds = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rounds + 1));
+  ojet_subrounds(n, n_single, cap_div, bounds);
+  for (int32_t v = 0; v < n; ++v) {
+    label[v] = v;
+    cw[v] = h->vwgt[v];
+    csize[v] = 1;
+    T[v] = T2[v] = -1;
+    last[v] = -1;
+  }
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int32_t a = bounds[r], b = bounds[r + 1];
+    /* 1. target clusters */
+    for (int32_t x = a; x < b; ++x) {
+      const int32_t u = order[x];
+      if (csize[u] != 1 || label[u] != u) continue;
+      int32_t nt = 0;
+      for (int64_t i = h->vptr[u]; i < h->vptr[u + 1]; ++i) {
+        const int32_t e = h->inc[i];
+        const int64_t size = h->eptr[e + 1] - h->eptr[e];
+        if (size < 2 || size > rmax) continue;
+        const uint64_t t = rating_term(h->ewgt[e], size);
+        for (int64_t p = h->eptr[e]; p < h->eptr[e + 1]; ++p) {
+          const int32_t v = h->pins[p];
+          if (v == u) continue;
+          const int32_t C = label[v];
+          if (C == u || last[C] == e) continue; /* once per edge and cluster */
+          if (last[C] < 0) touched[nt++] = C;
+          last[C] = e;
+          acc[C] += t;
+        }
+      }
+      int32_t best = -1;
+      for (int32_t q = 0; q < nt; ++q) {
+        const int32_t C = touched[q];
+        if (cw[C] + h->vwgt[u] <= cmax && (best < 0 || acc[C] > acc[best] || (acc[C] == acc[best] && C < best)))
+          best = C;
+      }
+      for (int32_t q = 0; q < nt; ++q) {
+        acc[touched[q]] = 0;
+        last[touched[q]] = -1;
+      }
+      T[u] = best;
+    }
+    /* 2. swap prevention, decided on the proposals as made */
+    for (int32_t x = a; x < b; ++x) {
+      const int32_t u = order[x];
+      if (T[u] >= 0) pw[T[u]] += h->vwgt[u];
+    }
+    for (int32_t x = a; x < b; ++x) {
+      const int32_t u = order[x];
+      const int32_t v = T[u];
+      T2[u] = v;
+      if (v < 0 || T[v] != u) continue;
+      const int64_t wu = h->vwgt[u] + pw[u] - h->vwgt[v];
+      const int64_t wv = h->vwgt[v] + pw[v] - h->vwgt[u];
+      if (wu > wv || (wu == wv && u < v)) T2[u] = -1; /* u stays, v joins u */
+    }
+    /* 3. approval per target label */
+    int32_t nm = 0;
+    for (int32_t x = a; x < b; ++x)
+      if (T2[order[x]] >= 0) members[nm++] = order[x];
+    g_cw_vwgt = h->vwgt;
+    g_cw_target = T2;
+    qsort(members, (size_t)nm, sizeof(int32_t), approve_order);
+    int32_t nmove = 0;
+    for (int32_t q = 0; q < nm;) {
+      const int32_t j = T2[members[q]];
+      const int64_t room = cmax - cw[j];
+      int64_t sum = 0;
+      int32_t z = q;
+      for (; z < nm && T2[members[z]] == j; ++z) {
+        sum += h->vwgt[members[z]];
+        if (sum <= room) members[nmove++] = members[z]; /* a prefix: weights ascend */
+        else sum = room + 1;
+      }
+      q = z;
+    }
+    /* 4. move */
+    for (int32_t q = 0; q < nmove; ++q) {
+      const int32_t u = members[q], j = T2[u];
+      label[u] = j;
+      cw[j] += h->vwgt[u];
+      cw[u] -= h->vwgt[u];
+      csize[j] += 1;
+      csize[u] -= 1;
+    }
+    for (int32_t x = a; x < b; ++x) {
+      const int32_t u = order[x];
+      if (T[u] >= 0) pw[T[u]] = 0;
+      T[u] = T2[u] = -1;
+    }
+  }
+  free(cw); free(csize); free(T); free(T2); free(pw); free(acc); free(last); free(touched); free(members);
+  free(bounds);
+  return 0;
+}
+
+static const int64_t *g_ct_eptr;
+static const int32_t *g_ct_pins;
+static int contract_order(const void *a, const void *b) {
+  const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  const int64_t sx = g_ct_eptr[x + 1] - g_ct_eptr[x], sy = g_ct_eptr[y + 1] - g_ct_eptr[y];
+  if (sx != sy) return sx < sy ? -1 : 1;
+  for (int64_t i = 0; i < sx; ++i) {
+    const int32_t px = g_ct_pins[g_ct_eptr[x] + i], py = g_ct_pins[g_ct_eptr[y] + i];
+    if (px != py) return px < py ? -1 : 1;
+  }
+  return (x > y) - (x < y);
+}
+
+static int cmp_i32(const void *a, const void *b) {
+  const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/*
+ * Contraction of the clusters (Section 6 reuses the contraction of the
+ * earlier deterministic partitioner; READING R25): the non-empty label
+ * classes become the coarse vertices, numbered in increasing label order,
+ * with c(C) the sum of their members' weights; map[v] is v's coarse vertex.
+ * Every hyperedge keeps its distinct coarse pins in increasing order and is
+ * dropped when fewer than two remain; hyperedges with identical pin sets are
+ * merged into the one of smallest id, their weights summed; coarse edges
+ * follow the order of those ids; the incidences of a coarse vertex are in
+ * increasing coarse edge id.  Output arrays are sized as the input's (n+1,
+ * P, n+1, P, n, m).  Returns 0, or -1 when a coarse weight leaves int32.
+ */
+int64_t ojet_contract(const ojet_hg *h, const int32_t *label, int32_t *map, int64_t *ceptr, int32_t *cpins,
+                      int64_t *cvptr, int32_t *cinc, int32_t *cvwgt, int32_t *cewgt, int32_t *nc_out,
+                      int32_t *mc_out, int64_t *pc_out) {
+  const int32_t n = h->n, m = h->m;
+  int32_t *cid = (int32_t *)malloc(sizeof(int32_t) * ((size_t)n + 1));
+  int64_t *w = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+  for (int32_t v = 0; v < n; ++v) cid[v] = -1;
+  for (int32_t v = 0; v < n; ++v) cid[label[v]] = 0;
+  int32_t nc = 0;
+  for (int32_t l = 0; l < n; ++l)
+    if (cid[l] == 0) cid[l] = nc++;
+  int rc = 0;
+  for (int32_t v = 0; v < n; ++v) {
+    map[v] = cid[label[v]];
+    w[map[v]] += h->vwgt[v];
+  }
+  for (int32_t c = 0; c < nc; ++c) {
+    if (w[c] > INT32_MAX) rc = -1;
+    cvwgt[c] = (int32_t)w[c];
+  }
+  /* distinct coarse pins of every edge, ascending */
+  int64_t *teptr = (int64_t *)malloc(sizeof(int64_t) * ((size_t)m + 1));
+  int32_t *tpins = (int32_t *)malloc(sizeof(int32_t) * ((size_t)h->P + 1));
+  teptr[0] = 0;
+  for (int32_t e = 0; e < m; ++e) {
+    const int64_t o = teptr[e];
+    int64_t len = 0;
+    for (int64_t p = h->eptr[e]; p < h->eptr[e + 1]; ++p) tpins[o + len++] = map[h->pins[p]];
+    qsort(tpins + o, (size_t)len, sizeof(int32_t), cmp_i32);
+    int64_t d = 0;
+    for (int64_t i = 0; i < len; ++i)
+      if (d == 0 || tpins[o + i] != tpins[o + d - 1]) tpins[o + d++] = tpins[o + i];
+    teptr[e + 1] = o + d;
+  }
+  /* identical pin sets: sort the kept edges by (size, pins, id); runs share a pin set */
+  int32_t *ord = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m + 1));
+  int32_t *rep = (int32_t *)malloc(sizeof(int32_t) * ((size_t)m + 1));
+  int64_t *ew = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
+  int32_t nk = 0;
+  for (int32_t e = 0; e < m; ++e) {
+    rep[e] = -1;
+    if (teptr[e + 1] - teptr[e] >= 2) ord[nk++] = e;
+  }
+  g_ct_eptr = teptr;
+  g_ct_pins = tpins;
+  qsort(ord, (size_t)nk, sizeof(int32_t), contract_order);
+  for (int32_t i = 0; i < nk; ++i) {
+    const int32_t e = ord[i];
+    const int32_t f = i > 0 ? ord[i - 1] : -1;
+    const int64_t size = teptr[e + 1] - teptr[e];
+    const int same = f >= 0 && teptr[f + 1] - teptr[f] == size &&
+                     memcmp(tpins + teptr[f], tpins + teptr[e], sizeof(int32_t) * (size_t)size) == 0;
+    rep[e] = same ? rep[f] : e; /* a run's first edge has the smallest id */
+    ew[rep[e]] += h->ewgt[e];
+  }
+  /* coarse edges in order of their representative's id */
+  int32_t mc = 0;
+  int64_t pc = 0;
+  ceptr[0] = 0;
+  for (int32_t e = 0; e < m; ++e) {
+    if (rep[e] != e) continue;
+    if (ew[e] > INT32_MAX) rc = -1;
+    cewgt[mc] = (int32_t)ew[e];
+    for (int64_t i = teptr[e]; i < teptr[e + 1]; ++i) cpins[pc++] = tpins[i];
+    ceptr[++mc] = pc;
+  }
+  /* incidences by coarse vertex, in increasing coarse edge id */
+  for (int32_t c = 0; c <= nc; ++c) cvptr[c] = 0;
+  for (int64_t i = 0; i < pc; ++i) cvptr[cpins[i] + 1] += 1;
+  for (int32_t c = 0; c < nc; ++c) cvptr[c + 1] += cvptr[c];
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)nc + 1));
+  for (int32_t c = 0; c < nc; ++c) fill[c] = cvptr[c];
+  for (int32_t f = 0; f < mc; ++f)
+    for (int64_t i = ceptr[f]; i < ceptr[f + 1]; ++i) cinc[fill[cpins[i]]++] = f;
+  *nc_out = nc;
+  *mc_out = mc;
+  *pc_out = pc;
+  free(cid); free(w); free(teptr); free(tpins); free(ord); free(rep); free(ew); free(fill);
+  return rc;
 }

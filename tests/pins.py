@@ -610,3 +610,233 @@ def run_all(orc_cls, params_cls, source=None):
     check_schedule_hand(o)
     for q in random_quotients():
         check_schedule_invariants(o, q)
+    check_coarsen_hand(O)
+    check_subrounds(o)
+    check_clustering(O)
+
+
+# ------------------------------------------------------------------ Section 6 (coarsening)
+
+def rating_term(w, size):
+    """omega(e)/(|e|-1) with 32 fraction bits, rounded down (reading R19)."""
+    return (int(w) << 32) // (int(size) - 1)
+
+
+def coarsen_hand_examples():
+    """(name, hypergraph, c_max, order, n_single, cap_div, expected labels), worked by hand.
+
+    A (unit weights, c_max 2, one vertex per sub-round, order 0..5):
+      edges {0,1} w4, {1,2,3} w2, {2,3} w3, {3,4,5} w2, {4,5} w1
+      u0: cluster 1 rated 4 -> joins 1 (weight 2);  u1: cluster {0,1} is not a singleton, stays
+      u2: cluster 1 rated 1 (over the bound: 2+1 > 2), cluster 3 rated 1+3 = 4 -> joins 3
+      u3: not a singleton;  u4: cluster 3 rated 1 (over the bound), cluster 5 rated 1+1 -> joins 5
+      labels [1,1,3,3,5,5]; contraction: edges {0,1} w2 and {1,2} w2, weights [2,2,2]
+    B (the corrected rating; c_max 10; order 1,0,2,3):
+      edges {0,1,2} w3, {0,3} w2, {1,2} w10
+      u1: cluster 2 rated 1.5 + 10, cluster 0 rated 1.5 -> joins 2
+      u0: edge {0,1,2} has two pins of cluster 2 but counts once: cluster 2 rated 1.5 < cluster 3
+          rated 2 -> joins 3 (counting per pin would give 3 > 2 and pick cluster 2)
+      labels [3,2,2,3]
+    C (ties to the smaller label): edges {0,1} w1, {0,2} w1; u0 rates clusters 1 and 2 equally -> 1;
+      u1 is no longer a singleton; u2 rates cluster 1 (through pin 0) -> joins it.  labels [1,1,1]
+      (ties to the larger label would give [2,2,2])
+    D (swap prevention and approval; weights [1,2,1,1], c_max 4, sub-rounds {0,1}, {2,3}):
+      edges {0,1} w5, {1,2} w1, {0,3} w1
+      sub-round {0,1}: T[0] = 1, T[1] = 0 (a swap); cluster 0 would weigh 1, cluster 1 weighs 2
+      -> 1 stays, 0 joins 1 (cluster 1 weighs 3)
+      sub-round {2,3}: both propose cluster 1 (3+1 <= 4); room 4-3 = 1; order (c, id): 2, 3
+      -> 2 joins, 3 stays.  labels [1,1,1,3]
+    E (approval by weight; weights [1,2,1,2], c_max 3, order 2,1,3,0, sub-rounds {2,1}, {3,0}):
+      edges {0,1} w1, {0,2} w1, {0,3} w1
+      sub-round {2,1}: both propose cluster 0; room 3-1 = 2; order (c, id): 2 (c 1), 1 (c 2):
+      sums 1, 3 -> only 2 joins.  sub-round {3,0}: cluster 0 weighs 2, 2+2 > 3: 3 stays;
+      0 is no longer a singleton.  labels [0,1,0,3]
+    """
+    ex = []
+    hg = synth.from_edges(6, [[0, 1], [1, 2, 3], [2, 3], [3, 4, 5], [4, 5]], ewgt=[4, 2, 3, 2, 1])
+    ex.append(("A", hg, 2, [0, 1, 2, 3, 4, 5], 100, 100, [1, 1, 3, 3, 5, 5]))
+    hg = synth.from_edges(4, [[0, 1, 2], [0, 3], [1, 2]], ewgt=[3, 2, 10])
+    ex.append(("B", hg, 10, [1, 0, 2, 3], 100, 100, [3, 2, 2, 3]))
+    hg = synth.from_edges(3, [[0, 1], [0, 2]])
+    ex.append(("C", hg, 10, [0, 1, 2], 100, 100, [1, 1, 1]))
+    hg = synth.from_edges(4, [[0, 1], [1, 2], [0, 3]], vwgt=[1, 2, 1, 1], ewgt=[5, 1, 1])
+    ex.append(("D", hg, 4, [0, 1, 2, 3], 0, 2, [1, 1, 1, 3]))
+    hg = synth.from_edges(4, [[0, 1], [0, 2], [0, 3]], vwgt=[1, 2, 1, 2])
+    ex.append(("E", hg, 3, [2, 1, 3, 0], 0, 2, [0, 1, 0, 3]))
+    return ex
+
+
+def check_coarsen_hand(make):
+    for name, hg, cmax, order, n_single, cap_div, want in coarsen_hand_examples():
+        o = make(hg)
+        got = o.cluster(cmax, np.array(order, np.int32), n_single=n_single, cap_div=cap_div)
+        assert list(got) == want, f"example {name}: {list(got)} != {want}"
+    name, hg, cmax, order, n_single, cap_div, want = coarsen_hand_examples()[0]
+    c, mp = make(hg).contract(np.array(want, np.int32))
+    assert list(mp) == [0, 0, 1, 1, 2, 2]
+    assert (c.n, c.m, list(c.eptr), list(c.pins), list(c.ewgt), list(c.vwgt)) == \
+        (3, 2, [0, 2, 4], [0, 1, 1, 2], [2, 2], [2, 2, 2])
+    assert list(c.vptr) == [0, 1, 3, 4] and list(c.inc) == [0, 0, 1, 1]
+
+
+def check_subrounds(orc):
+    """The prefix-doubling schedule against its statement: n_single sizes of 1, then 2, 4, 8, ... capped
+    at floor(n / cap_div) (at least 1), the last one ragged."""
+    assert list(np.diff(orc.subrounds(1000)))[:106] == [1] * 100 + [2, 4, 8, 10, 10, 10]
+    for n, ns, cd in ((1000, 100, 100), (7, 100, 100), (5000, 3, 10), (64, 0, 1), (1, 0, 1), (300, 10, 1000)):
+        cap = max(1, n // cd)
+        sizes, j = [], 0
+        while sum(sizes) < n:
+            s = 1 if len(sizes) < ns else min(2 ** (len(sizes) - ns + 1), cap)
+            sizes.append(min(s, n - sum(sizes)))
+        b = orc.subrounds(n, ns, cd)
+        assert list(np.diff(b)) == sizes and b[0] == 0 and b[-1] == n, (n, ns, cd)
+
+
+def sequential_clustering(hg, cmax, rmax, order):
+    """Clustering with every sub-round of one vertex, restated from Section 6 with sets: each singleton
+    vertex in turn joins its best-rated cluster within the weight bound (ties to the smaller label)."""
+    label = list(range(hg.n))
+    members = {v: {v} for v in range(hg.n)}
+    weight = {v: int(hg.vwgt[v]) for v in range(hg.n)}
+    for u in order:
+        if members[u] != {u}:
+            continue
+        rating = {}
+        for e in hg.inc[hg.vptr[u]:hg.vptr[u + 1]]:
+            pins = hg.pins[hg.eptr[e]:hg.eptr[e + 1]]
+            if len(pins) < 2 or len(pins) > rmax:
+                continue
+            for C in {label[v] for v in pins if v != u}:
+                rating[C] = rating.get(C, 0) + rating_term(hg.ewgt[e], len(pins))
+        ok = [C for C in rating if weight[C] + int(hg.vwgt[u]) <= cmax]
+        if not ok:
+            continue
+        best = min(ok, key=lambda C: (-rating[C], C))
+        members[u].discard(u)
+        members[best].add(u)
+        weight[best] += int(hg.vwgt[u])
+        weight[u] -= int(hg.vwgt[u])
+        label[u] = best
+    return label
+
+
+def synchronous_clustering(hg, cmax, rmax, order, bounds):
+    """Algorithm 4 restated with dictionaries, one sub-round at a time from the state at its start:
+    selection as above, swap pairs resolved by the would-be cluster weights, then per target the
+    longest prefix in (weight, id) order that fits the bound."""
+    label = list(range(hg.n))
+    size = [1] * hg.n
+    weight = [int(x) for x in hg.vwgt]
+    c = [int(x) for x in hg.vwgt]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        B = [int(u) for u in order[a:b]]
+        T = {}
+        for u in B:
+            if size[u] != 1:
+                continue
+            rating = {}
+            for e in hg.inc[hg.vptr[u]:hg.vptr[u + 1]]:
+                pins = hg.pins[hg.eptr[e]:hg.eptr[e + 1]]
+                if 2 <= len(pins) <= rmax:
+                    for C in {label[v] for v in pins if v != u}:
+                        rating[C] = rating.get(C, 0) + rating_term(hg.ewgt[e], len(pins))
+            ok = [C for C in rating if weight[C] + c[u] <= cmax]
+            if ok:
+                T[u] = min(ok, key=lambda C: (-rating[C], C))
+        incoming = {}
+        for u, j in T.items():
+            incoming[j] = incoming.get(j, 0) + c[u]
+        T2 = dict(T)
+        for u, v in T.items():
+            if T.get(v) == u:
+                wu = c[u] + incoming.get(u, 0) - c[v]
+                wv = c[v] + incoming.get(v, 0) - c[u]
+                if (wu, -u) > (wv, -v):
+                    del T2[u]
+        groups = {}
+        for u, j in T2.items():
+            groups.setdefault(j, []).append(u)
+        moves = []
+        for j, us in groups.items():
+            total = 0
+            for u in sorted(us, key=lambda x: (c[x], x)):
+                total += c[u]
+                if total > cmax - weight[j]:
+                    break
+                moves.append((u, j))
+        for u, j in moves:
+            label[u] = j
+            weight[j] += c[u]
+            weight[u] -= c[u]
+            size[j] += 1
+            size[u] -= 1
+    return label
+
+
+def expected_contraction(hg, label):
+    """The contracted hypergraph from its definition (reading R25), by dictionaries over pin sets."""
+    used = sorted(set(int(x) for x in label))
+    cid = {l: i for i, l in enumerate(used)}
+    mp = [cid[int(label[v])] for v in range(hg.n)]
+    vw = [0] * len(used)
+    for v in range(hg.n):
+        vw[mp[v]] += int(hg.vwgt[v])
+    sets = {}
+    for e in range(hg.m):
+        s = tuple(sorted({mp[v] for v in hg.pins[hg.eptr[e]:hg.eptr[e + 1]]}))
+        if len(s) >= 2:
+            if s not in sets:
+                sets[s] = [e, 0]
+            sets[s][1] += int(hg.ewgt[e])
+    edges = sorted(sets.items(), key=lambda kv: kv[1][0])
+    return mp, vw, [list(s) for s, _ in edges], [w for _, (_, w) in edges]
+
+
+def check_contraction(orc, hg, label, k=5, seed=3):
+    c, mp = orc.contract(label)
+    emp, evw, eedges, eew = expected_contraction(hg, label)
+    assert list(mp) == emp
+    assert list(c.vwgt) == evw and c.n == len(evw)
+    assert c.m == len(eedges) and list(c.ewgt) == eew
+    assert [list(c.pins[c.eptr[f]:c.eptr[f + 1]]) for f in range(c.m)] == eedges
+    inc = [[f for f in range(c.m) if v in eedges[f]] for v in range(c.n)]
+    assert [list(c.inc[c.vptr[v]:c.vptr[v + 1]]) for v in range(c.n)] == inc
+    # projection keeps (lambda-1) and the block weights of any partition of the coarse vertices
+    for s in range(3):
+        pc = (synth.stream_u64(seed + s, c.n) % np.uint64(k)).astype(np.int32)
+        pf = pc[mp]
+        assert objective_sets(c, pc) == objective_sets(hg, pf)
+        assert np.array_equal(np.bincount(pc, weights=c.vwgt, minlength=k), np.bincount(pf, weights=hg.vwgt, minlength=k))
+    return c
+
+
+def coarsen_instances(seed=41):
+    out = []
+    for i, (n, m, cap, cm, wm) in enumerate(((150, 170, 6, 1, 1), (200, 260, 12, 4, 3), (320, 300, 40, 3, 2),
+                                             (90, 400, 3, 2, 5))):
+        hg = synth.uniform(seed + i, n, m, base=2, geo=(1, 2), size_cap=cap, c_max=cm, w_max=wm)
+        order = synth.stream_u64(seed + 10 + i, n).argsort(kind="stable").astype(np.int32)
+        out.append((hg, order))
+    return out
+
+
+def check_clustering(make):
+    for i, (hg, order) in enumerate(coarsen_instances()):
+        o = make(hg)
+        W = int(hg.vwgt.sum())
+        for cmax in (2, 4, max(3, W // 20), W):
+            for rmax in (1000, 4):
+                got = o.cluster(cmax, order, rmax=rmax, n_single=hg.n, cap_div=100)
+                assert list(got) == sequential_clustering(hg, cmax, rmax, order), (i, cmax, rmax, "sequential")
+                for ns, cd in ((100, 100), (0, 1), (3, 8)):
+                    got = o.cluster(cmax, order, rmax=rmax, n_single=ns, cap_div=cd)
+                    want = synchronous_clustering(hg, cmax, rmax, order, list(o.subrounds(hg.n, ns, cd)))
+                    assert list(got) == want, (i, cmax, rmax, ns, cd)
+                    # invariants: clusters of several vertices within the bound; no label swaps
+                    lab = np.asarray(got)
+                    w = np.bincount(lab, weights=hg.vwgt, minlength=hg.n)
+                    cnt = np.bincount(lab, minlength=hg.n)
+                    assert np.all(w[cnt > 1] <= cmax)
+                    assert not np.any((lab != np.arange(hg.n)) & (lab[lab] == np.arange(hg.n)))
+            check_contraction(o, hg, o.cluster(cmax, order), seed=i)

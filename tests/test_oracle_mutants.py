@@ -66,6 +66,24 @@ MUTANTS = {
     "schedule_tie_larger_id": ("(deg[order[y]] == deg[b] && order[y] > b))) {", "(deg[order[y]] == deg[b] && order[y] < b))) {"),
     "schedule_partner_lowest_degree": ("(best < 0 || deg[j] > deg[best])) best = j;", "(best < 0 || deg[j] < deg[best])) best = j;"),
     "schedule_one_pair_per_round": ("      round_of[np] = round;\n      ++np;\n    }", "      round_of[np] = round;\n      ++np;\n      break;\n    }"),
+    # Section 6, Algorithm 4 (coarsening) and contraction
+    "subrounds_no_doubling": ("    else size *= 2;\n", "\n"),
+    "subrounds_cap_ignored": ("    if (size > cap) size = cap;\n", "\n"),
+    "rating_counts_per_pin": ("if (C == u || last[C] == e) continue; /* once per edge and cluster */", "if (C == u) continue;"),
+    "rating_divides_by_size": ("/ (uint64_t)(size - 1); }", "/ (uint64_t)size; }"),
+    "rating_ignores_edge_limit": ("      if (size < 2 || size > rmax) continue;\n        const uint64_t t", "      if (size < 2) continue;\n        const uint64_t t"),
+    "cluster_tie_larger_label": ("(acc[C] == acc[best] && C < best)", "(acc[C] == acc[best] && C > best)"),
+    "cluster_ignores_weight_bound": ("if (cw[C] + h->vwgt[u] <= cmax && (best < 0", "if ((best < 0"),
+    "cluster_moves_non_singletons": ("if (csize[u] != 1 || label[u] != u) continue;", "if (label[u] != u) continue;"),
+    "swap_not_prevented": ("if (wu > wv || (wu == wv && u < v)) T2[u] = -1; /* u stays, v joins u */", ""),
+    "swap_lighter_stays": ("if (wu > wv || (wu == wv && u < v)) T2[u] = -1;", "if (wu < wv || (wu == wv && u < v)) T2[u] = -1;"),
+    "approve_heavier_first": ("if (g_cw_vwgt[x] != g_cw_vwgt[y]) return g_cw_vwgt[x] < g_cw_vwgt[y] ? -1 : 1;",
+                              "if (g_cw_vwgt[x] != g_cw_vwgt[y]) return g_cw_vwgt[x] > g_cw_vwgt[y] ? -1 : 1;"),
+    "approve_room_ignores_cluster": ("const int64_t room = cmax - cw[j];", "const int64_t room = cmax;"),
+    "contract_keeps_single_pin_edges": ("if (teptr[e + 1] - teptr[e] >= 2) ord[nk++] = e;", "if (teptr[e + 1] - teptr[e] >= 1) ord[nk++] = e;"),
+    "contract_no_merge": ("rep[e] = same ? rep[f] : e;", "rep[e] = e;"),
+    "contract_merge_drops_weight": ("ew[rep[e]] += h->ewgt[e];", "ew[rep[e]] = h->ewgt[e];"),
+    "contract_no_dedupe": ("if (d == 0 || tpins[o + i] != tpins[o + d - 1]) tpins", "if (1) tpins"),
     "round_always_rebalances_once": ("  if (over) st->rebalance_rounds = ojet_rebalance(h, p, part, phi, bw, &st->rebalance_moves);",
                                      "  if (over) { st->rebalance_rounds = 1; ojet_rebalance_round(h, p, part, phi, bw, NULL, NULL); }"),
 }

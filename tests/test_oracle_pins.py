@@ -192,3 +192,47 @@ def test_schedule_of_a_complete_quotient():
         pairs, rnd, nr = oracle.schedule(q)
         assert len(pairs) == k * (k - 1) // 2
         assert nr >= k - 1
+
+
+# Section 6, Algorithm 4 (coarsening) and contraction
+
+def test_coarsen_hand_examples():
+    pins.check_coarsen_hand(make)
+
+
+def test_subround_schedule():
+    pins.check_subrounds(make(pins.hand_example()[0]))
+
+
+def test_clustering_against_restatements():
+    pins.check_clustering(make)
+
+
+def test_clustering_edge_cases():
+    """No edges: every vertex stays alone.  One vertex heavier than the bound: it never joins and no
+    cluster it would grow is rated.  All sub-rounds of one vertex equal the sequential restatement."""
+    hg = synth.from_edges(5, [])
+    assert list(make(hg).cluster(10, np.arange(5, dtype=np.int32))) == [0, 1, 2, 3, 4]
+    hg = synth.from_edges(3, [[0, 1, 2]], vwgt=[9, 1, 1])
+    lab = make(hg).cluster(5, np.arange(3, dtype=np.int32))
+    assert lab[0] == 0 and lab[1] == lab[2]
+    c, mp = make(hg).contract(lab)
+    assert c.n == 2 and c.m == 1 and list(c.vwgt) == [9, 2]
+
+
+def test_rating_overflow_is_reported():
+    # a vertex in three edges of weight 2^31 - 1 and size 2: three terms of about 2^63
+    hg = synth.from_edges(2, [[0, 1]] * 3, ewgt=[2 ** 31 - 1] * 3)
+    with pytest.raises(OverflowError):
+        make(hg).cluster(10, np.arange(2, dtype=np.int32))
+
+
+def test_projection_keeps_objective_over_levels():
+    hg = synth.uniform(8, 2000, 2300, base=2, geo=(1, 2), size_cap=30, c_max=3, w_max=2)
+    order = synth.stream_u64(8, hg.n).argsort(kind="stable").astype(np.int32)
+    for _ in range(3):
+        o = make(hg)
+        c = pins.check_contraction(o, hg, o.cluster(int(hg.vwgt.sum()) // 50, order))
+        assert c.n < hg.n
+        hg = c
+        order = synth.stream_u64(9, hg.n).argsort(kind="stable").astype(np.int32)
