@@ -259,6 +259,70 @@ int jet_uncoarsen(jet_ctx *const *levels, int32_t n_levels, const int32_t *const
                   jet_refine_result *results, void *stream);
 
 /*
+ * Coarsening (Section 6, Algorithm 4): one level of deterministic
+ * synchronous clustering, then the contraction of its clusters.
+ *
+ * jet_cluster.  Clusters are label classes; label[v] (DEVICE, n, out)
+ * starts as v.  The vertices are visited in sub-rounds of order (DEVICE, n,
+ * a permutation of [0, n): the random split of Algorithm 4, an input so
+ * that the result is reproducible): single_subrounds sub-rounds of one
+ * vertex, then sizes 2, 4, 8, ... up to max(1, floor(n / subround_cap_div))
+ * (prefix doubling, Section 6; the paper uses 100 and 100).  Within a
+ * sub-round, from the state at its start, each vertex still in a singleton
+ * cluster rates the clusters C of its neighbours, sum over its edges e with
+ * 2 <= |e| <= rating_max_edge that touch C of omega(e)/(|e|-1) (the
+ * corrected heavy-edge rating: once per edge and cluster; 32.32 fixed point,
+ * each term rounded down), over the clusters with
+ * c(C) + c(u) <= max_cluster_weight, and proposes the best (ties to the
+ * smaller label).  Mutual proposals u <-> v go towards the heavier would-be
+ * cluster (its weight plus its other proposers; ties: the smaller id stays),
+ * each target accepts the longest prefix of its proposers in (c(u), u)
+ * order that keeps it within max_cluster_weight, and the accepted vertices
+ * move at once.  Synchronizes.  Errors: JET_ERR_INVALID_ARG (NULL pointers,
+ * max_cluster_weight < 1, rating_max_edge < 2, single_subrounds < 0,
+ * subround_cap_div < 1), JET_ERR_DATA (malformed CSR, or order not a
+ * permutation), JET_ERR_OVERFLOW (a vertex's rating sum reaches 2^63, or
+ * its rated edges hold more than 2^27 pins), JET_ERR_OOM, JET_ERR_CUDA.
+ *
+ * jet_contract.  The non-empty label classes of label (DEVICE, n, values in
+ * [0, n)) become the coarse vertices, numbered in increasing label order,
+ * weighing the sum of their members; map (DEVICE, n, out) gives each vertex
+ * its coarse vertex.  Every edge keeps its distinct coarse pins in
+ * increasing order and is dropped below two; edges with equal pin sets merge
+ * into the one of smallest id with their weights summed; coarse edges keep
+ * the order of those ids; the incidences of a coarse vertex are in
+ * increasing coarse-edge id.  out holds DEVICE buffers owned by the caller,
+ * sized as the input's (eptr m+1, pins P, vptr n+1, inc P, vwgt n, ewgt m);
+ * *n_out, *m_out, *P_out (HOST) get the coarse sizes.  Synchronizes.
+ * Errors: JET_ERR_INVALID_ARG, JET_ERR_DATA (malformed CSR or a label
+ * outside [0, n)), JET_ERR_OVERFLOW (a coarse weight leaves int32),
+ * JET_ERR_OOM, JET_ERR_CUDA.
+ *
+ * Both allocate stream-ordered scratch and free it before returning; both
+ * report errors through jet_last_error(NULL); `stream` is a cudaStream_t.
+ */
+typedef struct {
+  int64_t max_cluster_weight; /* bound on the weight of a cluster              */
+  int32_t rating_max_edge;    /* edges with more pins add nothing to a rating  */
+  int32_t single_subrounds;   /* one-vertex sub-rounds at the start            */
+  int32_t subround_cap_div;   /* sub-rounds grow to floor(n / this) vertices   */
+} jet_coarsen_params;
+
+typedef struct { /* DEVICE buffers owned by the caller */
+  int64_t *eptr;
+  int32_t *pins;
+  int64_t *vptr;
+  int32_t *inc;
+  int32_t *vwgt;
+  int32_t *ewgt;
+} jet_hypergraph_out;
+
+int jet_cluster(const jet_hypergraph *hg, const jet_coarsen_params *params, const int32_t *order, int32_t *label,
+                void *stream);
+int jet_contract(const jet_hypergraph *hg, const int32_t *label, int32_t *map, const jet_hypergraph_out *out,
+                 int32_t *n_out, int32_t *m_out, int64_t *P_out, void *stream);
+
+/*
  * Serving: a request loop that refines submitted jobs (each = jet_refine_host
  * on the job's host buffers: upload, Algorithm 1 as one graph, download) with
  * up to max_active jobs on the device at once, each on its own stream and

@@ -28,7 +28,7 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune",
            "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
            "jet_server_last_error", "jet_server_destroy", "jet_profile_work", "jet_quotient_schedule",
-           "jet_uncoarsen")
+           "jet_uncoarsen", "jet_cluster", "jet_contract")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -39,6 +39,15 @@ _P = ctypes.c_void_p
 class JetHypergraph(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("P", ctypes.c_int64),
                 ("eptr", _P), ("pins", _P), ("vptr", _P), ("inc", _P), ("vwgt", _P), ("ewgt", _P)]
+
+
+class JetCoarsenParams(ctypes.Structure):
+    _fields_ = [("max_cluster_weight", ctypes.c_int64), ("rating_max_edge", ctypes.c_int32),
+                ("single_subrounds", ctypes.c_int32), ("subround_cap_div", ctypes.c_int32)]
+
+
+class JetHypergraphOut(ctypes.Structure):
+    _fields_ = [("eptr", _P), ("pins", _P), ("vptr", _P), ("inc", _P), ("vwgt", _P), ("ewgt", _P)]
 
 
 class JetParams(ctypes.Structure):
@@ -112,6 +121,9 @@ def load_library():
             lib.jet_quotient_schedule.argtypes = [_P, _P, _P, _P, pp(i32), pp(i32)]
             lib.jet_uncoarsen.argtypes = [pp(_P), i32, pp(_P), pp(i32), i32, i32, pp(_P), pp(_P), pp(_P),
                                           pp(JetRefineResult), _P]
+            lib.jet_cluster.argtypes = [pp(JetHypergraph), pp(JetCoarsenParams), _P, _P, _P]
+            lib.jet_contract.argtypes = [pp(JetHypergraph), _P, _P, pp(JetHypergraphOut), pp(i32), pp(i32), pp(i64),
+                                         _P]
             lib.jet_batch_create.argtypes = [pp(_P), pp(_P), i32, _P]
             lib.jet_batch_destroy.argtypes = [_P]
             lib.jet_batch_destroy.restype = None
@@ -180,11 +192,66 @@ class DeviceHypergraph:
         self.eptr, self.pins, self.vptr, self.inc = t(hg.eptr), t(hg.pins), t(hg.vptr), t(hg.inc)
         self.vwgt, self.ewgt = t(hg.vwgt), t(hg.ewgt)
 
+    @classmethod
+    def from_tensors(cls, n, m, P, eptr, pins, vptr, inc, vwgt, ewgt):
+        """A hypergraph already on the device (e.g. a contraction's output), trimmed to its sizes."""
+        self = cls.__new__(cls)
+        self.n, self.m, self.P = int(n), int(m), int(P)
+        self.host = None
+        self.eptr, self.pins, self.vptr, self.inc = eptr[: m + 1], pins[:P], vptr[: n + 1], inc[:P]
+        self.vwgt, self.ewgt = vwgt[:n], ewgt[:m]
+        return self
+
+    def to_host(self):
+        from . import synth
+        c = lambda t: t.cpu().numpy().copy()
+        return synth.Hypergraph(n=self.n, m=self.m, eptr=c(self.eptr), pins=c(self.pins), vptr=c(self.vptr),
+                                inc=c(self.inc), vwgt=c(self.vwgt), ewgt=c(self.ewgt))
+
     def c(self) -> JetHypergraph:
         import torch
         return JetHypergraph(self.n, self.m, self.P, _ptr(self.eptr, torch.int64), _ptr(self.pins, torch.int32),
                              _ptr(self.vptr, torch.int64), _ptr(self.inc, torch.int32),
                              _ptr(self.vwgt, torch.int32), _ptr(self.ewgt, torch.int32))
+
+
+RATING_MAX_EDGE = 1000   # edges with more pins add nothing to a coarsening rating
+SINGLE_SUBROUNDS = 100   # one-vertex sub-rounds at the start of a clustering level (Section 6)
+SUBROUND_CAP_DIV = 100   # sub-rounds grow to 1% of the vertices (Section 6)
+
+
+def jet_cluster(dh, cmax, order, rmax=RATING_MAX_EDGE, n_single=SINGLE_SUBROUNDS, cap_div=SUBROUND_CAP_DIV,
+                stream=None):
+    """One level of synchronous clustering (Section 6, Algorithm 4): the label tensor (int32, n)."""
+    import torch
+    label = torch.empty(max(dh.n, 1), dtype=torch.int32, device=dh.eptr.device)
+    prm = JetCoarsenParams(int(cmax), int(rmax), int(n_single), int(cap_div))
+    _check(load_library().jet_cluster(ctypes.byref(dh.c()), ctypes.byref(prm), _ptr(order, torch.int32, "order"),
+                                      _ptr(label, torch.int32), _stream_ptr(stream)))
+    return label[: dh.n]
+
+
+def jet_contract(dh, label, stream=None):
+    """Contraction of the label classes: (coarse DeviceHypergraph, map tensor)."""
+    import torch
+    dev = dh.eptr.device
+    e = lambda n, dt: torch.empty(max(n, 1), dtype=dt, device=dev)
+    eptr, pins, vptr, inc = e(dh.m + 1, torch.int64), e(dh.P, torch.int32), e(dh.n + 1, torch.int64), e(dh.P, torch.int32)
+    vwgt, ewgt, mp = e(dh.n, torch.int32), e(dh.m, torch.int32), e(dh.n, torch.int32)
+    out = JetHypergraphOut(_ptr(eptr), _ptr(pins), _ptr(vptr), _ptr(inc), _ptr(vwgt), _ptr(ewgt))
+    nc, mc, pc = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(load_library().jet_contract(ctypes.byref(dh.c()), _ptr(label, torch.int32, "label"), _ptr(mp),
+                                       ctypes.byref(out), ctypes.byref(nc), ctypes.byref(mc), ctypes.byref(pc),
+                                       _stream_ptr(stream)))
+    coarse = DeviceHypergraph.from_tensors(nc.value, mc.value, pc.value, eptr, pins, vptr, inc, vwgt, ewgt)
+    return coarse, mp[: dh.n]
+
+
+def jet_coarsen(dh, cmax, order, stream=None, **kw):
+    """One coarsening level: (coarse DeviceHypergraph, map, labels)."""
+    label = jet_cluster(dh, cmax, order, stream=stream, **kw)
+    coarse, mp = jet_contract(dh, label, stream)
+    return coarse, mp, label
 
 
 def params(k, eps=(3, 100), d=(1, 10), max_rebalance_rounds=32) -> JetParams:

@@ -337,3 +337,8 @@ def hierarchy(h: Hypergraph, levels: int) -> tuple[list, list]:
         hs.insert(0, c)
         maps.insert(0, mp)
     return hs, maps
+
+
+def vertex_order(seed: int, n: int) -> np.ndarray:
+    """A seeded permutation of [0, n) (the random vertex split of a clustering level)."""
+    return stream_u64(seed, n).argsort(kind="stable").astype(np.int32)
