@@ -429,47 +429,79 @@ def run_batched(args, dev):
                       "k from {2, 8, 32}, unit weights, eps = 3/100, hash partitions"}
 
 
-def run_uncoarsen(args, hg, k, dev):
-    """The uncoarsening phase (§7.2): a fixed test hierarchy of the workload (vertex pairs contracted level
-    by level, the finest level being the workload itself), the coarsest level's partition projected and
-    refined (Algorithm 1, schedule 3/4, 3/8, 0, limit 8) at every level -- the whole chain by ONE graph
-    launch per step (jet_uncoarsen).  Each step restores the coarsest level's initial partition first."""
+def run_multilevel(args, hg, k, dev):
+    """The multilevel pass of the paper (Sections 6 and 7.2) on the workload: deterministic coarsening on the
+    GPU (jet_cluster + jet_contract per level; c_max = ceil(c(V) / (160 k)), until at most 160 k vertices
+    remain or a level shrinks by less than 1%), a balanced hash partition of the coarsest level standing in
+    for initial partitioning, then the uncoarsening (projection + Algorithm 1 at every level) as one graph
+    launch (jet_uncoarsen).  Each level's vertex order is a seeded permutation generated beforehand."""
     import torch
 
     from paper_2504_12013_gb300 import jet
-    t0 = time.time()
-    hs, maps = synth.hierarchy(hg, args.uncoarsen_levels)
     stream = torch.cuda.current_stream(dev)
-    ctxs = [jet.jet_ctx_create(jet.DeviceHypergraph(h, dev), jet.params(k), stream) for h in hs]
-    p0 = synth.part_perm(args.seed, hs[0].n, k)
-    states = [jet.JetState(ctxs[0], p0)] + [jet.JetState(c, np.zeros(h.n, np.int32))
-                                            for c, h in zip(ctxs[1:], hs[1:])]
-    init = states[0].part.clone()
-    dmaps = [torch.as_tensor(m).to(dev) for m in maps]
-    log(f"uncoarsen: {len(hs)} levels, n = {[h.n for h in hs]} (set up in {time.time() - t0:.1f}s)")
-    for _ in range(max(args.warmup, 1)):
-        states[0].part.copy_(init)
-        res = jet.jet_uncoarsen(ctxs, dmaps, SCHEDULE, LIMIT, states, stream)
+    limit = 160 * k
+    cmax = -(-int(hg.vwgt.astype(np.int64).sum()) // limit)
+    orders = {}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def coarsen_all():
+        levels, maps, rows = [jet.DeviceHypergraph(hg, dev)], [], []
+        while levels[-1].n > limit:
+            cur = levels[-1]
+            if len(levels) not in orders:
+                orders[len(levels)] = torch.as_tensor(synth.vertex_order(args.seed + len(levels), cur.n)).to(dev)
+            torch.cuda.synchronize(dev)
+            ev0.record(stream)
+            label = jet.jet_cluster(cur, cmax, orders[len(levels)], stream=stream)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_cl = ev0.elapsed_time(ev1)
+            ev0.record(stream)
+            coarse, mp = jet.jet_contract(cur, label, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            rows.append({"n": cur.n, "m": cur.m, "pins": cur.P, "cluster_ms": t_cl, "contract_ms": ev0.elapsed_time(ev1)})
+            if coarse.n > 0.99 * cur.n:
+                break
+            levels.append(coarse)
+            maps.append(mp)
+        return levels, maps, rows
+
+    coarsen_all()  # warm-up (module load, allocator pools); same orders, same result
+    t0 = time.perf_counter()
+    levels, maps, rows = coarsen_all()
+    coarsen_s = time.perf_counter() - t0
+    hs, mps = levels[::-1], maps[::-1]
+    ctxs = [jet.jet_ctx_create(h, jet.params(k), stream) for h in hs]
+    p0 = synth.part_perm(args.seed, hs[0].n, k)
+    states = [jet.JetState(ctxs[0], p0)] + [jet.JetState(c, np.zeros(h.n, np.int32)) for c, h in zip(ctxs[1:], hs[1:])]
+    init = states[0].part.clone()
     times = []
-    for _ in range(args.batch_steps):
+    for it in range(1 + max(args.batch_steps, 1)):
         states[0].part.copy_(init)
         torch.cuda.synchronize(dev)
         ev0.record(stream)
-        res = jet.jet_uncoarsen(ctxs, dmaps, SCHEDULE, LIMIT, states, stream)
+        res = jet.jet_uncoarsen(ctxs, mps, SCHEDULE, LIMIT, states, stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
-        times.append(ev0.elapsed_time(ev1))
+        if it:
+            times.append(ev0.elapsed_time(ev1))
     ms = sum(times) / len(times)
-    work = sum(h.P * r["iterations"] for h, r in zip(hs, res))
     for c in ctxs:
         c.close()
-    return {"value": work / (ms / 1e3), "unit": "pin*iterations/s", "ms_per_hierarchy": ms,
-            "levels": [{"n": h.n, "m": h.m, "pins": h.P, "iterations": r["iterations"],
-                        "initial_objective": r["initial_objective"], "objective": r["objective"],
-                        "balanced": r["balanced"]} for h, r in zip(hs, res)],
-            "what": "project + Algorithm 1 per level of a paired-vertex hierarchy of the workload, one graph "
-                    "launch (jet_uncoarsen); CUDA events, mean of the timed launches"}
+    work = sum(h.P * r["iterations"] for h, r in zip(hs, res))
+    fine = res[-1]
+    return {"coarsening": {"levels": rows, "seconds": coarsen_s, "max_cluster_weight": cmax,
+                           "pins_per_s": sum(r["pins"] for r in rows) / coarsen_s,
+                           "what": "jet_cluster + jet_contract per level, wall time of all levels (host syncs "
+                                   "included), per-level device times in levels"},
+            "uncoarsening": {"ms": ms, "pin_iterations_per_s": work / (ms / 1e3),
+                             "levels": [{"n": h.n, "pins": h.P, "iterations": r["iterations"],
+                                         "initial_objective": r["initial_objective"], "objective": r["objective"],
+                                         "balanced": r["balanced"]} for h, r in zip(hs, res)],
+                             "what": "projection + Algorithm 1 per level, one graph launch; mean over timed launches"},
+            "objective": fine["objective"], "balanced": fine["balanced"],
+            "seconds_total": coarsen_s + ms / 1e3}
 
 
 def run_served(args, dev):
@@ -581,8 +613,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--uncoarsen-levels", type=int, default=3)
-    ap.add_argument("--no-uncoarsen", action="store_true")
+    ap.add_argument("--no-multilevel", action="store_true")
     ap.add_argument("--eager", action="store_true",
                     help="time the kernel-by-kernel form instead of the CUDA graphs (same work and results; "
                          "ncu cannot profile kernels inside graphs with conditional nodes)")
@@ -609,7 +640,7 @@ def main():
     e2e = None if args.no_e2e else run_e2e(args, hg, k, r["part0"], r["dev"])
     batched = None if args.no_batched else run_batched(args, r["dev"])
     served = None if args.no_served else run_served(args, r["dev"])
-    uncoarsen = None if args.no_uncoarsen else run_uncoarsen(args, hg, k, r["dev"])
+    multilevel = None if args.no_multilevel else run_multilevel(args, hg, k, r["dev"])
     cpu = None if args.no_cpu_baseline else cpu_baseline(hg, k, r["part0"], args.cpu_budget)
 
     import json as _j
@@ -686,7 +717,7 @@ def main():
         "cpu_baseline": cpu,
         "batched": batched,
         "served": served,
-        "uncoarsen": uncoarsen,
+        "multilevel": multilevel,
         "matching_schedule": r["schedule"],
         "trace_first_steps": r["trace"][:3],
     }

@@ -15,9 +15,11 @@
 // prefix of its proposers in (weight, id) order that fits, and the accepted
 // vertices move together.
 //
-//   k_cl_serial   the leading one-vertex sub-rounds, one warp, in order
-//   k_cl_rate     warp per vertex: hash table of the neighbour clusters
-//                 (shared memory when small, else a slice of a global pool)
+//   k_cl_serial   the leading one-vertex sub-rounds, one block, in order
+//   k_cl_rate     hash table of the neighbour clusters per vertex, a warp
+//                 per vertex (table in shared memory, else a slice of a
+//                 global pool sized per sub-round)
+//   k_cl_rate_heavy  the whole block per vertex with a very large table
 //   k_cl_swap     swap prevention, group lists of the proposals
 //   k_cl_approve  weight-ordered prefix per target (fast path: all fit)
 //   k_cl_apply    moves, resets the per-sub-round state
@@ -38,6 +40,11 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTile = 2048;        // scan / radix tile: 256 threads x 8 items
 constexpr int kSmemTab = 128;      // hash-table entries per warp held in shared memory
+constexpr int kWarpTab = 2048;     // larger tables: the whole block rates the vertex (heavy vertices)
+constexpr int kBlockTab = 4096;    // a heavy vertex's table in shared memory up to this size
+constexpr int kSetCap = 1024;      // per-warp set of the distinct clusters of one edge (heavy vertices)
+constexpr int kSetEdge = kSetCap / 2;  // edges up to this size are deduplicated in that set
+constexpr size_t kHeavySmem = sizeof(int32_t) * 8 * kSetCap + 16 * kBlockTab;
 constexpr int64_t kMaxTab = 1 << 28;
 
 struct Tab {
@@ -315,19 +322,37 @@ __global__ void k_cl_setup(jet_hypergraph g, int32_t rmax, Cl cl, int *err) {
   }
 }
 
-// Global-pool entries each sub-round needs (tables larger than the shared-memory ones).
+// The sub-round of each position x (bounds[r] <= x < bounds[r+1]).
+__device__ __forceinline__ int round_of(const int32_t *bounds, int32_t rounds, int64_t x) {
+  int lo = 0, hi = rounds - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bounds[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per sub-round: heavy vertices (tables beyond kWarpTab) and the global-pool entries of the tables that
+// fit neither a warp's shared slice nor a block's shared memory.
 __global__ void k_cl_need(const int32_t *order, int32_t n, const int32_t *bounds, int32_t rounds, const int32_t *cap,
-                          unsigned long long *need) {
+                          unsigned long long *need, unsigned long long *heavy) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = cap[order[x]];
     if (c <= kSmemTab) continue;
-    int lo = 0, hi = rounds - 1;  // the sub-round r with bounds[r] <= x < bounds[r+1]
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (bounds[mid] <= x) lo = mid;
-      else hi = mid - 1;
-    }
-    atomicAdd(&need[lo], (unsigned long long)c);
+    const int r = round_of(bounds, rounds, x);
+    if (c > kWarpTab) atomicAdd(&heavy[r], 1ull);
+    if (c <= kWarpTab || c > kBlockTab) atomicAdd(&need[r], (unsigned long long)c);
+  }
+}
+
+// The heavy positions of every sub-round, at hoff[r] onwards (any order within a sub-round).
+__global__ void k_cl_heavy_list(const int32_t *order, int32_t n, const int32_t *bounds, int32_t rounds,
+                                const int32_t *cap, const int64_t *hoff, unsigned long long *hcur, int32_t *hpos) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    if (cap[order[x]] <= kWarpTab) continue;
+    const int r = round_of(bounds, rounds, x);
+    hpos[hoff[r] + (int64_t)atomicAdd(&hcur[r], 1ull)] = (int32_t)x;
   }
 }
 
@@ -400,19 +425,166 @@ __device__ int32_t rate_vertex(const jet_hypergraph &g, int32_t u, const int32_t
   return bk;
 }
 
-// One-vertex sub-rounds x0..x1 in order, by one warp: no swaps, and a proposal always fits
-// (it was rated only if c(C) + c(u) <= cmax), so the vertex moves at once.
-__global__ void __launch_bounds__(32) k_cl_serial(jet_hypergraph g, const int32_t *order, int32_t x0, int32_t x1,
-                                                  long long cmax, int32_t rmax, Cl cl, Tab *pool) {
-  __shared__ Tab s_tab[kSmemTab];
-  const int lane = threadIdx.x;
+__device__ __forceinline__ uint32_t tab_slot(Tab *tab, int32_t cap, int32_t C) {
+  uint32_t h = mix32((uint32_t)C) & (uint32_t)(cap - 1);
+  for (;;) {
+    int32_t k = *(volatile int32_t *)&tab[h].key;
+    if (k == -1) {
+      k = atomicCAS(&tab[h].key, -1, C);
+      if (k == -1) k = C;
+    }
+    if (k == C) return h;
+    h = (h + 1) & (uint32_t)(cap - 1);
+  }
+}
+
+// Inserts C into a warp's set of the clusters of one edge (scap slots, cleared to -1 before the edge);
+// true if it was not there.
+__device__ __forceinline__ bool set_insert(int32_t *set, int32_t scap, int32_t C) {
+  uint32_t h = mix32((uint32_t)C) & (uint32_t)(scap - 1);
+  for (;;) {
+    int32_t k = *(volatile int32_t *)&set[h];
+    if (k == -1) {
+      k = atomicCAS(&set[h], -1, C);
+      if (k == -1) return true;
+    }
+    if (k == C) return false;
+    h = (h + 1) & (uint32_t)(scap - 1);
+  }
+}
+
+// The rating of a heavy vertex by the whole block (same result as rate_vertex).  Its edges are spread
+// over the warps and the sums are atomic (integer, order-free); a cluster counts once per edge through
+// match_any within a chunk and, for edges of 33 to kSetEdge pins, the warp's set of the edge's
+// clusters.  Larger edges follow, by warp 0 alone, counted once per edge and cluster through the
+// entry's last edge.  s_set: 8 warps x kSetCap words; s_bk/s_bv: per-warp reduction scratch.
+__device__ int32_t rate_block(const jet_hypergraph &g, int32_t u, const int32_t *label, const long long *cw,
+                              long long cmax, int32_t rmax, Tab *tab, int32_t cap, int32_t *s_set,
+                              int32_t *s_bk, unsigned long long *s_bv) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+  for (int i = t; i < cap; i += blockDim.x) {
+    tab[i].key = -1;
+    tab[i].last = -1;
+    tab[i].val = 0;
+  }
+  __syncthreads();
+  int32_t *set = s_set + wid * kSetCap;
+  const int64_t i0 = g.vptr[u], i1 = g.vptr[u + 1];
+  bool big = false;
+  for (int64_t i = i0 + wid; i < i1; i += nw) {
+    const int32_t e = g.inc[i];
+    const int64_t p0 = g.eptr[e], p1 = g.eptr[e + 1], size = p1 - p0;
+    if (size < 2 || size > rmax) continue;
+    if (size > kSetEdge) {
+      big = true;
+      continue;
+    }
+    const unsigned long long term = ((unsigned long long)(uint32_t)g.ewgt[e] << 32) / (unsigned long long)(size - 1);
+    int32_t scap = 0;
+    if (size > 32) {
+      scap = 64;
+      while (scap < 2 * size) scap <<= 1;
+      for (int q = lane; q < scap; q += 32) set[q] = -1;
+      __syncwarp();
+    }
+    for (int64_t p = p0; p < p1; p += 32) {
+      int32_t C = -1;
+      if (p + lane < p1) {
+        const int32_t v = g.pins[p + lane];
+        if (v != u) C = label[v];
+      }
+      const unsigned peers = __match_any_sync(kFull, C);
+      if (C >= 0 && C != u && lane == __ffs(peers) - 1 && (size <= 32 || set_insert(set, scap, C)))
+        atomicAdd(&tab[tab_slot(tab, cap, C)].val, term);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) s_bk[wid] = big ? 1 : 0;
+  __syncthreads();
+  int any_big = 0;
+  for (int w = 0; w < nw; ++w) any_big |= s_bk[w];
+  if (any_big && wid == 0) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const int32_t e = g.inc[i];
+      const int64_t p0 = g.eptr[e], p1 = g.eptr[e + 1], size = p1 - p0;
+      if (size <= kSetEdge || size > rmax) continue;
+      const unsigned long long term = ((unsigned long long)(uint32_t)g.ewgt[e] << 32) / (unsigned long long)(size - 1);
+      for (int64_t p = p0; p < p1; p += 32) {
+        int32_t C = -1;
+        if (p + lane < p1) {
+          const int32_t v = g.pins[p + lane];
+          if (v != u) C = label[v];
+        }
+        const unsigned peers = __match_any_sync(kFull, C);
+        if (C >= 0 && C != u && lane == __ffs(peers) - 1) {
+          const uint32_t h = tab_slot(tab, cap, C);
+          if (tab[h].last != e) {
+            tab[h].last = e;
+            tab[h].val += term;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  const long long cu = g.vwgt[u];
+  unsigned long long bv = 0;
+  int32_t bk = -1;
+  for (int i = t; i < cap; i += blockDim.x) {
+    const int32_t k = tab[i].key;
+    if (k < 0 || cw[k] + cu > cmax) continue;
+    const unsigned long long v = tab[i].val;
+    if (bk < 0 || v > bv || (v == bv && k < bk)) {
+      bv = v;
+      bk = k;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ov = __shfl_xor_sync(kFull, bv, o);
+    const int32_t ok = __shfl_xor_sync(kFull, bk, o);
+    if (ok >= 0 && (bk < 0 || ov > bv || (ov == bv && ok < bk))) {
+      bv = ov;
+      bk = ok;
+    }
+  }
+  __syncthreads();  // s_bk reuse
+  if (lane == 0) {
+    s_bk[wid] = bk;
+    s_bv[wid] = bv;
+  }
+  __syncthreads();
+  bk = -1;
+  bv = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int32_t ok = s_bk[w];
+    const unsigned long long ov = s_bv[w];
+    if (ok >= 0 && (bk < 0 || ov > bv || (ov == bv && ok < bk))) {
+      bv = ov;
+      bk = ok;
+    }
+  }
+  __syncthreads();
+  return bk;
+}
+
+// One-vertex sub-rounds x0..x1 in order, by one block: no swaps, and a proposal always fits (it was
+// rated only if c(C) + c(u) <= cmax), so the vertex moves at once.  Dynamic shared memory: kHeavySmem.
+__global__ void __launch_bounds__(256) k_cl_serial(jet_hypergraph g, const int32_t *order, int32_t x0, int32_t x1,
+                                                   long long cmax, int32_t rmax, Cl cl, Tab *pool) {
+  extern __shared__ unsigned long long s_dyn[];
+  __shared__ int32_t s_bk[8];
+  __shared__ unsigned long long s_bv[8];
+  Tab *s_tab = reinterpret_cast<Tab *>(s_dyn);
+  int32_t *s_set = reinterpret_cast<int32_t *>(s_tab + kBlockTab);
   for (int32_t x = x0; x < x1; ++x) {
     const int32_t u = order[x];
     if (cl.csize[u] != 1 || cl.label[u] != u) continue;
     const int32_t cap = cl.cap[u];
-    Tab *tab = cap <= kSmemTab ? s_tab : pool;
-    const int32_t j = rate_vertex(g, u, cl.label, cl.cw, cmax, rmax, tab, cap, lane);
-    if (j >= 0 && lane == 0) {
+    const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, cap <= kBlockTab ? s_tab : pool, cap, s_set,
+                                 s_bk, s_bv);
+    if (j >= 0 && threadIdx.x == 0) {
       const long long c = g.vwgt[u];
       cl.label[u] = j;
       cl.cw[j] += c;
@@ -420,10 +592,12 @@ __global__ void __launch_bounds__(32) k_cl_serial(jet_hypergraph g, const int32_
       cl.csize[j] += 1;
       cl.csize[u] -= 1;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
+// Warp per position of the sub-round: the vertices of tables up to kWarpTab entries (in the warp's
+// shared slice, else a slice of the global pool).
 __global__ void __launch_bounds__(256) k_cl_rate(jet_hypergraph g, const int32_t *order, int32_t a, int32_t b,
                                                  long long cmax, int32_t rmax, Cl cl, Tab *pool,
                                                  unsigned long long *ctr) {
@@ -432,8 +606,8 @@ __global__ void __launch_bounds__(256) k_cl_rate(jet_hypergraph g, const int32_t
   const int64_t x = a + blockIdx.x * 8ll + wid;
   if (x >= b) return;
   const int32_t u = order[x];
-  if (cl.csize[u] != 1 || cl.label[u] != u) return;
   const int32_t cap = cl.cap[u];
+  if (cap > kWarpTab || cl.csize[u] != 1 || cl.label[u] != u) return;
   Tab *tab = s_tab[wid];
   if (cap > kSmemTab) {
     unsigned long long off = 0;
@@ -442,6 +616,31 @@ __global__ void __launch_bounds__(256) k_cl_rate(jet_hypergraph g, const int32_t
   }
   const int32_t j = rate_vertex(g, u, cl.label, cl.cw, cmax, rmax, tab, cap, lane);
   if (lane == 0 && j >= 0) {
+    cl.T[u] = j;
+    atomicAdd(reinterpret_cast<unsigned long long *>(&cl.pw[j]), (unsigned long long)g.vwgt[u]);
+  }
+}
+
+// Block per heavy position of the sub-round (hpos).  Dynamic shared memory: kHeavySmem.
+__global__ void __launch_bounds__(256) k_cl_rate_heavy(jet_hypergraph g, const int32_t *order, const int32_t *hpos,
+                                                       long long cmax, int32_t rmax, Cl cl, Tab *pool,
+                                                       unsigned long long *ctr) {
+  extern __shared__ unsigned long long s_dyn[];
+  __shared__ int32_t s_bk[8];
+  __shared__ unsigned long long s_bv[8];
+  __shared__ unsigned long long s_off;
+  const int32_t u = order[hpos[blockIdx.x]];
+  if (cl.csize[u] != 1 || cl.label[u] != u) return;
+  const int32_t cap = cl.cap[u];
+  Tab *tab = reinterpret_cast<Tab *>(s_dyn);
+  int32_t *s_set = reinterpret_cast<int32_t *>(tab + kBlockTab);
+  if (cap > kBlockTab) {
+    if (threadIdx.x == 0) s_off = atomicAdd(ctr, (unsigned long long)cap);
+    __syncthreads();
+    tab = pool + s_off;
+  }
+  const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, tab, cap, s_set, s_bk, s_bv);
+  if (threadIdx.x == 0 && j >= 0) {
     cl.T[u] = j;
     atomicAdd(reinterpret_cast<unsigned long long *>(&cl.pw[j]), (unsigned long long)g.vwgt[u]);
   }
@@ -798,25 +997,34 @@ int jet_cluster(const jet_hypergraph *hg, const jet_coarsen_params *p, const int
   const std::vector<int32_t> bounds = subround_bounds(n, p->single_subrounds, p->subround_cap_div);
   const int32_t rounds = (int32_t)bounds.size() - 1;
   int32_t *d_bounds = sc.get<int32_t>((int64_t)bounds.size());
-  unsigned long long *d_need = sc.get<unsigned long long>(2 * (int64_t)rounds + 1);  // need[r], then ctr[r]
+  // per sub-round: pool entries, pool cursor, heavy count, heavy cursor
+  unsigned long long *d_need = sc.get<unsigned long long>(4 * (int64_t)rounds);
+  int64_t *d_hoff = sc.get<int64_t>(rounds);
   if (sc.err != cudaSuccess) return cuda_error(sc.err, "jet_cluster: workspace");
+  unsigned long long *d_ctr = d_need + rounds, *d_heavy = d_need + 2 * rounds, *d_hcur = d_need + 3 * rounds;
   cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_need, 0, sizeof(unsigned long long) * (2 * (size_t)rounds + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_need, 0, sizeof(unsigned long long) * 4 * (size_t)rounds, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_bounds, bounds.data(), sizeof(int32_t) * bounds.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(cl.T, 0, sizeof(int32_t) * (size_t)n, s);  // "seen" of the order check
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cl_serial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeavySmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_cl_rate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHeavySmem);
   if (e != cudaSuccess) return cuda_error(e, "jet_cluster");
   rc = validate_hg(hg, d_err, s, sms);
   if (rc != JET_OK) return rc;
   const int g = grid_for(n, 256, sms, 4);
   k_check_order<<<g, 256, 0, s>>>(order, n, cl.T, d_err);
   k_cl_setup<<<g, 256, 0, s>>>(*hg, p->rating_max_edge, cl, d_err);
-  k_cl_need<<<g, 256, 0, s>>>(order, n, d_bounds, rounds, cl.cap, d_need);
+  k_cl_need<<<g, 256, 0, s>>>(order, n, d_bounds, rounds, cl.cap, d_need, d_heavy);
   int h_err = 0;
-  std::vector<unsigned long long> need(rounds);
+  std::vector<unsigned long long> need(rounds), heavy(rounds);
   e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(need.data(), d_need, sizeof(unsigned long long) * (size_t)rounds, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(heavy.data(), d_heavy, sizeof(unsigned long long) * (size_t)rounds, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_error(e, "jet_cluster: set-up");
   if (h_err & 2) return gfail(JET_ERR_DATA, "%s", "order is not a permutation of the vertices");
@@ -824,18 +1032,30 @@ int jet_cluster(const jet_hypergraph *hg, const jet_coarsen_params *p, const int
   if (h_err & 8) return gfail(JET_ERR_OVERFLOW, "%s", "a vertex's rated neighbourhood exceeds 2^27 pins");
   unsigned long long pool_entries = 1;
   for (unsigned long long x : need) pool_entries = std::max(pool_entries, x);
+  std::vector<int64_t> hoff(rounds);
+  int64_t n_heavy = 0;
+  for (int32_t q = 0; q < rounds; ++q) {
+    hoff[q] = n_heavy;
+    n_heavy += (int64_t)heavy[q];
+  }
   Tab *pool = sc.get<Tab>((int64_t)pool_entries);
+  int32_t *hpos = sc.get<int32_t>(n_heavy);
   if (sc.err != cudaSuccess) return cuda_error(sc.err, "jet_cluster: rating tables");
-  // leading one-vertex sub-rounds: one warp, in order
+  e = cudaMemcpyAsync(d_hoff, hoff.data(), sizeof(int64_t) * (size_t)rounds, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_error(e, "jet_cluster");
+  if (n_heavy > 0) k_cl_heavy_list<<<g, 256, 0, s>>>(order, n, d_bounds, rounds, cl.cap, d_hoff, d_hcur, hpos);
+  // leading one-vertex sub-rounds: one block, in order
   int32_t r = 0;
   while (r < rounds && bounds[r + 1] - bounds[r] == 1) ++r;
-  if (r > 0) k_cl_serial<<<1, 32, 0, s>>>(*hg, order, bounds[0], bounds[r], p->max_cluster_weight,
-                                          p->rating_max_edge, cl, pool);
+  if (r > 0) k_cl_serial<<<1, 256, kHeavySmem, s>>>(*hg, order, bounds[0], bounds[r], p->max_cluster_weight,
+                                                    p->rating_max_edge, cl, pool);
   for (; r < rounds; ++r) {
     const int32_t a = bounds[r], b = bounds[r + 1];
     const unsigned gw = (unsigned)((b - a + 7) / 8), gt = (unsigned)((b - a + 255) / 256);
-    k_cl_rate<<<gw, 256, 0, s>>>(*hg, order, a, b, p->max_cluster_weight, p->rating_max_edge, cl, pool,
-                                 d_need + rounds + r);
+    k_cl_rate<<<gw, 256, 0, s>>>(*hg, order, a, b, p->max_cluster_weight, p->rating_max_edge, cl, pool, d_ctr + r);
+    if (heavy[r] > 0)
+      k_cl_rate_heavy<<<(unsigned)heavy[r], 256, kHeavySmem, s>>>(*hg, order, hpos + hoff[r], p->max_cluster_weight,
+                                                                  p->rating_max_edge, cl, pool, d_ctr + r);
     k_cl_swap<<<gt, 256, 0, s>>>(hg->vwgt, order, a, b, cl);
     k_cl_approve<<<gt, 256, 0, s>>>(hg->vwgt, order, a, b, p->max_cluster_weight, cl);
     k_cl_apply<<<gt, 256, 0, s>>>(hg->vwgt, order, a, b, cl);
