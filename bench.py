@@ -429,7 +429,7 @@ def run_batched(args, dev):
                       "k from {2, 8, 32}, unit weights, eps = 3/100, hash partitions"}
 
 
-def run_multilevel(args, hg, k, dev):
+def run_multilevel(args, hg, k, dev, coarsen_only=False):
     """The multilevel pass of the paper (Sections 6 and 7.2) on the workload: deterministic coarsening on the
     GPU (jet_cluster + jet_contract per level; c_max = ceil(c(V) / (160 k)), until at most 160 k vertices
     remain or a level shrinks by less than 1%), a balanced hash partition of the coarsest level standing in
@@ -460,7 +460,10 @@ def run_multilevel(args, hg, k, dev):
             coarse, mp = jet.jet_contract(cur, label, stream)
             ev1.record(stream)
             torch.cuda.synchronize(dev)
-            rows.append({"n": cur.n, "m": cur.m, "pins": cur.P, "cluster_ms": t_cl, "contract_ms": ev0.elapsed_time(ev1)})
+            sz = (cur.eptr[1:] - cur.eptr[:-1]).double()
+            rated = sz[(sz >= 2) & (sz <= jet.RATING_MAX_EDGE)]
+            rows.append({"n": cur.n, "m": cur.m, "pins": cur.P, "cluster_ms": t_cl, "contract_ms": ev0.elapsed_time(ev1),
+                         "rating_pin_visits_bound": int((rated * rated).sum().item())})
             if coarse.n > 0.99 * cur.n:
                 break
             levels.append(coarse)
@@ -471,6 +474,13 @@ def run_multilevel(args, hg, k, dev):
     t0 = time.perf_counter()
     levels, maps, rows = coarsen_all()
     coarsen_s = time.perf_counter() - t0
+    coarsening = {"levels": rows, "seconds": coarsen_s, "max_cluster_weight": cmax,
+                  "pins_per_s": sum(r["pins"] for r in rows) / coarsen_s,
+                  "what": "jet_cluster + jet_contract per level, wall time of all levels (host syncs included), "
+                          "per-level device times in levels; rating_pin_visits_bound = sum of |e|^2 over the "
+                          "rated edges (each vertex of a rated edge visits its pins)"}
+    if coarsen_only:
+        return {"coarsening": coarsening}
     hs, mps = levels[::-1], maps[::-1]
     ctxs = [jet.jet_ctx_create(h, jet.params(k), stream) for h in hs]
     p0 = synth.part_perm(args.seed, hs[0].n, k)
@@ -491,10 +501,7 @@ def run_multilevel(args, hg, k, dev):
         c.close()
     work = sum(h.P * r["iterations"] for h, r in zip(hs, res))
     fine = res[-1]
-    return {"coarsening": {"levels": rows, "seconds": coarsen_s, "max_cluster_weight": cmax,
-                           "pins_per_s": sum(r["pins"] for r in rows) / coarsen_s,
-                           "what": "jet_cluster + jet_contract per level, wall time of all levels (host syncs "
-                                   "included), per-level device times in levels"},
+    return {"coarsening": coarsening,
             "uncoarsening": {"ms": ms, "pin_iterations_per_s": work / (ms / 1e3),
                              "levels": [{"n": h.n, "pins": h.P, "iterations": r["iterations"],
                                          "initial_objective": r["initial_objective"], "objective": r["objective"],
@@ -614,6 +621,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-multilevel", action="store_true")
+    ap.add_argument("--coarsen-only", action="store_true",
+                    help="time only the GPU coarsening of the workload (Section 6) and print its JSON line")
     ap.add_argument("--eager", action="store_true",
                     help="time the kernel-by-kernel form instead of the CUDA graphs (same work and results; "
                          "ncu cannot profile kernels inside graphs with conditional nodes)")
@@ -623,6 +632,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.coarsen_only:
+        return run_coarsen_only(args, rank)
 
     if world > 1:
         import torch
@@ -726,6 +737,21 @@ def main():
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_coarsen_only(args, rank):
+    """Coarsening alone (one warm-up pass, one timed pass over all levels), for profiling."""
+    import torch
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    desc, make = WORKLOADS[args.workload]
+    hg, k, _ = make(args.seed)
+    c = run_multilevel(args, hg, k, dev, coarsen_only=True)["coarsening"]
+    print(json.dumps({"metric": "coarsening pins/s (all levels)", "value": c["pins_per_s"], "unit": "pins/s",
+                      "config": {"workload": desc, "n": hg.n, "m": hg.m, "pins": hg.P, "k": k},
+                      "coarsening": c}), flush=True)
 
 
 def run_reference(args, rank, world):

@@ -42,9 +42,10 @@ constexpr int kTile = 2048;        // scan / radix tile: 256 threads x 8 items
 constexpr int kSmemTab = 128;      // hash-table entries per warp held in shared memory
 constexpr int kWarpTab = 2048;     // larger tables: the whole block rates the vertex (heavy vertices)
 constexpr int kBlockTab = 4096;    // a heavy vertex's table in shared memory up to this size
-constexpr int kSetCap = 1024;      // per-warp set of the distinct clusters of one edge (heavy vertices)
+constexpr int kHeavyWarps = 16;    // warps of a block that rates one heavy vertex
+constexpr int kSetCap = 2048;      // per-warp set of the distinct clusters of one edge (heavy vertices)
 constexpr int kSetEdge = kSetCap / 2;  // edges up to this size are deduplicated in that set
-constexpr size_t kHeavySmem = sizeof(int32_t) * 8 * kSetCap + 16 * kBlockTab;
+constexpr size_t kHeavySmem = sizeof(int32_t) * kHeavyWarps * kSetCap + 16 * kBlockTab;
 constexpr int64_t kMaxTab = 1 << 28;
 
 struct Tab {
@@ -356,6 +357,21 @@ __global__ void k_cl_heavy_list(const int32_t *order, int32_t n, const int32_t *
   }
 }
 
+// Slot of cluster C in a table of cap entries (a power of two above the number of keys), inserted if new.
+__device__ __forceinline__ uint32_t tab_slot(Tab *tab, int32_t cap, int32_t C) {
+  uint32_t h = mix32((uint32_t)C) & (uint32_t)(cap - 1);
+  for (;;) {
+    int32_t k = *(volatile int32_t *)&tab[h].key;
+    if (k == -1) {
+      k = atomicCAS(&tab[h].key, -1, C);
+      if (k == -1) k = C;
+    }
+    if (k == C) return h;
+    h = (h + 1) & (uint32_t)(cap - 1);
+  }
+}
+
+
 // The rating of u over the clusters of its neighbours, accumulated in tab (cap entries, a power of
 // two above twice the rated pins), and the best cluster within the weight bound (-1 if none).
 // Called by a whole warp.
@@ -374,30 +390,27 @@ __device__ int32_t rate_vertex(const jet_hypergraph &g, int32_t u, const int32_t
     const int64_t size = p1 - p0;
     if (size < 2 || size > rmax) continue;
     const unsigned long long term = ((unsigned long long)(uint32_t)g.ewgt[e] << 32) / (unsigned long long)(size - 1);
-    for (int64_t p = p0; p < p1; p += 32) {
-      int32_t C = -1;
-      if (p + lane < p1) {
-        const int32_t v = g.pins[p + lane];
-        if (v != u) C = label[v];
+    for (int64_t p = p0; p < p1; p += 128) {  // four chunks of 32 pins in flight, applied in order
+      int32_t C[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t pp = p + q * 32 + lane;
+        C[q] = pp < p1 ? g.pins[pp] : u;
       }
-      const unsigned peers = __match_any_sync(kFull, C);
-      if (C >= 0 && C != u && lane == __ffs(peers) - 1) {  // one lane per distinct cluster of this chunk
-        uint32_t h = mix32((uint32_t)C) & (uint32_t)(cap - 1);
-        for (;;) {
-          int32_t k = *(volatile int32_t *)&tab[h].key;
-          if (k == -1) {
-            k = atomicCAS(&tab[h].key, -1, C);
-            if (k == -1) k = C;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) C[q] = C[q] != u ? label[C[q]] : -1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned peers = __match_any_sync(kFull, C[q]);
+        if (C[q] >= 0 && C[q] != u && lane == __ffs(peers) - 1) {  // one lane per distinct cluster of this chunk
+          const uint32_t h = tab_slot(tab, cap, C[q]);
+          if (tab[h].last != e) {  // once per edge and cluster
+            tab[h].last = e;
+            tab[h].val += term;
           }
-          if (k == C) break;
-          h = (h + 1) & (uint32_t)(cap - 1);
         }
-        if (tab[h].last != e) {  // once per edge and cluster
-          tab[h].last = e;
-          tab[h].val += term;
-        }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
   const long long cu = g.vwgt[u];
@@ -425,19 +438,6 @@ __device__ int32_t rate_vertex(const jet_hypergraph &g, int32_t u, const int32_t
   return bk;
 }
 
-__device__ __forceinline__ uint32_t tab_slot(Tab *tab, int32_t cap, int32_t C) {
-  uint32_t h = mix32((uint32_t)C) & (uint32_t)(cap - 1);
-  for (;;) {
-    int32_t k = *(volatile int32_t *)&tab[h].key;
-    if (k == -1) {
-      k = atomicCAS(&tab[h].key, -1, C);
-      if (k == -1) k = C;
-    }
-    if (k == C) return h;
-    h = (h + 1) & (uint32_t)(cap - 1);
-  }
-}
-
 // Inserts C into a warp's set of the clusters of one edge (scap slots, cleared to -1 before the edge);
 // true if it was not there.
 __device__ __forceinline__ bool set_insert(int32_t *set, int32_t scap, int32_t C) {
@@ -457,7 +457,8 @@ __device__ __forceinline__ bool set_insert(int32_t *set, int32_t scap, int32_t C
 // over the warps and the sums are atomic (integer, order-free); a cluster counts once per edge through
 // match_any within a chunk and, for edges of 33 to kSetEdge pins, the warp's set of the edge's
 // clusters.  Larger edges follow, by warp 0 alone, counted once per edge and cluster through the
-// entry's last edge.  s_set: 8 warps x kSetCap words; s_bk/s_bv: per-warp reduction scratch.
+// entry's last edge.  s_set: kHeavyWarps x kSetCap words; s_bk/s_bv: per-warp reduction scratch.
+// Chunks of an edge are taken four at a time, so that their loads overlap.
 __device__ int32_t rate_block(const jet_hypergraph &g, int32_t u, const int32_t *label, const long long *cw,
                               long long cmax, int32_t rmax, Tab *tab, int32_t cap, int32_t *s_set,
                               int32_t *s_bk, unsigned long long *s_bv) {
@@ -480,22 +481,35 @@ __device__ int32_t rate_block(const jet_hypergraph &g, int32_t u, const int32_t 
       continue;
     }
     const unsigned long long term = ((unsigned long long)(uint32_t)g.ewgt[e] << 32) / (unsigned long long)(size - 1);
-    int32_t scap = 0;
-    if (size > 32) {
-      scap = 64;
-      while (scap < 2 * size) scap <<= 1;
-      for (int q = lane; q < scap; q += 32) set[q] = -1;
-      __syncwarp();
-    }
-    for (int64_t p = p0; p < p1; p += 32) {
+    if (size <= 32) {
       int32_t C = -1;
-      if (p + lane < p1) {
-        const int32_t v = g.pins[p + lane];
+      if (lane < size) {
+        const int32_t v = g.pins[p0 + lane];
         if (v != u) C = label[v];
       }
       const unsigned peers = __match_any_sync(kFull, C);
-      if (C >= 0 && C != u && lane == __ffs(peers) - 1 && (size <= 32 || set_insert(set, scap, C)))
-        atomicAdd(&tab[tab_slot(tab, cap, C)].val, term);
+      if (C >= 0 && C != u && lane == __ffs(peers) - 1) atomicAdd(&tab[tab_slot(tab, cap, C)].val, term);
+      continue;
+    }
+    int32_t scap = 64;
+    while (scap < 2 * size) scap <<= 1;
+    for (int q = lane; q < scap; q += 32) set[q] = -1;
+    __syncwarp();
+    for (int64_t p = p0; p < p1; p += 128) {
+      int32_t C[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t pp = p + q * 32 + lane;
+        C[q] = pp < p1 ? g.pins[pp] : u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) C[q] = C[q] != u ? label[C[q]] : -1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned peers = __match_any_sync(kFull, C[q]);
+        if (C[q] >= 0 && C[q] != u && lane == __ffs(peers) - 1 && set_insert(set, scap, C[q]))
+          atomicAdd(&tab[tab_slot(tab, cap, C[q])].val, term);
+      }
     }
     __syncwarp();
   }
@@ -571,11 +585,11 @@ __device__ int32_t rate_block(const jet_hypergraph &g, int32_t u, const int32_t 
 
 // One-vertex sub-rounds x0..x1 in order, by one block: no swaps, and a proposal always fits (it was
 // rated only if c(C) + c(u) <= cmax), so the vertex moves at once.  Dynamic shared memory: kHeavySmem.
-__global__ void __launch_bounds__(256) k_cl_serial(jet_hypergraph g, const int32_t *order, int32_t x0, int32_t x1,
+__global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_serial(jet_hypergraph g, const int32_t *order, int32_t x0, int32_t x1,
                                                    long long cmax, int32_t rmax, Cl cl, Tab *pool) {
   extern __shared__ unsigned long long s_dyn[];
-  __shared__ int32_t s_bk[8];
-  __shared__ unsigned long long s_bv[8];
+  __shared__ int32_t s_bk[kHeavyWarps];
+  __shared__ unsigned long long s_bv[kHeavyWarps];
   Tab *s_tab = reinterpret_cast<Tab *>(s_dyn);
   int32_t *s_set = reinterpret_cast<int32_t *>(s_tab + kBlockTab);
   for (int32_t x = x0; x < x1; ++x) {
@@ -622,12 +636,12 @@ __global__ void __launch_bounds__(256) k_cl_rate(jet_hypergraph g, const int32_t
 }
 
 // Block per heavy position of the sub-round (hpos).  Dynamic shared memory: kHeavySmem.
-__global__ void __launch_bounds__(256) k_cl_rate_heavy(jet_hypergraph g, const int32_t *order, const int32_t *hpos,
+__global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_rate_heavy(jet_hypergraph g, const int32_t *order, const int32_t *hpos,
                                                        long long cmax, int32_t rmax, Cl cl, Tab *pool,
                                                        unsigned long long *ctr) {
   extern __shared__ unsigned long long s_dyn[];
-  __shared__ int32_t s_bk[8];
-  __shared__ unsigned long long s_bv[8];
+  __shared__ int32_t s_bk[kHeavyWarps];
+  __shared__ unsigned long long s_bv[kHeavyWarps];
   __shared__ unsigned long long s_off;
   const int32_t u = order[hpos[blockIdx.x]];
   if (cl.csize[u] != 1 || cl.label[u] != u) return;
@@ -1047,14 +1061,14 @@ int jet_cluster(const jet_hypergraph *hg, const jet_coarsen_params *p, const int
   // leading one-vertex sub-rounds: one block, in order
   int32_t r = 0;
   while (r < rounds && bounds[r + 1] - bounds[r] == 1) ++r;
-  if (r > 0) k_cl_serial<<<1, 256, kHeavySmem, s>>>(*hg, order, bounds[0], bounds[r], p->max_cluster_weight,
+  if (r > 0) k_cl_serial<<<1, kHeavyWarps * 32, kHeavySmem, s>>>(*hg, order, bounds[0], bounds[r], p->max_cluster_weight,
                                                     p->rating_max_edge, cl, pool);
   for (; r < rounds; ++r) {
     const int32_t a = bounds[r], b = bounds[r + 1];
     const unsigned gw = (unsigned)((b - a + 7) / 8), gt = (unsigned)((b - a + 255) / 256);
     k_cl_rate<<<gw, 256, 0, s>>>(*hg, order, a, b, p->max_cluster_weight, p->rating_max_edge, cl, pool, d_ctr + r);
     if (heavy[r] > 0)
-      k_cl_rate_heavy<<<(unsigned)heavy[r], 256, kHeavySmem, s>>>(*hg, order, hpos + hoff[r], p->max_cluster_weight,
+      k_cl_rate_heavy<<<(unsigned)heavy[r], kHeavyWarps * 32, kHeavySmem, s>>>(*hg, order, hpos + hoff[r], p->max_cluster_weight,
                                                                   p->rating_max_edge, cl, pool, d_ctr + r);
     k_cl_swap<<<gt, 256, 0, s>>>(hg->vwgt, order, a, b, cl);
     k_cl_approve<<<gt, 256, 0, s>>>(hg->vwgt, order, a, b, p->max_cluster_weight, cl);
