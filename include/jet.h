@@ -168,6 +168,26 @@ int jet_refine_round(jet_ctx *ctx, int32_t tau_num, int32_t tau_den, int32_t *pa
 int jet_set_graph_mode(jet_ctx *ctx, int enable);
 
 /*
+ * Graph path (default off; the paper notes that graphs get a specialised
+ * implementation, Section 7).  Allowed only when every edge has exactly two
+ * distinct pins (JET_ERR_INVALID_ARG otherwise).  For an edge e = {v, u},
+ * Lambda(e) = {Pi(v), Pi(u)} and |e cap V_Pi(v)| > 1 iff Pi(u) = Pi(v), so
+ * gains, rebalancing targets and (lambda-1) (the weighted edge cut) are read
+ * from the neighbours' blocks through an adjacency array built here
+ * (4 bytes per incidence, context-owned), and moves change only Pi and the
+ * block weights: phi and the edge bitmasks are not maintained.  Results are
+ * identical to the hypergraph path.  While the graph path is on: phi
+ * arguments may be NULL; jet_refine_round, jet_rebalance and the rollback
+ * leave phi as it was; jet_refine, batches and jet_uncoarsen rebuild phi
+ * (when not NULL) from the final partition; jet_build_pincounts builds
+ * block_w (and phi when not NULL); jet_quotient_schedule is refused.  After
+ * turning it off, call jet_build_pincounts before the next round.
+ * Switching drops the context's captured graphs; do it before building a
+ * batch of this context.  Synchronizes.
+ */
+int jet_set_graph_path(jet_ctx *ctx, int enable);
+
+/*
  * Deterministic rebalancing (Section 4.3) until no block exceeds L_max, a
  * round moves nothing, or params.max_rebalance_rounds rounds ran.  Per
  * round, from the state at its start: every vertex v of an overloaded block

@@ -81,7 +81,7 @@ cudaError_t reset_counters(jet_ctx *c) {
 }
 
 cudaError_t ensure_masks(jet_ctx *c, const int32_t *phi) {
-  if (c->phi_owner == phi) return cudaSuccess;
+  if (c->graph_path || c->phi_owner == phi) return cudaSuccess;
   return launch_masks_from_phi(c, phi);
 }
 
@@ -224,7 +224,7 @@ cudaError_t capture_iteration(jet_ctx *c, cudaStream_t s_main, cudaStream_t s_bo
     c->stream = s_main;
     if (eb != cudaSuccess) return eb;
     if (e != cudaSuccess) return e;
-    if ((e = launch_objective_masks(c)) != cudaSuccess) return e;
+    if ((e = launch_objective(c, part)) != cudaSuccess) return e;
     return launch_stats(c, bw, stats, 0);
   }();
   c->stream = saved;
@@ -473,7 +473,7 @@ void jet_ctx_destroy(jet_ctx *c) {
   cudaStreamSynchronize(c->stream);
   void *dev[] = {c->cnt, c->v_light, c->e_tiny, c->mask, c->cand, c->rg, c->mv_v, c->mv_st, c->vcount, c->rbb,
                  c->rb_hi, c->rb_v, c->rb_hist, c->rb_ct, c->best_part, c->locked_ws, c->vheavy, c->stats_scratch,
-                 c->ab_seg, c->ab_slot_edge, c->ab_tab, c->ab_nm, c->sched_q, c->sched_counts};
+                 c->ab_seg, c->ab_slot_edge, c->ab_tab, c->ab_nm, c->sched_q, c->sched_counts, c->adj};
   for (void *p : dev) dfree(c, p);
   cudaStreamSynchronize(c->stream);
   for (auto &g : c->graphs) {
@@ -498,7 +498,7 @@ void jet_ctx_destroy(jet_ctx *c) {
 int jet_build_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int64_t *block_w) {
   int rc = check_ctx(c);
   if (rc) return rc;
-  if ((c->n > 0 && !part) || (c->m > 0 && !phi) || !block_w)
+  if ((c->n > 0 && !part) || (c->m > 0 && !phi && !c->graph_path) || !block_w)
     return fail(c, JET_ERR_INVALID_ARG, "part, phi or block_w is NULL");
   CKP(F_PIN, launch_pincounts(c, part, phi, block_w), "pin counts");
   return JET_OK;
@@ -518,7 +518,7 @@ int jet_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, const int32_t *
   if (rc) return rc;
   if ((rc = check_tau(c, tau_num, tau_den))) return rc;
   if (c->n > 0 && (!part || !locked || !target || !gain || !in_m)) return fail(c, JET_ERR_INVALID_ARG, "NULL array");
-  if (c->m > 0 && !phi) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
+  if (c->m > 0 && !phi && !c->graph_path) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
   CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
   CKP(F_CAND, launch_candidates(c, tau_num, tau_den, part, phi, locked), "candidates");
   CKP(F_OTHER, launch_export_candidates(c, target, gain, in_m), "candidates export");
@@ -529,7 +529,7 @@ int jet_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi, int32_t
   int rc = check_ctx(c);
   if (rc) return rc;
   if (c->n > 0 && (!part || !rg || !approved)) return fail(c, JET_ERR_INVALID_ARG, "NULL array");
-  if (c->m > 0 && !phi) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
+  if (c->m > 0 && !phi && !c->graph_path) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
   CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
   CK(reset_counters(c), "counters");
   CKP(F_AB, launch_afterburner(c, part, phi), "afterburner");
@@ -540,12 +540,12 @@ int jet_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi, int32_t
 int jet_rebalance(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w, jet_round_stats *stats) {
   int rc = check_ctx(c);
   if (rc) return rc;
-  if ((c->n > 0 && !part) || (c->m > 0 && !phi) || !block_w)
+  if ((c->n > 0 && !part) || (c->m > 0 && !phi && !c->graph_path) || !block_w)
     return fail(c, JET_ERR_INVALID_ARG, "part, phi or block_w is NULL");
   CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
   CK(reset_counters(c), "counters");
   if ((rc = rebalance_loop(c, part, phi, block_w))) return rc;
-  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_objective(c, part), "objective");
   CKP(F_OBJ, launch_stats(c, block_w, stats ? stats : c->stats_scratch, 1), "stats");
   return JET_OK;
 }
@@ -555,7 +555,7 @@ int jet_refine_round(jet_ctx *c, int32_t tau_num, int32_t tau_den, int32_t *part
   int rc = check_ctx(c);
   if (rc) return rc;
   if ((rc = check_tau(c, tau_num, tau_den))) return rc;
-  if ((c->n > 0 && (!part || !locked)) || (c->m > 0 && !phi) || !block_w)
+  if ((c->n > 0 && (!part || !locked)) || (c->m > 0 && !phi && !c->graph_path) || !block_w)
     return fail(c, JET_ERR_INVALID_ARG, "part, phi, block_w or locked is NULL");
   CKP(F_PIN, ensure_masks(c, phi), "bitmasks");
   if (!stats) stats = c->stats_scratch;
@@ -566,7 +566,7 @@ int jet_refine_round(jet_ctx *c, int32_t tau_num, int32_t tau_den, int32_t *part
   CKP(F_APPROVE, launch_approve(c, locked, nullptr, nullptr, true), "approve");
   CKP(F_APPLY, launch_apply(c, part, phi, block_w), "apply");
   if ((rc = rebalance_loop(c, part, phi, block_w))) return rc;
-  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_objective(c, part), "objective");
   CKP(F_OBJ, launch_stats(c, block_w, stats, 0), "stats");
   return JET_OK;
 }
@@ -578,6 +578,38 @@ int jet_set_graph_mode(jet_ctx *c, int enable) {
   return JET_OK;
 }
 
+int jet_set_graph_path(jet_ctx *c, int enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  enable = enable ? 1 : 0;
+  if (enable == c->graph_path) return JET_OK;
+  if (enable) {
+    if (!c->adj) CK(dalloc(c, &c->adj, (size_t)c->P), "adjacency");
+    int32_t *bad = nullptr;
+    int32_t h_bad = 0;
+    CK(dalloc(c, &bad, 1), "scratch");
+    cudaError_t e = launch_build_adj(c, bad);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    dfree(c, bad);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph path set-up");
+    if (h_bad) return fail(c, JET_ERR_INVALID_ARG, "the graph path needs every edge to have two distinct pins (%d do not)",
+                           h_bad);
+  } else {
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+  }
+  // captured graphs bake in the path: drop them
+  for (auto &g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = jet_ctx::RoundGraph{};
+  }
+  destroy_refine_graph(c);
+  c->graph_path = enable;
+  c->phi_owner = nullptr;  // the bitmasks are stale after the graph path ran
+  return JET_OK;
+}
+
 int jet_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *part, int32_t *phi,
                int64_t *block_w, jet_refine_result *result) {
   int rc = check_ctx(c);
@@ -586,7 +618,7 @@ int jet_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limi
     return fail(c, JET_ERR_INVALID_ARG, "bad schedule (n_tau %d, limit %d)", n_tau, limit);
   for (int i = 0; i < n_tau; ++i)
     if ((rc = check_tau(c, tau_pairs[2 * i], tau_pairs[2 * i + 1]))) return rc;
-  if ((c->n > 0 && !part) || (c->m > 0 && !phi) || !block_w || !result)
+  if ((c->n > 0 && !part) || (c->m > 0 && !phi && !c->graph_path) || !block_w || !result)
     return fail(c, JET_ERR_INVALID_ARG, "part, phi, block_w or result is NULL");
   memset(result, 0, sizeof(*result));
   if (c->use_graphs) return refine_graph(c, tau_pairs, n_tau, limit, part, phi, block_w, result);
@@ -597,7 +629,7 @@ int jet_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limi
   };
   CKP(F_PIN, launch_pincounts(c, part, phi, block_w), "pin counts");
   CK(reset_counters(c), "counters");
-  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_objective(c, part), "objective");
   CKP(F_OBJ, launch_stats(c, block_w, c->stats_scratch, 1), "stats");
   if ((rc = read_stats())) return rc;
   result->initial_objective = st->objective;
@@ -632,8 +664,9 @@ int jet_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, int32_t limi
       CKP(F_APPLY, launch_apply(c, part, phi, block_w), "rollback apply");
     }
   }
+  if (c->graph_path && phi) CKP(F_PIN, launch_pincounts(c, part, phi, block_w), "final pin counts");
   CK(reset_counters(c), "counters");
-  CKP(F_OBJ, launch_objective_masks(c), "objective");
+  CKP(F_OBJ, launch_objective(c, part), "objective");
   CKP(F_OBJ, launch_stats(c, block_w, c->stats_scratch, 1), "stats");
   if ((rc = read_stats())) return rc;
   result->objective = st->objective;
@@ -676,6 +709,7 @@ int jet_quotient_schedule(jet_ctx *c, const int32_t *phi, int32_t *pairs, int32_
                           int32_t *n_rounds) {
   int rc = check_ctx(c);
   if (rc) return rc;
+  if (c->graph_path) return fail(c, JET_ERR_INVALID_ARG, "the matching schedule reads phi: turn the graph path off");
   if (c->m > 0 && !phi) return fail(c, JET_ERR_INVALID_ARG, "phi is NULL");
   if (!pairs || !round_of || !n_pairs || !n_rounds) return fail(c, JET_ERR_INVALID_ARG, "NULL output");
   if (!c->sched_q) {

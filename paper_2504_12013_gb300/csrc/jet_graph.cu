@@ -117,7 +117,7 @@ cudaError_t capture_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, 
     cudaError_t e;
     if ((e = launch_pincounts(c, part, phi, block_w)) != cudaSuccess) return e;
     if ((e = reset_counters(c)) != cudaSuccess) return e;
-    if ((e = launch_objective_masks(c)) != cudaSuccess) return e;
+    if ((e = launch_objective(c, part)) != cudaSuccess) return e;
     if ((e = launch_stats(c, block_w, c->stats_scratch, 1)) != cudaSuccess) return e;
     k_refine_begin<<<1, 1, 0, s0>>>(c->stats_scratch, rs);
     k_snapshot<<<gn, 256, 0, s0>>>(c->best_part, part, c->n, rs);
@@ -165,8 +165,9 @@ cudaError_t capture_refine(jet_ctx *c, const int32_t *tau_pairs, int32_t n_tau, 
       if ((e = launch_rollback_moves(c, part, c->best_part, &rs->have_best)) != cudaSuccess) return e;
       if ((e = launch_apply(c, part, phi, block_w)) != cudaSuccess) return e;
     }
+    if (c->graph_path && phi && (e = launch_pincounts(c, part, phi, block_w)) != cudaSuccess) return e;  // final phi
     if ((e = reset_counters(c)) != cudaSuccess) return e;
-    if ((e = launch_objective_masks(c)) != cudaSuccess) return e;
+    if ((e = launch_objective(c, part)) != cudaSuccess) return e;
     if ((e = launch_stats(c, block_w, c->stats_scratch, 1)) != cudaSuccess) return e;
     k_refine_end<<<1, 1, 0, s0>>>(c->stats_scratch, rs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -350,7 +351,7 @@ int check_batch_args(jet_batch *b, const int32_t *tau, int32_t n_tau, int32_t li
   if (!part || !phi || !block_w) return bfail(b, JET_ERR_INVALID_ARG, "NULL state array list");
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     const jet_ctx *c = b->ctx[i];
-    if ((c->n > 0 && !part[i]) || (c->m > 0 && !phi[i]) || !block_w[i])
+    if ((c->n > 0 && !part[i]) || (c->m > 0 && !phi[i] && !c->graph_path) || !block_w[i])
       return bfail(b, JET_ERR_INVALID_ARG, "NULL state array of an instance");
   }
   return JET_OK;
@@ -511,7 +512,7 @@ int jet_uncoarsen(jet_ctx *const *levels, int32_t n_levels, const int32_t *const
     const jet_ctx *c = levels[l];
     if (!c) return bfail(nullptr, JET_ERR_INVALID_ARG, "a level's context is NULL");
     if (c->k != levels[0]->k) return bfail(nullptr, JET_ERR_INVALID_ARG, "the levels have different k");
-    if ((c->n > 0 && !part[l]) || (c->m > 0 && !phi[l]) || !block_w[l])
+    if ((c->n > 0 && !part[l]) || (c->m > 0 && !phi[l] && !c->graph_path) || !block_w[l])
       return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL state array of a level");
     if (l > 0 && c->n > 0 && !maps[l - 1]) return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL map of a level");
     for (int j = 0; j < l; ++j)

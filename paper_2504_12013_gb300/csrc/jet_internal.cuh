@@ -168,6 +168,10 @@ struct jet_ctx {
   RoundGraph graphs[kGraphCache];
   int graph_next = 0;
   int use_graphs = 1;
+  // graph path (every edge two distinct pins): adj[j] = the other pin of incidence j; phi and the
+  // bitmasks are then not kept up to date (jet_set_graph_path)
+  int graph_path = 0;
+  int32_t *adj = nullptr;
   int capturing = 0;
   cudaStream_t cap_stream[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t graph_ev[2] = {nullptr, nullptr};  // idle targets of the graphs' event-record nodes
@@ -224,7 +228,8 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg);
 cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int64_t *block_w);
 cudaError_t launch_masks_from_phi(jet_ctx *c, const int32_t *phi);
 cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *out);
-cudaError_t launch_objective_masks(jet_ctx *c);
+cudaError_t launch_objective(jet_ctx *c, const int32_t *part);  // (lambda-1) into cnt->objective
+cudaError_t launch_build_adj(jet_ctx *c, int32_t *bad_edges);       // graph path set-up
 // candidates (k_cand.cu)
 cudaError_t prepare_candidate_kernels(jet_ctx *c);
 cudaError_t launch_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, const int32_t *part, const int32_t *phi,

@@ -26,6 +26,7 @@ struct CandArgs {
   const int64_t *vptr;
   const int32_t *inc, *ewgt, *vwgt, *part, *phi;
   const uint32_t *mask;
+  const int32_t *adj;  // graph path: the other pin of every incidence (NULL: hypergraph rows)
   const uint8_t *locked;
   const uint8_t *vheavy;
   const int32_t *vlist;
@@ -177,8 +178,16 @@ __device__ __forceinline__ int32_t accumulate_heavy(const CandArgs &a, int v, in
     if (ok) {
       e = a.inc[j];
       w = a.ewgt[e];
-      load_rows<KWP>(a.mask + (int64_t)e * 2 * KWP, M, M2);
-      if (mask_bit<KWP>(M2, s)) Ap += w;  // phi_e[s] >= 2
+      if (a.adj) {  // e = {v, u}: Lambda(e) = {s, Pi(u)}, and phi_e[s] >= 2 iff Pi(u) = s
+        const int pu = a.part[a.adj[j]];
+#pragma unroll
+        for (int q = 0; q < KWP; ++q)
+          M[q] = ((s >> 5) == q ? 1u << (s & 31) : 0u) | ((pu >> 5) == q ? 1u << (pu & 31) : 0u);
+        if (pu == s) Ap += w;
+      } else {
+        load_rows<KWP>(a.mask + (int64_t)e * 2 * KWP, M, M2);
+        if (mask_bit<KWP>(M2, s)) Ap += w;  // phi_e[s] >= 2
+      }
     }
     const int cntc = (int)((j1 - base) < 32 ? (j1 - base) : 32);
     for (int l = 0; l < cntc; ++l) {
@@ -391,6 +400,32 @@ __device__ __forceinline__ int32_t stage_accumulate(const CandArgs &a, uint8_t *
     for (int p = 0; p < NP; ++p) pl[p][q] = 0;
   }
   int32_t A = 0;
+  if (a.adj) {  // graph path: e = {v, u} gives Lambda(e) = {s, Pi(u)}; four neighbours in flight
+    for (int j = 0; j < deg; j += 4) {
+      int pu[4], w[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) pu[t] = j + t < deg ? a.adj[j0 + j + t] : -1;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        w[t] = UNIT || pu[t] < 0 ? 1 : a.ewgt[a.inc[j0 + j + t]];
+        pu[t] = pu[t] >= 0 ? a.part[pu[t]] : -1;
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (pu[t] < 0) continue;
+        uint32_t M[KWP];
+#pragma unroll
+        for (int qq = 0; qq < KWP; ++qq)
+          M[qq] = ((s >> 5) == qq ? 1u << (s & 31) : 0u) | ((pu[t] >> 5) == qq ? 1u << (pu[t] & 31) : 0u);
+        if (pu[t] == s) A += w[t];
+#pragma unroll
+        for (int qq = 0; qq < KWP; ++qq) any[qq] |= M[qq];
+        if (UNIT) add_one<KWP, NP>(pl, M);
+        else add_weighted<KWP, NP>(pl, M, (uint32_t)w[t]);
+      }
+    }
+    return A;
+  }
   const int nb = (deg + R - 1) / R;
   int e[R];
   auto load_inc = [&](int b) {
@@ -804,6 +839,7 @@ CandArgs make_args(jet_ctx *c, const int32_t *part, const int32_t *phi) {
   a.part = part;
   a.phi = phi;
   a.mask = c->mask;
+  a.adj = c->graph_path ? c->adj : nullptr;
   a.k = c->k;
   a.cand = c->cand;
   a.rbb = c->rbb;

@@ -25,6 +25,7 @@ struct MoveArgs {
   const int32_t *mv_v;
   const uint32_t *mv_st;
   int32_t k, kwp;
+  int graph;  // graph path: phi and the bitmasks are not kept, a move changes Pi and c(V_i) only
   Counters *cnt;
 };
 
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
     const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
     const int64_t j1 = a.vptr[v + 1];
     if (sub == 0) pins += (unsigned long long)(j1 - a.vptr[v]);
+    if (a.graph) continue;
     for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
       const int64_t e = a.inc[j];
       const int os = atomicSub(&a.phi[e * a.k + s], 1);  // os -> os - 1
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(256) k_rb_apply(RbArgs r, MoveArgs a) {
           pins += (unsigned long long)(j1 - j0);
         }
         const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
-        for (int64_t j = j0 + sub; j < j1; j += kMoveLanes) {
+        for (int64_t j = a.graph ? j1 : j0 + sub; j < j1; j += kMoveLanes) {
           const int64_t e = a.inc[j];
           const int os = atomicSub(&a.phi[e * a.k + s], 1);  // os -> os - 1
           const int ot = atomicAdd(&a.phi[e * a.k + t], 1);  // ot -> ot + 1
@@ -429,6 +431,7 @@ MoveArgs move_args(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   a.bw = block_w;
   a.vcount = c->vcount;
   a.mask = c->mask;
+  a.graph = c->graph_path;
   a.mv_v = c->mv_v;
   a.mv_st = c->mv_st;
   a.k = c->k;

@@ -270,6 +270,37 @@ __global__ void __launch_bounds__(256) k_objective_masks(const uint32_t *mask, c
   if (threadIdx.x == 0 && tot) add_i64(&cnt->objective, tot);
 }
 
+// (lambda-1) of a graph (every edge two pins): the weighted edge cut.
+__global__ void __launch_bounds__(256) k_objective_cut(const int64_t *eptr, const int32_t *pins, const int32_t *part,
+                                                       const int32_t *ewgt, int32_t m, Counters *cnt) {
+  long long acc = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = eptr[e];
+    if (part[pins[p]] != part[pins[p + 1]]) acc += ewgt[e];
+  }
+  long long tot = block_sum_ll(acc);
+  if (threadIdx.x == 0 && tot) add_i64(&cnt->objective, tot);
+}
+
+// Edges that are not two distinct pins (the graph path needs none).
+__global__ void k_count_non_pairs(const int64_t *eptr, const int32_t *pins, int32_t m, int32_t *bad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = eptr[e];
+    if (eptr[e + 1] - p != 2 || pins[p] == pins[p + 1]) atomicAdd(bad, 1);
+  }
+}
+
+// adj[j] = the other pin of edge inc[j], for every incidence j of every vertex.
+__global__ void k_build_adj(const int64_t *vptr, const int32_t *inc, const int64_t *eptr, const int32_t *pins,
+                            int32_t n, int32_t *adj) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t j = vptr[v]; j < vptr[v + 1]; ++j) {
+      const int64_t p = eptr[inc[j]];
+      adj[j] = pins[p] == (int32_t)v ? pins[p + 1] : pins[p];
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_validate(jet_ctx *c, int64_t *wdeg_tmp, int32_t *degcount_tmp, unsigned long long *scal) {
@@ -389,7 +420,7 @@ cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int6
   cudaError_t e = cudaMemsetAsync(block_w, 0, sizeof(int64_t) * c->k, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->vcount, 0, sizeof(int32_t) * c->k, s);
   if (e != cudaSuccess) return e;
-  if (c->m > 0) {
+  if (c->m > 0 && phi) {
     const int threads = 256;
     size_t smem = (size_t)(threads / 32) * c->k * sizeof(int);
     k_pincounts<<<grid_for((int64_t)c->m * 32, threads, c->launch_sms), threads, smem, s>>>(
@@ -428,11 +459,31 @@ cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *o
   return cudaGetLastError();
 }
 
-cudaError_t launch_objective_masks(jet_ctx *c) {
+cudaError_t launch_objective(jet_ctx *c, const int32_t *part) {
   cudaError_t e = cudaMemsetAsync(&c->cnt->objective, 0, sizeof(long long), c->stream);
   if (e != cudaSuccess || c->m == 0) return e;
-  k_objective_masks<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->mask, c->ewgt, c->m, c->kwp, c->cnt);
+  if (c->graph_path)
+    k_objective_cut<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->eptr, c->pins, part, c->ewgt, c->m,
+                                                                             c->cnt);
+  else
+    k_objective_masks<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->mask, c->ewgt, c->m, c->kwp,
+                                                                               c->cnt);
   ++c->kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_adj(jet_ctx *c, int32_t *bad_edges) {
+  cudaError_t e = cudaMemsetAsync(bad_edges, 0, sizeof(int32_t), c->stream);
+  if (e != cudaSuccess) return e;
+  if (c->m > 0) {
+    k_count_non_pairs<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->eptr, c->pins, c->m, bad_edges);
+    ++c->kernel_launches;
+  }
+  if (c->n > 0 && c->adj) {
+    k_build_adj<<<grid_for(c->n, 256, c->launch_sms), 256, 0, c->stream>>>(c->vptr, c->inc, c->eptr, c->pins, c->n,
+                                                                         c->adj);
+    ++c->kernel_launches;
+  }
   return cudaGetLastError();
 }
 

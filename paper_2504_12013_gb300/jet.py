@@ -28,7 +28,7 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune",
            "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
            "jet_server_last_error", "jet_server_destroy", "jet_profile_work", "jet_quotient_schedule",
-           "jet_uncoarsen", "jet_cluster", "jet_contract")
+           "jet_uncoarsen", "jet_cluster", "jet_contract", "jet_set_graph_path")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -117,6 +117,7 @@ def load_library():
             lib.jet_profile_read.argtypes = [_P, pp(ctypes.c_double), pp(i64), pp(i64), ctypes.c_int]
             lib.jet_block_weights_noalloc.argtypes = [_P, _P, i32, i32, _P, _P, _P]
             lib.jet_set_graph_mode.argtypes = [_P, ctypes.c_int]
+            lib.jet_set_graph_path.argtypes = [_P, ctypes.c_int]
             lib.jet_profile_work.argtypes = [_P, pp(i64), i32]
             lib.jet_quotient_schedule.argtypes = [_P, _P, _P, _P, pp(i32), pp(i32)]
             lib.jet_uncoarsen.argtypes = [pp(_P), i32, pp(_P), pp(i32), i32, i32, pp(_P), pp(_P), pp(_P),
@@ -371,6 +372,11 @@ def jet_set_graph_mode(ctx: Ctx, enable: bool = True):
     _check(load_library().jet_set_graph_mode(ctx.handle, 1 if enable else 0), ctx)
 
 
+def jet_set_graph_path(ctx: Ctx, enable: bool = True):
+    """Graph path (every edge two distinct pins): neighbour blocks instead of phi; phi is not maintained."""
+    _check(load_library().jet_set_graph_path(ctx.handle, 1 if enable else 0), ctx)
+
+
 def jet_profile_enable(ctx: Ctx, enable: bool = True):
     _check(load_library().jet_profile_enable(ctx.handle, 1 if enable else 0), ctx)
 
@@ -590,12 +596,13 @@ def jet_server_load(server: Server) -> dict:
 class JetState:
     """Device state of one refinement: Pi, phi, c(V_i), locks and a stats slot."""
 
-    def __init__(self, ctx: Ctx, part):
+    def __init__(self, ctx: Ctx, part, with_phi: bool = True):
         import torch
         dev = ctx.hg.eptr.device
         self.ctx = ctx
         self.part = torch.as_tensor(part, dtype=torch.int32).to(dev).contiguous()
-        self.phi = torch.empty(max(ctx.hg.m * ctx.k, 1), dtype=torch.int32, device=dev)
+        # without phi (graph path only): no m*k table at all
+        self.phi = torch.empty(max(ctx.hg.m * ctx.k, 1), dtype=torch.int32, device=dev) if with_phi else None
         self.block_w = torch.empty(ctx.k, dtype=torch.int64, device=dev)
         self.locked = torch.zeros(max(ctx.hg.n, 1), dtype=torch.uint8, device=dev)
         self.stats = torch.zeros(8, dtype=torch.int64, device=dev)

@@ -342,3 +342,43 @@ def hierarchy(h: Hypergraph, levels: int) -> tuple[list, list]:
 def vertex_order(seed: int, n: int) -> np.ndarray:
     """A seeded permutation of [0, n) (the random vertex split of a clustering level)."""
     return stream_u64(seed, n).argsort(kind="stable").astype(np.int32)
+
+
+def from_pairs(n: int, u: np.ndarray, v: np.ndarray, vwgt=None, ewgt=None) -> Hypergraph:
+    """A graph as a hypergraph of two-pin edges (pins of each edge ascending), both CSR views."""
+    m = len(u)
+    lo = np.minimum(u, v).astype(np.int32)
+    hi = np.maximum(u, v).astype(np.int32)
+    pins = np.empty(2 * m, np.int32)
+    pins[0::2], pins[1::2] = lo, hi
+    eptr = (2 * np.arange(m + 1, dtype=np.int64))
+    eid = np.repeat(np.arange(m, dtype=np.int32), 2)
+    order = np.lexsort((eid, pins))
+    inc = eid[order]
+    vptr = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(pins, minlength=n), out=vptr[1:])
+    vw = np.ones(n, np.int32) if vwgt is None else np.asarray(vwgt, np.int32)
+    ew = np.ones(m, np.int32) if ewgt is None else np.asarray(ewgt, np.int32)
+    return Hypergraph(n=n, m=m, eptr=eptr, pins=pins, vptr=vptr, inc=inc, vwgt=vw, ewgt=ew)
+
+
+def graph(seed: int, n: int, m: int, *, local: float = 0.8, window: int = 1000, c_max: int = 1,
+          w_max: int = 1) -> Hypergraph:
+    """Seeded graph with m edges {u, v}, u != v: u uniform; with probability `local` v is u plus an offset
+    uniform in [1, window] (mod n), otherwise uniform over the other vertices.  Parallel edges may occur.
+    c uniform in 1..c_max, omega uniform in 1..w_max."""
+    r = stream_u64(seed, 4 * m + n)
+    u = (r[:m] % np.uint64(n)).astype(np.int64)
+    is_local = (r[m:2 * m] % np.uint64(1 << 20)).astype(np.float64) < local * (1 << 20)
+    off_local = 1 + (r[2 * m:3 * m] % np.uint64(min(window, n - 1))).astype(np.int64)
+    off_far = 1 + (r[2 * m:3 * m] % np.uint64(n - 1)).astype(np.int64)
+    v = (u + np.where(is_local, off_local, off_far)) % n
+    ew = 1 + (r[3 * m:4 * m] % np.uint64(w_max)).astype(np.int32)
+    vw = 1 + (r[4 * m:4 * m + n] % np.uint64(c_max)).astype(np.int32)
+    return from_pairs(n, u, v, vwgt=vw, ewgt=ew)
+
+
+def config_graph_16m(seed: int = 1):
+    """n=4,000,000, m=16,000,000 two-pin edges (80 % within +-1,000 ids), unit weights, k=64."""
+    h = graph(seed, 4_000_000, 16_000_000)
+    return h, 64, part_perm(seed, h.n, 64)
