@@ -511,6 +511,50 @@ def run_multilevel(args, hg, k, dev, coarsen_only=False):
             "seconds_total": coarsen_s + ms / 1e3}
 
 
+def run_graph(args, dev):
+    """The graph path (jet_set_graph_path) against the hypergraph path on a graph: 4M vertices, 16M two-pin
+    edges (80 % local), k = 64.  The same K Jet iterations at tau = 3/4 from the same partition, each path
+    one graph launch per iteration, CUDA events; the final partitions must be identical."""
+    import torch
+
+    from paper_2504_12013_gb300 import jet
+    t0 = time.time()
+    hg, k, part0 = synth.config_graph_16m(args.seed)
+    gen_s = time.time() - t0
+    stream = torch.cuda.current_stream(dev)
+    dh = jet.DeviceHypergraph(hg, dev)
+    out = {}
+    parts = {}
+    for name, graph_path in (("hypergraph_path", False), ("graph_path", True)):
+        ctx = jet.jet_ctx_create(dh, jet.params(k), stream)
+        if graph_path:
+            jet.jet_set_graph_path(ctx, True)
+        st = jet.JetState(ctx, part0, with_phi=not graph_path)
+        for _ in range(max(args.warmup, 1)):
+            st.round(TAU)
+        st = jet.JetState(ctx, part0, with_phi=not graph_path)
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st.round(TAU)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / args.steps
+        stats = st.stats_dict()
+        parts[name] = st.part.cpu().numpy()[: hg.n]
+        out[name] = {"ms_per_step": ms, "pins_per_s": hg.P / (ms / 1e3), "objective": stats["objective"],
+                     "phi_bytes": 0 if graph_path else hg.m * k * 4}
+        ctx.close()
+        del st
+    out["speedup"] = out["hypergraph_path"]["ms_per_step"] / out["graph_path"]["ms_per_step"]
+    out["results_identical"] = bool(np.array_equal(parts["hypergraph_path"], parts["graph_path"]))
+    out["config"] = {"n": hg.n, "m": hg.m, "pins": hg.P, "k": k, "steps": args.steps, "tau": "3/4",
+                     "generated_s": round(gen_s, 1),
+                     "workload": "graph: u uniform, v = u + U[1, 1000] (80 %) or uniform (20 %), unit weights"}
+    return out
+
+
 def run_served(args, dev):
     """The served form: refinement requests (P log-uniform in [10k, 5M], n = P / 3.85, m = 1.1 n,
     |e| = 2 + Geometric(0.4) <= 256, c in 1..8, k from {2, 4, ..., 256}, balanced random partitions, each
@@ -621,6 +665,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-multilevel", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--coarsen-only", action="store_true",
                     help="time only the GPU coarsening of the workload (Section 6) and print its JSON line")
     ap.add_argument("--eager", action="store_true",
@@ -652,6 +697,7 @@ def main():
     batched = None if args.no_batched else run_batched(args, r["dev"])
     served = None if args.no_served else run_served(args, r["dev"])
     multilevel = None if args.no_multilevel else run_multilevel(args, hg, k, r["dev"])
+    graph = None if args.no_graph else run_graph(args, r["dev"])
     cpu = None if args.no_cpu_baseline else cpu_baseline(hg, k, r["part0"], args.cpu_budget)
 
     import json as _j
@@ -729,6 +775,7 @@ def main():
         "batched": batched,
         "served": served,
         "multilevel": multilevel,
+        "graph": graph,
         "matching_schedule": r["schedule"],
         "trace_first_steps": r["trace"][:3],
     }
