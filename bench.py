@@ -279,19 +279,25 @@ def run_gpu(args, rank, world):
 
 def schedule_timing(jet, ctx, st, stream, dev):
     """Matching schedule of the quotient graph (Section 5) of the partition after the timed steps: the
-    quotient kernel over every edge bitmask row plus the one-block schedule kernel, device time."""
+    quotient kernel over every edge bitmask row plus the one-warp schedule kernel.  Device time from the
+    context's event pairs around the two kernels; the call time adds the host's result copies."""
     import torch
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times = []
+    jet.jet_profile_read(ctx, reset=True)
+    jet.jet_profile_enable(ctx, True)
     for _ in range(3):
         ev0.record(stream)
         pairs, rnd, nr = jet.jet_quotient_schedule(ctx, st.phi)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         times.append(ev0.elapsed_time(ev1))
-    return {"ms": min(times), "pairs": int(len(pairs)), "rounds": int(nr),
+    prof = jet.jet_profile_read(ctx, reset=True)["other"]
+    jet.jet_profile_enable(ctx, False)
+    return {"ms": prof["ms"] / max(prof["calls"], 1), "call_ms": min(times), "pairs": int(len(pairs)),
+            "rounds": int(nr), "launches_per_call": prof["launches"] / max(prof["calls"], 1),
             "what": "quotient graph of the partition after the timed steps and its rounds of maximal matchings "
-                    "(jet_quotient_schedule, Section 5)"}
+                    "(jet_quotient_schedule, Section 5): device time of the kernels; call_ms with the host copies"}
 
 
 def run_e2e(args, hg, k, part0, dev):

@@ -8,10 +8,10 @@
 // k_quotient builds Q as k rows of KWP bit words from the edge bitmasks
 // Lambda(e) (for every block i of Lambda(e), row i |= Lambda(e)), aggregated
 // per thread block in shared memory.  k_schedule runs the rounds in one
-// thread block (thread j owns block j): per round the blocks are sorted by
-// (remaining degree desc, id asc); each one still unmatched in its turn
-// takes its unmatched remaining neighbour of the largest remaining degree
-// (ties to the smaller id).
+// warp: per round the blocks are ordered by (remaining degree at the round's
+// start desc, id asc); each one still unmatched in its turn takes its
+// unmatched remaining neighbour of the largest such degree (ties to the
+// smaller id).
 #include "jet_internal.cuh"
 
 namespace jet {
@@ -47,85 +47,102 @@ __global__ void __launch_bounds__(256) k_quotient(const uint32_t *mask, int32_t 
     if (s_q[x]) atomicOr(&q[x], s_q[x]);
 }
 
-// Bitonic sort of blockDim.x (a power of two >= k) keys in shared memory, ascending.
-__device__ __forceinline__ void block_sort(uint32_t *key) {
-  const int n = blockDim.x, t = threadIdx.x;
-  for (int size = 2; size <= n; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      const int o = t ^ stride;
-      if (o > t) {
-        const bool up = (t & size) == 0;
-        const uint32_t a = key[t], b = key[o];
-        if ((a > b) == up) {
-          key[t] = b;
-          key[o] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kMaxK) k_schedule(const uint32_t *q, int32_t k, int kwp, int32_t *pairs,
-                                                     int32_t *round_of, int32_t *out_counts) {
+// The schedule by one warp: lane l owns blocks l, l+32, ...  Per round the
+// blocks are ordered by (remaining degree desc, id asc) with a stable
+// counting sort over the degrees; each turn is one warp-wide maximum of the
+// partner bids (degree + 1) << 8 | (255 - id), so no block-level barrier is
+// needed anywhere.
+__global__ void __launch_bounds__(32) k_schedule(const uint32_t *q, int32_t k, int kwp, int32_t *pairs,
+                                                 int32_t *round_of, int32_t *out_counts) {
   __shared__ uint32_t s_rem[kMaxK * 8];
-  __shared__ uint32_t s_key[kMaxK];
   __shared__ int s_deg[kMaxK];
   __shared__ int s_matched[kMaxK];
-  __shared__ int s_best[kMaxK / 32];
-  __shared__ int s_np, s_left;
-  const int j = threadIdx.x, lane = j & 31, wid = j >> 5;
-  for (int x = j; x < k * kwp; x += blockDim.x) s_rem[x] = q[x];
-  __syncthreads();
-  if (j < k) s_rem[j * kwp + (j >> 5)] &= ~(1u << (j & 31));  // no self pairs
-  if (j == 0) s_np = 0;
-  __syncthreads();
-  int round = 0;
+  __shared__ int s_order[kMaxK];
+  __shared__ int s_cnt[kMaxK];
+  const int lane = threadIdx.x;
+  const unsigned lt = (1u << lane) - 1;
+  for (int x = lane; x < k * kwp; x += 32) s_rem[x] = q[x];
+  __syncwarp();
+  for (int j = lane; j < k; j += 32) s_rem[j * kwp + (j >> 5)] &= ~(1u << (j & 31));  // no self pairs
+  __syncwarp();
+  int np = 0, round = 0;
   for (;;) {
-    int d = 0;
-    if (j < k)
+    int left = 0;
+    for (int j = lane; j < k; j += 32) {
+      int d = 0;
       for (int w = 0; w < kwp; ++w) d += __popc(s_rem[j * kwp + w]);
-    s_deg[j] = d;
-    s_matched[j] = 0;
-    // (degree desc, id asc): ascending keys (255 - degree) << 8 | id; absent blocks sort last
-    s_key[j] = j < k ? ((uint32_t)(255 - d) << 8) | (uint32_t)j : 0xffffffffu;
-    if (j == 0) s_left = 0;
-    __syncthreads();
-    if (d) atomicAdd(&s_left, d);
-    block_sort(s_key);  // ends with a barrier
-    if (s_left == 0) break;
-    for (int x = 0; x < k; ++x) {
-      const int i = (int)(s_key[x] & 255);
-      if (s_deg[i] == 0) break;  // the rest have no remaining edge
-      if (s_matched[i]) continue;  // uniform: shared state
-      // this thread's bid: its block j as i's partner
-      const bool cand = j < k && !s_matched[j] && ((s_rem[i * kwp + (j >> 5)] >> (j & 31)) & 1u);
-      int bid = cand ? (s_deg[j] << 8) | (255 - j) : -1;
+      s_deg[j] = d;
+      s_matched[j] = 0;
+      left += d;
+    }
+    for (int x = lane; x < kMaxK; x += 32) s_cnt[x] = 0;
+    left = __reduce_add_sync(kFull, left);
+    if (left == 0) break;
+    __syncwarp();
+    // stable counting sort by key 255 - degree (degree desc), ids ascending within a key
+    for (int j = lane; j < k; j += 32) atomicAdd(&s_cnt[255 - s_deg[j]], 1);
+    __syncwarp();
+    {
+      int v[8], sum = 0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) bid = max(bid, __shfl_xor_sync(kFull, bid, o));
-      if (lane == 0) s_best[wid] = bid;
-      __syncthreads();
-      if (j == 0) {
-        int b = -1;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = max(b, s_best[w]);
-        if (b >= 0) {
-          const int p = 255 - (b & 255);
-          s_matched[i] = s_matched[p] = 1;
-          s_rem[i * kwp + (p >> 5)] &= ~(1u << (p & 31));
-          s_rem[p * kwp + (i >> 5)] &= ~(1u << (i & 31));
-          pairs[2 * s_np] = i;
-          pairs[2 * s_np + 1] = p;
-          round_of[s_np] = round;
-          ++s_np;
-        }
+      for (int t = 0; t < 8; ++t) {
+        v[t] = s_cnt[lane * 8 + t];
+        sum += v[t];
       }
-      __syncthreads();
+      int incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int run = incl - sum;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        s_cnt[lane * 8 + t] = run;
+        run += v[t];
+      }
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < k; c0 += 32) {
+      const int j = c0 + lane;
+      const int key = j < k ? 255 - s_deg[j] : 256 + lane;
+      const unsigned peers = __match_any_sync(kFull, key);
+      const int rank = __popc(peers & lt);
+      const int base = j < k ? s_cnt[key] : 0;
+      __syncwarp();
+      if (j < k) {
+        s_order[base + rank] = j;
+        if (rank == 0) s_cnt[key] = base + __popc(peers);
+      }
+      __syncwarp();
+    }
+    for (int x = 0; x < k; ++x) {
+      const int i = s_order[x];
+      if (s_deg[i] == 0) break;  // the rest have no remaining edge
+      if (s_matched[i]) continue;
+      unsigned bid = 0;
+      for (int j = lane; j < k; j += 32)
+        if (!s_matched[j] && ((s_rem[i * kwp + (j >> 5)] >> (j & 31)) & 1u))
+          bid = max(bid, ((unsigned)(s_deg[j] + 1) << 8) | (unsigned)(255 - j));
+      bid = __reduce_max_sync(kFull, bid);
+      if (bid == 0) continue;
+      const int p = 255 - (int)(bid & 255u);
+      if (lane == 0) {
+        s_matched[i] = s_matched[p] = 1;
+        s_rem[i * kwp + (p >> 5)] &= ~(1u << (p & 31));
+        s_rem[p * kwp + (i >> 5)] &= ~(1u << (i & 31));
+        pairs[2 * np] = i;
+        pairs[2 * np + 1] = p;
+        round_of[np] = round;
+      }
+      ++np;
+      __syncwarp();
     }
     ++round;
-    __syncthreads();
+    __syncwarp();
   }
-  if (j == 0) {
-    out_counts[0] = s_np;
+  if (lane == 0) {
+    out_counts[0] = np;
     out_counts[1] = round;
   }
 }
@@ -140,7 +157,7 @@ cudaError_t launch_quotient_schedule(jet_ctx *c, uint32_t *qbits, int32_t *pairs
     k_quotient<<<grid_for(c->m, 256, c->launch_sms, 4), 256, 0, c->stream>>>(c->mask, c->m, c->kwp, c->k, qbits);
     ++c->kernel_launches;
   }
-  k_schedule<<<1, kMaxK, 0, c->stream>>>(qbits, c->k, c->kwp, pairs, round_of, counts);
+  k_schedule<<<1, 32, 0, c->stream>>>(qbits, c->k, c->kwp, pairs, round_of, counts);
   ++c->kernel_launches;
   return cudaGetLastError();
 }
