@@ -549,8 +549,20 @@ def run_graph(args, dev):
         ms = ev0.elapsed_time(ev1) / args.steps
         stats = st.stats_dict()
         parts[name] = st.part.cpu().numpy()[: hg.n]
+        # untimed kernel-by-kernel replay of the same steps: device time per kernel family
+        st = jet.JetState(ctx, part0, with_phi=not graph_path)
+        jet.jet_set_graph_mode(ctx, False)
+        jet.jet_profile_read(ctx, reset=True)
+        jet.jet_profile_enable(ctx, True)
+        for _ in range(args.steps):
+            st.round(TAU)
+        prof = jet.jet_profile_read(ctx, reset=True)
+        jet.jet_profile_enable(ctx, False)
+        assert st.stats_dict() == stats, "replay diverged from the timed run"
         out[name] = {"ms_per_step": ms, "pins_per_s": hg.P / (ms / 1e3), "objective": stats["objective"],
-                     "phi_bytes": 0 if graph_path else hg.m * k * 4}
+                     "phi_bytes": 0 if graph_path else hg.m * k * 4,
+                     "family_ms_per_step_replay": {f: round(v["ms"] / args.steps, 4) for f, v in prof.items()
+                                                   if v["ms"] > 0}}
         ctx.close()
         del st
     out["speedup"] = out["hypergraph_path"]["ms_per_step"] / out["graph_path"]["ms_per_step"]

@@ -531,10 +531,84 @@ __global__ void k_export_cand(const uint64_t *cand, int32_t n, int32_t *target, 
   }
 }
 
+// Graph path: for a two-pin edge e = {v, u} the replay of Algorithm 2 gives v
+// +omega(e) when u's block at v's turn differs from s (the last departure) and
+// -omega(e) when it differs from t (the first arrival); u's block at v's turn
+// is t(u) if u is a candidate ordered before v, else Pi(u).  So rg(v) is a
+// sum over v's neighbours, computed per candidate with no atomics: a lane per
+// vertex of degree <= 64 (four neighbours in flight), the whole warp for
+// larger degrees.
+struct AbGraphArgs {
+  const int64_t *vptr;
+  const int32_t *adj, *inc, *ewgt, *part;
+  const uint64_t *cand;
+  int32_t *rg;
+  int32_t n;
+  int unit;
+};
+
+__device__ __forceinline__ int32_t ab_graph_term(const AbGraphArgs &a, uint64_t kv, int s, int t, int64_t j) {
+  const int u = a.adj[j];
+  const uint64_t ru = a.cand[u];
+  const int bu = ru ? (cand_key(ru, u) < kv ? cand_t(ru) : cand_s(ru)) : a.part[u];
+  const int32_t w = a.unit ? 1 : a.ewgt[a.inc[j]];
+  return w * ((int)(bu != s) - (int)(bu != t));
+}
+
+__global__ void __launch_bounds__(256) k_ab_graph(AbGraphArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; base < a.n; base += stride) {
+    const int64_t v = base + lane;
+    const uint64_t rec = v < a.n ? a.cand[v] : 0ull;
+    int64_t j0 = 0, j1 = 0;
+    if (rec) {
+      j0 = a.vptr[v];
+      j1 = a.vptr[v + 1];
+    }
+    const bool heavy = rec && j1 - j0 > 64;
+    if (rec && !heavy) {
+      const uint64_t kv = cand_key(rec, (int32_t)v);
+      const int s = cand_s(rec), t = cand_t(rec);
+      int32_t acc = 0;
+      int64_t j = j0;
+      for (; j + 4 <= j1; j += 4) {
+        int32_t x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = ab_graph_term(a, kv, s, t, j + q);
+        acc += x[0] + x[1] + x[2] + x[3];
+      }
+      for (; j < j1; ++j) acc += ab_graph_term(a, kv, s, t, j);
+      a.rg[v] = acc;
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, heavy);
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const int64_t hv = base + src;
+      const uint64_t hrec = __shfl_sync(0xffffffffu, rec, src);
+      const int64_t h0 = __shfl_sync(0xffffffffu, j0, src), h1 = __shfl_sync(0xffffffffu, j1, src);
+      const uint64_t kv = cand_key(hrec, (int32_t)hv);
+      const int s = cand_s(hrec), t = cand_t(hrec);
+      int32_t acc = 0;
+      for (int64_t j = h0 + lane; j < h1; j += 32) acc += ab_graph_term(a, kv, s, t, j);
+      acc = __reduce_add_sync(0xffffffffu, acc);
+      if (lane == 0) a.rg[hv] = acc;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi) {
   (void)phi;  // phi_e[b] = |D_b| is tested through the non-candidate pins' blocks
+  if (c->graph_path) {
+    if (c->n == 0) return cudaSuccess;
+    AbGraphArgs g{c->vptr, c->adj, c->inc, c->ewgt, part, c->cand, c->rg, c->n, c->unit_ewgt};
+    k_ab_graph<<<grid_for(c->n, 256, c->launch_sms, 8), 256, 0, c->stream>>>(g);
+    ++c->kernel_launches;
+    return cudaGetLastError();
+  }
   AbArgs a{};
   a.eptr = c->eptr;
   a.pins = c->pins;

@@ -270,13 +270,14 @@ __global__ void __launch_bounds__(256) k_objective_masks(const uint32_t *mask, c
   if (threadIdx.x == 0 && tot) add_i64(&cnt->objective, tot);
 }
 
-// (lambda-1) of a graph (every edge two pins): the weighted edge cut.
-__global__ void __launch_bounds__(256) k_objective_cut(const int64_t *eptr, const int32_t *pins, const int32_t *part,
-                                                       const int32_t *ewgt, int32_t m, Counters *cnt) {
+// (lambda-1) of a graph (every edge two pins, so edge e's pins are pins[2e], pins[2e+1]): the weighted
+// edge cut.  `pairs` is pins read as 8-byte pairs (NULL when pins is not 8-byte aligned); unit: all omega = 1.
+__global__ void __launch_bounds__(256) k_objective_cut(const int32_t *pins, const int2 *pairs, const int32_t *part,
+                                                       const int32_t *ewgt, int32_t m, int unit, Counters *cnt) {
   long long acc = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = eptr[e];
-    if (part[pins[p]] != part[pins[p + 1]]) acc += ewgt[e];
+    const int2 p = pairs ? pairs[e] : make_int2(pins[2 * e], pins[2 * e + 1]);
+    if (part[p.x] != part[p.y]) acc += unit ? 1 : ewgt[e];
   }
   long long tot = block_sum_ll(acc);
   if (threadIdx.x == 0 && tot) add_i64(&cnt->objective, tot);
@@ -462,9 +463,11 @@ cudaError_t launch_connectivity_dense(jet_ctx *c, const int32_t *phi, int64_t *o
 cudaError_t launch_objective(jet_ctx *c, const int32_t *part) {
   cudaError_t e = cudaMemsetAsync(&c->cnt->objective, 0, sizeof(long long), c->stream);
   if (e != cudaSuccess || c->m == 0) return e;
-  if (c->graph_path)
-    k_objective_cut<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->eptr, c->pins, part, c->ewgt, c->m,
-                                                                             c->cnt);
+  if (c->graph_path) {
+    const int2 *pairs = ((uintptr_t)c->pins & 7) ? nullptr : reinterpret_cast<const int2 *>(c->pins);
+    k_objective_cut<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->pins, pairs, part, c->ewgt, c->m,
+                                                                             c->unit_ewgt, c->cnt);
+  }
   else
     k_objective_masks<<<grid_for(c->m, 256, c->launch_sms), 256, 0, c->stream>>>(c->mask, c->ewgt, c->m, c->kwp,
                                                                                c->cnt);
