@@ -533,6 +533,8 @@ def run_graph(args, dev):
     parts = {}
     for name, graph_path in (("hypergraph_path", False), ("graph_path", True)):
         ctx = jet.jet_ctx_create(dh, jet.params(k), stream)
+        if args.eager:
+            jet.jet_set_graph_mode(ctx, False)
         if graph_path:
             jet.jet_set_graph_path(ctx, True)
         st = jet.JetState(ctx, part0, with_phi=not graph_path)
@@ -684,6 +686,8 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-multilevel", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--graph-only", action="store_true",
+                    help="time only the graph workload on both paths (with --eager: kernel by kernel) and print its line")
     ap.add_argument("--coarsen-only", action="store_true",
                     help="time only the GPU coarsening of the workload (Section 6) and print its JSON line")
     ap.add_argument("--eager", action="store_true",
@@ -697,6 +701,8 @@ def main():
         return run_reference(args, rank, world)
     if args.coarsen_only:
         return run_coarsen_only(args, rank)
+    if args.graph_only:
+        return run_graph_only(args, rank)
 
     if world > 1:
         import torch
@@ -817,6 +823,18 @@ def run_coarsen_only(args, rank):
     print(json.dumps({"metric": "coarsening pins/s (all levels)", "value": c["pins_per_s"], "unit": "pins/s",
                       "config": {"workload": desc, "n": hg.n, "m": hg.m, "pins": hg.P, "k": k},
                       "coarsening": c}), flush=True)
+
+
+def run_graph_only(args, rank):
+    """The graph workload alone on both paths (for profiling)."""
+    import torch
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    g = run_graph(args, dev)
+    print(json.dumps({"metric": "Jet-round pins/s on a graph (graph path)", "value": g["graph_path"]["pins_per_s"],
+                      "unit": "pins/s", "graph": g}), flush=True)
 
 
 def run_reference(args, rank, world):
