@@ -435,7 +435,7 @@ def run_batched(args, dev):
                       "k from {2, 8, 32}, unit weights, eps = 3/100, hash partitions"}
 
 
-def run_multilevel(args, hg, k, dev, coarsen_only=False):
+def run_multilevel(args, hg, k, dev, coarsen_only=False, graph_path=False):
     """The multilevel pass of the paper (Sections 6 and 7.2) on the workload: deterministic coarsening on the
     GPU (jet_cluster + jet_contract per level; c_max = ceil(c(V) / (160 k)), until at most 160 k vertices
     remain or a level shrinks by less than 1%), a balanced hash partition of the coarsest level standing in
@@ -489,8 +489,12 @@ def run_multilevel(args, hg, k, dev, coarsen_only=False):
         return {"coarsening": coarsening}
     hs, mps = levels[::-1], maps[::-1]
     ctxs = [jet.jet_ctx_create(h, jet.params(k), stream) for h in hs]
+    if graph_path:  # every level of a graph's hierarchy is a graph (contraction drops one-pin edges)
+        for c in ctxs:
+            jet.jet_set_graph_path(c, True)
     p0 = synth.part_perm(args.seed, hs[0].n, k)
-    states = [jet.JetState(ctxs[0], p0)] + [jet.JetState(c, np.zeros(h.n, np.int32)) for c, h in zip(ctxs[1:], hs[1:])]
+    states = [jet.JetState(ctxs[0], p0, with_phi=not graph_path)] + [
+        jet.JetState(c, np.zeros(h.n, np.int32), with_phi=not graph_path) for c, h in zip(ctxs[1:], hs[1:])]
     init = states[0].part.clone()
     times = []
     for it in range(1 + max(args.batch_steps, 1)):
@@ -569,6 +573,20 @@ def run_graph(args, dev):
         del st
     out["speedup"] = out["hypergraph_path"]["ms_per_step"] / out["graph_path"]["ms_per_step"]
     out["results_identical"] = bool(np.array_equal(parts["hypergraph_path"], parts["graph_path"]))
+    if not args.no_multilevel:  # the multilevel pass on the graph, graph path at every level
+        ml = run_multilevel(args, hg, k, dev, graph_path=True)
+        flat_ctx = jet.jet_ctx_create(dh, jet.params(k), stream)
+        jet.jet_set_graph_path(flat_ctx, True)
+        st = jet.JetState(flat_ctx, part0, with_phi=False)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        flat = jet.jet_refine(flat_ctx, SCHEDULE, LIMIT, st.part, None, st.block_w)
+        flat_s = time.perf_counter() - t1
+        flat_ctx.close()
+        ml["flat_refinement"] = {"objective": flat["objective"], "iterations": flat["iterations"],
+                                 "seconds": flat_s, "what": "Algorithm 1 on the finest level from the hash "
+                                                            "partition (graph path, one graph launch)"}
+        out["multilevel"] = ml
     out["config"] = {"n": hg.n, "m": hg.m, "pins": hg.P, "k": k, "steps": args.steps, "tau": "3/4",
                      "generated_s": round(gen_s, 1),
                      "workload": "graph: u uniform, v = u + U[1, 1000] (80 %) or uniform (20 %), unit weights"}
