@@ -7,3 +7,4 @@ _spec = importlib.util.spec_from_file_location(
 _mod = importlib.util.module_from_spec(_spec)
 _spec.loader.exec_module(_mod)
 trajectory = _mod.trajectory
+coarsening = _mod.coarsening
