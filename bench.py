@@ -125,6 +125,24 @@ def kernel_bytes(hg, k, deg, st_before, round_stats):
     return b
 
 
+def graph_cand_bytes(hg, deg, st_before):
+    """Compulsory bytes of the graph path's candidate kernels for one round: the bitmask rows are replaced
+    by the neighbour ids (4 B per incidence) and their blocks (a gather from the 4n-byte partition)."""
+    n, m = hg.n, hg.m
+    Pu = int(deg[~st_before].sum())
+    b = 8 * (n + 1) + 4 * n + n + n + 8 * n                  # vptr, partition, heavy flags, locks, records
+    b += 4 * Pu + min(4 * Pu, 4 * n)                         # neighbour ids, their blocks
+    if not ctx_unit_weights(hg):
+        b += 4 * Pu + min(4 * Pu, 4 * m)                     # incidences and omega(e) gathers
+    return b
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(path)) if os.path.exists(path) else {}
+    return float(peaks.get("hbm_gbs", 6800.0)), "measured" if "hbm_gbs" in peaks else "fallback"
+
+
 def ctx_unit_weights(hg):
     return bool(hg.m == 0 or int(hg.ewgt.max()) <= 1)
 
@@ -468,8 +486,10 @@ def run_multilevel(args, hg, k, dev, coarsen_only=False, graph_path=False):
             torch.cuda.synchronize(dev)
             sz = (cur.eptr[1:] - cur.eptr[:-1]).double()
             rated = sz[(sz >= 2) & (sz <= jet.RATING_MAX_EDGE)]
+            visits = int((rated * rated).sum().item())
             rows.append({"n": cur.n, "m": cur.m, "pins": cur.P, "cluster_ms": t_cl, "contract_ms": ev0.elapsed_time(ev1),
-                         "rating_pin_visits_bound": int((rated * rated).sum().item())})
+                         "rating_pin_visits_bound": visits,
+                         "rating_gbs": 8 * visits / (t_cl / 1e3) / 1e9 if t_cl > 0 else None})
             if coarse.n > 0.99 * cur.n:
                 break
             levels.append(coarse)
@@ -533,6 +553,7 @@ def run_graph(args, dev):
     gen_s = time.time() - t0
     stream = torch.cuda.current_stream(dev)
     dh = jet.DeviceHypergraph(hg, dev)
+    deg = np.diff(hg.vptr)
     out = {}
     parts = {}
     for name, graph_path in (("hypergraph_path", False), ("graph_path", True)):
@@ -560,13 +581,26 @@ def run_graph(args, dev):
         jet.jet_set_graph_mode(ctx, False)
         jet.jet_profile_read(ctx, reset=True)
         jet.jet_profile_enable(ctx, True)
+        cand_bytes = 0
         for _ in range(args.steps):
+            locked_before = st.locked.cpu().numpy()[: hg.n].astype(bool)
+            if graph_path:
+                cand_bytes += graph_cand_bytes(hg, deg, locked_before)
+            else:
+                cand_bytes += kernel_bytes(hg, k, deg, locked_before, None)
             st.round(TAU)
         prof = jet.jet_profile_read(ctx, reset=True)
         jet.jet_profile_enable(ctx, False)
         assert st.stats_dict() == stats, "replay diverged from the timed run"
+        peak, peak_src = hbm_peak()
+        cms = prof["candidates"]["ms"]
+        cand_gbs = cand_bytes / (cms / 1e3) / 1e9 if cms > 0 else None
         out[name] = {"ms_per_step": ms, "pins_per_s": hg.P / (ms / 1e3), "objective": stats["objective"],
                      "phi_bytes": 0 if graph_path else hg.m * k * 4,
+                     "candidates_roofline": {"bound": "hbm", "achieved": cand_gbs, "peak": peak, "unit": "GB/s",
+                                             "frac": cand_gbs / peak if cand_gbs else None,
+                                             "bytes_per_step": cand_bytes / args.steps, "peak_source": peak_src,
+                                             "timing": "kernel-by-kernel replay, CUDA events around the launches"},
                      "family_ms_per_step_replay": {f: round(v["ms"] / args.steps, 4) for f, v in prof.items()
                                                    if v["ms"] > 0}}
         ctx.close()
