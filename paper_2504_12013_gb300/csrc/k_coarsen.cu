@@ -457,22 +457,29 @@ __device__ __forceinline__ bool set_insert(int32_t *set, int32_t scap, int32_t C
 // over the warps and the sums are atomic (integer, order-free); a cluster counts once per edge through
 // match_any within a chunk and, for edges of 33 to kSetEdge pins, the warp's set of the edge's
 // clusters.  Larger edges follow, by warp 0 alone, counted once per edge and cluster through the
-// entry's last edge.  s_set: kHeavyWarps x kSetCap words; s_bk/s_bv: per-warp reduction scratch.
+// entry's last edge.  s_set: kHeavyWarps x kSetCap words; s_bk/s_bv: per-warp reduction scratch;
+// s_next: the shared edge counter.
 // Chunks of an edge are taken four at a time, so that their loads overlap.
 __device__ int32_t rate_block(const jet_hypergraph &g, int32_t u, const int32_t *label, const long long *cw,
                               long long cmax, int32_t rmax, Tab *tab, int32_t cap, int32_t *s_set,
-                              int32_t *s_bk, unsigned long long *s_bv) {
+                              int32_t *s_bk, unsigned long long *s_bv, int *s_next) {
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
   for (int i = t; i < cap; i += blockDim.x) {
     tab[i].key = -1;
     tab[i].last = -1;
     tab[i].val = 0;
   }
+  if (t == 0) *s_next = 0;
   __syncthreads();
   int32_t *set = s_set + wid * kSetCap;
   const int64_t i0 = g.vptr[u], i1 = g.vptr[u + 1];
   bool big = false;
-  for (int64_t i = i0 + wid; i < i1; i += nw) {
+  // edges are taken one at a time from a shared counter, so that warps that drew small edges take more
+  for (;;) {
+    int64_t i = 0;
+    if (lane == 0) i = i0 + atomicAdd(s_next, 1);
+    i = __shfl_sync(kFull, i, 0);
+    if (i >= i1) break;
     const int32_t e = g.inc[i];
     const int64_t p0 = g.eptr[e], p1 = g.eptr[e + 1], size = p1 - p0;
     if (size < 2 || size > rmax) continue;
@@ -590,6 +597,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_serial(jet_hypergraph g
   extern __shared__ unsigned long long s_dyn[];
   __shared__ int32_t s_bk[kHeavyWarps];
   __shared__ unsigned long long s_bv[kHeavyWarps];
+  __shared__ int s_next;
   Tab *s_tab = reinterpret_cast<Tab *>(s_dyn);
   int32_t *s_set = reinterpret_cast<int32_t *>(s_tab + kBlockTab);
   for (int32_t x = x0; x < x1; ++x) {
@@ -597,7 +605,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_serial(jet_hypergraph g
     if (cl.csize[u] != 1 || cl.label[u] != u) continue;
     const int32_t cap = cl.cap[u];
     const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, cap <= kBlockTab ? s_tab : pool, cap, s_set,
-                                 s_bk, s_bv);
+                                 s_bk, s_bv, &s_next);
     if (j >= 0 && threadIdx.x == 0) {
       const long long c = g.vwgt[u];
       cl.label[u] = j;
@@ -643,6 +651,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_rate_heavy(jet_hypergra
   __shared__ int32_t s_bk[kHeavyWarps];
   __shared__ unsigned long long s_bv[kHeavyWarps];
   __shared__ unsigned long long s_off;
+  __shared__ int s_next;
   const int32_t u = order[hpos[blockIdx.x]];
   if (cl.csize[u] != 1 || cl.label[u] != u) return;
   const int32_t cap = cl.cap[u];
@@ -653,7 +662,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_rate_heavy(jet_hypergra
     __syncthreads();
     tab = pool + s_off;
   }
-  const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, tab, cap, s_set, s_bk, s_bv);
+  const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, tab, cap, s_set, s_bk, s_bv, &s_next);
   if (threadIdx.x == 0 && j >= 0) {
     cl.T[u] = j;
     atomicAdd(reinterpret_cast<unsigned long long *>(&cl.pw[j]), (unsigned long long)g.vwgt[u]);
