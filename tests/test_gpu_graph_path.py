@@ -108,3 +108,32 @@ def test_graph_path_errors():
     want = orc.refine_round(oracle.Params(k), (3, 4), ost.part, ost.phi, ost.bw, ost.locked)
     st.round((3, 4))
     assert st.stats_dict() == want
+
+
+def test_uncoarsening_of_a_graph_hierarchy_on_the_graph_path():
+    """The oracle coarsens a graph twice (every coarse level is a graph again); jet_uncoarsen refines
+    the hierarchy with graph-path contexts and no phi tables, and every level must equal the oracle's
+    projection and refinement."""
+    g = synth.graph(75, 6_000, 20_000, local=0.7, window=40)
+    k = 16
+    hs, maps = [g], []
+    for level in range(2):
+        coarse, mp, _ = oracle.Oracle(hs[0]).coarsen(40, synth.vertex_order(level, hs[0].n))
+        assert np.all(np.diff(coarse.eptr) == 2)
+        hs.insert(0, coarse)
+        maps.insert(0, mp)
+    part0 = synth.part_perm(3, hs[0].n, k)
+    want, p = [], part0.copy()
+    for l, h in enumerate(hs):
+        if l:
+            p = p[maps[l - 1]].astype(np.int32)
+        iters, obj, _ = oracle.Oracle(h).refine(oracle.Params(k), p)
+        want.append((iters, obj, p.copy()))
+    ctxs = [_ctx(h, k) for h in hs]
+    states = [jet.JetState(ctxs[0], part0, with_phi=False)] + [
+        jet.JetState(c, np.zeros(h.n, np.int32), with_phi=False) for c, h in zip(ctxs[1:], hs[1:])]
+    res = jet.jet_uncoarsen(ctxs, [torch.as_tensor(m).cuda() for m in maps], oracle.TAU_SCHEDULE,
+                            oracle.ITERATION_LIMIT, states)
+    for l, (h, r, st, (iters, obj, p)) in enumerate(zip(hs, res, states, want)):
+        assert (r["iterations"], r["objective"]) == (iters, obj), f"level {l}"
+        assert np.array_equal(st.part.cpu().numpy()[: h.n], p), f"level {l}: partition"
