@@ -426,7 +426,10 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
       int levels = (tb + kRbMaxDigit - 1) / kRbMaxDigit;
       int digit = (tb + levels - 1) / levels;
       const long long cap = std::max(4ll * c->n, 2048ll * c->k);
-      while (digit > 11 && ((long long)c->k << digit) > cap) digit = (tb + ++levels - 1) / levels;
+      while (digit > 11 && ((long long)c->k << digit) > cap) {
+        ++levels;
+        digit = (tb + levels - 1) / levels;
+      }
       c->rb_digit = digit;
     }
     // class lists, workspace
@@ -751,7 +754,7 @@ int jet_refine_host(const jet_hypergraph *hh, const jet_params *p, const int32_t
   void **bufs[] = {(void **)&eptr, (void **)&vptr, (void **)&bw, (void **)&pins, (void **)&inc,
                    (void **)&vw, (void **)&ew, (void **)&pt, (void **)&phi};
   size_t sizes[] = {8 * (m + 1), 8 * (n + 1), 8 * k, 4 * (P ? P : 1), 4 * (P ? P : 1),
-                    4 * (n ? n : 1), 4 * (m ? m : 1), 4 * (n ? n : 1), 4 * (m * k ? m * k : 1)};
+                    4 * (n ? n : 1), 4 * (m ? m : 1), 4 * (n ? n : 1), 4 * (m * k > 0 ? m * k : 1)};
   int rc = JET_OK;
   for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaMallocAsync(bufs[i], sizes[i], s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(eptr, hh->eptr, 8 * (m + 1), cudaMemcpyHostToDevice, s);
