@@ -43,6 +43,7 @@ constexpr int kSmemTab = 128;      // hash-table entries per warp held in shared
 constexpr int kWarpTab = 2048;     // larger tables: the whole block rates the vertex (heavy vertices)
 constexpr int kBlockTab = 4096;    // a heavy vertex's table in shared memory up to this size
 constexpr int kHeavyWarps = 16;    // warps of a block that rates one heavy vertex
+constexpr int kFirstEdge = 64;     // a heavy vertex's edges above this size are rated first
 constexpr int kSetCap = 2048;      // per-warp set of the distinct clusters of one edge (heavy vertices)
 constexpr int kSetEdge = kSetCap / 2;  // edges up to this size are deduplicated in that set
 constexpr size_t kHeavySmem = sizeof(int32_t) * kHeavyWarps * kSetCap + 16 * kBlockTab;
@@ -458,7 +459,7 @@ __device__ __forceinline__ bool set_insert(int32_t *set, int32_t scap, int32_t C
 // match_any within a chunk and, for edges of 33 to kSetEdge pins, the warp's set of the edge's
 // clusters.  Larger edges follow, by warp 0 alone, counted once per edge and cluster through the
 // entry's last edge.  s_set: kHeavyWarps x kSetCap words; s_bk/s_bv: per-warp reduction scratch;
-// s_next: the shared edge counter.
+// s_next: the shared edge counters of the two passes.
 // Chunks of an edge are taken four at a time, so that their loads overlap.
 __device__ int32_t rate_block(const jet_hypergraph &g, int32_t u, const int32_t *label, const long long *cw,
                               long long cmax, int32_t rmax, Tab *tab, int32_t cap, int32_t *s_set,
@@ -469,20 +470,22 @@ __device__ int32_t rate_block(const jet_hypergraph &g, int32_t u, const int32_t 
     tab[i].last = -1;
     tab[i].val = 0;
   }
-  if (t == 0) *s_next = 0;
+  if (t < 2) s_next[t] = 0;
   __syncthreads();
   int32_t *set = s_set + wid * kSetCap;
   const int64_t i0 = g.vptr[u], i1 = g.vptr[u + 1];
   bool big = false;
-  // edges are taken one at a time from a shared counter, so that warps that drew small edges take more
+  // edges are taken one at a time from a shared counter, so that warps that drew small edges take more;
+  // edges of more than kFirstEdge pins in a first pass, the rest in a second (largest work first)
+  for (int pass = 0; pass < 2; ++pass)
   for (;;) {
     int64_t i = 0;
-    if (lane == 0) i = i0 + atomicAdd(s_next, 1);
+    if (lane == 0) i = i0 + atomicAdd(&s_next[pass], 1);
     i = __shfl_sync(kFull, i, 0);
     if (i >= i1) break;
     const int32_t e = g.inc[i];
     const int64_t p0 = g.eptr[e], p1 = g.eptr[e + 1], size = p1 - p0;
-    if (size < 2 || size > rmax) continue;
+    if (size < 2 || size > rmax || (size > kFirstEdge) != (pass == 0)) continue;
     if (size > kSetEdge) {
       big = true;
       continue;
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_serial(jet_hypergraph g
   extern __shared__ unsigned long long s_dyn[];
   __shared__ int32_t s_bk[kHeavyWarps];
   __shared__ unsigned long long s_bv[kHeavyWarps];
-  __shared__ int s_next;
+  __shared__ int s_next[2];
   Tab *s_tab = reinterpret_cast<Tab *>(s_dyn);
   int32_t *s_set = reinterpret_cast<int32_t *>(s_tab + kBlockTab);
   for (int32_t x = x0; x < x1; ++x) {
@@ -605,7 +608,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_serial(jet_hypergraph g
     if (cl.csize[u] != 1 || cl.label[u] != u) continue;
     const int32_t cap = cl.cap[u];
     const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, cap <= kBlockTab ? s_tab : pool, cap, s_set,
-                                 s_bk, s_bv, &s_next);
+                                 s_bk, s_bv, s_next);
     if (j >= 0 && threadIdx.x == 0) {
       const long long c = g.vwgt[u];
       cl.label[u] = j;
@@ -651,7 +654,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_rate_heavy(jet_hypergra
   __shared__ int32_t s_bk[kHeavyWarps];
   __shared__ unsigned long long s_bv[kHeavyWarps];
   __shared__ unsigned long long s_off;
-  __shared__ int s_next;
+  __shared__ int s_next[2];
   const int32_t u = order[hpos[blockIdx.x]];
   if (cl.csize[u] != 1 || cl.label[u] != u) return;
   const int32_t cap = cl.cap[u];
@@ -662,7 +665,7 @@ __global__ void __launch_bounds__(kHeavyWarps * 32) k_cl_rate_heavy(jet_hypergra
     __syncthreads();
     tab = pool + s_off;
   }
-  const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, tab, cap, s_set, s_bk, s_bv, &s_next);
+  const int32_t j = rate_block(g, u, cl.label, cl.cw, cmax, rmax, tab, cap, s_set, s_bk, s_bv, s_next);
   if (threadIdx.x == 0 && j >= 0) {
     cl.T[u] = j;
     atomicAdd(reinterpret_cast<unsigned long long *>(&cl.pw[j]), (unsigned long long)g.vwgt[u]);
