@@ -19,7 +19,10 @@
 //   k_cl_rate     hash table of the neighbour clusters per vertex, a warp
 //                 per vertex (table in shared memory, else a slice of a
 //                 global pool sized per sub-round)
-//   k_cl_rate_heavy  the whole block per vertex with a very large table
+//   k_cl_rate_heavy  a 16-warp block per vertex whose table exceeds 2048
+//                 entries: the warps take its edges from a shared counter
+//                 (edges above 64 pins first), each edge's clusters
+//                 deduplicated in a per-warp set, the sums integer atomics
 //   k_cl_swap     swap prevention, group lists of the proposals
 //   k_cl_approve  weight-ordered prefix per target (fast path: all fit)
 //   k_cl_apply    moves, resets the per-sub-round state
