@@ -236,3 +236,27 @@ def test_projection_keeps_objective_over_levels():
         assert c.n < hg.n
         hg = c
         order = synth.stream_u64(9, hg.n).argsort(kind="stable").astype(np.int32)
+
+
+def test_graph_afterburner_is_a_neighbour_sum():
+    """On graphs (two-pin edges), Algorithm 2's recomputed gain of a candidate v equals the sum over
+    its neighbours u of omega(e) * ([b'(u) != s] - [b'(u) != t]), where b'(u) is u's target if u is a
+    candidate ordered before v (gain desc, id asc), else Pi(u): the graph path's afterburner (R27)."""
+    for seed in range(6):
+        g = synth.graph(seed, 300, 1200, local=0.6, window=12, w_max=4)
+        k = (2, 4, 8)[seed % 3]
+        part = synth.part_random(seed + 40, g.n, k)
+        o = make(g)
+        phi, _ = o.pincounts(k, part)
+        for tau in ((3, 4), (0, 1)):
+            _, target, gain, in_m = o.candidates(k, part, phi, np.zeros(g.n, np.uint8), tau)
+            _, rg, _ = o.afterburner(k, part, phi, target, gain, in_m)
+            for v in np.flatnonzero(in_m):
+                s, t, acc = part[v], target[v], 0
+                for e in g.inc[g.vptr[v]:g.vptr[v + 1]]:
+                    a, b = g.pins[g.eptr[e]:g.eptr[e + 1]]
+                    u = b if a == v else a
+                    before = in_m[u] and (gain[u] > gain[v] or (gain[u] == gain[v] and u < v))
+                    bu = target[u] if before else part[u]
+                    acc += int(g.ewgt[e]) * (int(bu != s) - int(bu != t))
+                assert acc == rg[v], (seed, tau, int(v))
