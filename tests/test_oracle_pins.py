@@ -6,6 +6,8 @@ sequential replay that Algorithm 2 is defined to approximate exactly per edge,
 closed forms of the connectivity metric, exact-rational rebalancing selection,
 and a hand-worked example.
 """
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -260,3 +262,35 @@ def test_graph_afterburner_is_a_neighbour_sum():
                     bu = target[u] if before else part[u]
                     acc += int(g.ewgt[e]) * (int(bu != s) - int(bu != t))
                 assert acc == rg[v], (seed, tau, int(v))
+
+
+def test_graph_candidates_from_neighbour_blocks():
+    """On graphs, conn(v, b) = sum of omega over neighbours in b and A(v) = conn(v, Pi(v)), so the best
+    target (ties to the smaller block), its gain and the temperature filter follow from the neighbours'
+    blocks alone (R27); they must equal the oracle's phi-based candidates."""
+    for seed in range(6):
+        g = synth.graph(seed + 20, 250, 1000, local=0.5, window=9, w_max=5)
+        k = (3, 8, 16)[seed % 3]
+        part = synth.part_random(seed + 60, g.n, k)
+        o = make(g)
+        phi, _ = o.pincounts(k, part)
+        for tau in ((3, 4), (3, 8), (0, 1)):
+            _, target, gain, in_m = o.candidates(k, part, phi, np.zeros(g.n, np.uint8), tau)
+            for v in range(g.n):
+                s = part[v]
+                conn = {}
+                for e in g.inc[g.vptr[v]:g.vptr[v + 1]]:
+                    a, b = g.pins[g.eptr[e]:g.eptr[e + 1]]
+                    u = b if a == v else a
+                    conn[part[u]] = conn.get(part[u], 0) + int(g.ewgt[e])
+                A = conn.get(s, 0)
+                adj = [b for b in conn if b != s]
+                if not adj:
+                    assert not in_m[v]
+                    continue
+                t = min(adj, key=lambda b: (-conn[b], b))
+                gv = conn[t] - A
+                keep = Fraction(gv) >= -Fraction(tau[0], tau[1]) * A
+                assert bool(in_m[v]) == keep, (seed, tau, v)
+                if keep:
+                    assert (target[v], gain[v]) == (t, gv), (seed, tau, v)
