@@ -45,3 +45,24 @@ def test_binding_loads_and_reports_errors_without_gpu():
 
 def test_sources_target_sm_103a_only():
     assert cuda_build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_coarsening_graph_path_and_uncoarsening_argument_errors_without_gpu():
+    """The newer entry points reject bad arguments on the host, before any CUDA call."""
+    lib = jet.load_library()
+    hg = jet.JetHypergraph(4, 2, 4, 1, 1, 1, 1, 1, 1)  # sizes only; no pointer is dereferenced here
+    assert lib.jet_cluster(None, None, None, None, None) == -1
+    assert lib.jet_cluster(ctypes.byref(hg), None, None, None, None) == -1
+    for bad in (jet.JetCoarsenParams(0, 1000, 100, 100), jet.JetCoarsenParams(10, 1, 100, 100),
+                jet.JetCoarsenParams(10, 1000, -1, 100), jet.JetCoarsenParams(10, 1000, 100, 0)):
+        assert lib.jet_cluster(ctypes.byref(hg), ctypes.byref(bad), 1, 1, None) == -1
+    neg = jet.JetHypergraph(-1, 2, 4, 1, 1, 1, 1, 1, 1)
+    ok = jet.JetCoarsenParams(10, 1000, 100, 100)
+    assert lib.jet_cluster(ctypes.byref(neg), ctypes.byref(ok), 1, 1, None) == -1
+    n, m, P = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    assert lib.jet_contract(None, None, None, None, ctypes.byref(n), ctypes.byref(m), ctypes.byref(P), None) == -1
+    assert lib.jet_contract(ctypes.byref(hg), 1, 1, None, ctypes.byref(n), ctypes.byref(m), ctypes.byref(P),
+                            None) == -1  # no output buffers
+    assert lib.jet_set_graph_path(None, 1) == -1
+    assert lib.jet_uncoarsen(None, 0, None, None, 0, 8, None, None, None, None, None) == -1
+    assert lib.jet_quotient_schedule(None, None, None, None, None, None) == -1
