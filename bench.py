@@ -4,10 +4,12 @@
 A step is one Jet iteration (the body of Algorithm 1: candidates,
 afterburner, apply, rebalancing if needed, objective) on the whole
 hypergraph; the metric is pins/s = P * steps / time.  The default workload is
-the VLSI-netlist-shaped hypergraph (n = 2,000,000, m = 2,200,000,
-power-law 2.5 sizes on [2, 5000], 80 % of pins within +-20,000 ids,
-c(v) in 1..4, k = 64, eps = 3/100), started from a seeded balanced
-partition; the timed steps are the first K iterations at temperature 3/4.
+the largest one-GPU configuration, the sparse-matrix row-net hypergraph
+(n = m = 4,000,000, log-normal(2, 1) row lengths plus 200 hub rows of
+50,000-200,000 pins, unit weights, k = 128, eps = 3/100), started from a
+seeded balanced partition; the timed steps are the first K iterations at
+temperature 3/4.  The VLSI-shaped hypergraph (n = 2,000,000, k = 64) is
+measured the same way and reported beside it.
 
 One JSON line on stdout (rank 0).  --impl reference times the CPU oracle
 (single-threaded, test infrastructure) on the same workload instead.
@@ -163,6 +165,35 @@ def rebalance_target_bytes(hg, k, stats, work, unit):
     return b
 
 
+def afterburner_bytes(hg, unit):
+    """Algorithmic bytes of the afterburner over one iteration: the edge offsets and pins streamed once; the
+    candidate records (8 B per vertex) and the partition (4 B per vertex) gathered per pin, each table counted
+    once (min(gathers, table)); omega(e) per edge unless unit; the recomputed gains written (4 B per vertex)."""
+    n, m, P = hg.n, hg.m, hg.P
+    return 8 * (m + 1) + 4 * P + min(8 * P, 8 * n) + min(4 * P, 4 * n) + (0 if unit else 4 * m) + 4 * n
+
+
+def approve_bytes(hg, stats):
+    """Approval and locks over one iteration: per vertex its record (8 B), recomputed gain (4 B read, 4 B
+    cleared) and lock (1 B); per approved move its move-list entry (8 B)."""
+    return 17 * hg.n + 8 * stats["approved"]
+
+
+def selection_bytes(work):
+    """Rebalancing selection over one iteration: every record (16 B: key, vertex, weight and blocks) is read
+    once per radix level after the first (the first level's histogram is built by the target kernels).  The
+    per-block histogram rows the pick kernels scan are not counted."""
+    return 16 * max(work["select_levels"] - 1, 0) * work["rebalance_evaluated"]
+
+
+def objective_bytes(hg, k, unit):
+    """(lambda-1) from the compact bitmasks: one Lambda(e) row (ceil(k/32) words, rounded to 1/2/4/8) per edge,
+    plus omega(e) unless unit."""
+    kw = (k + 31) // 32
+    kwp = 1 if kw <= 1 else 2 if kw <= 2 else 4 if kw <= 4 else 8
+    return 4 * hg.m * kwp + (0 if unit else 4 * hg.m)
+
+
 def apply_move_bytes(stats, work):
     """Algorithmic bytes of the apply kernels over one iteration: per Jet move its list entry (vertex,
     source/target), the partition write, c(v) and the offsets; per rebalancing record (the rebalancing
@@ -267,19 +298,29 @@ def run_gpu(args, rank, world):
         prof_eager_timed = prof_timed
     jet.jet_profile_read(ctx, reset=True)
     deg = np.diff(hg.vptr)
+    unit = ctx_unit_weights(hg)
     model_bytes = 0
     rb_bytes = 0
     apply_bytes = 0
+    fam_bytes = {"candidates": 0, "afterburner": 0, "approve": 0, "apply": 0, "rebalance_targets": 0,
+                 "rebalance_select": 0, "objective": 0}
     trace = []
     for _ in range(args.steps):
         locked_before = st.locked.cpu().numpy()[: hg.n].astype(bool)
         st.round(TAU)
         s = st.stats_dict()
         trace.append(s)
-        model_bytes += kernel_bytes(hg, k, deg, locked_before, s)
+        cb = kernel_bytes(hg, k, deg, locked_before, s)
+        model_bytes += cb
         work = jet.jet_profile_work(ctx)
-        rb_bytes += rebalance_target_bytes(hg, k, s, work, ctx_unit_weights(hg))
-        apply_bytes += apply_move_bytes(s, work)
+        rb = rebalance_target_bytes(hg, k, s, work, unit)
+        ap = apply_move_bytes(s, work)
+        rb_bytes += rb
+        apply_bytes += ap
+        for f, b in (("candidates", cb), ("afterburner", afterburner_bytes(hg, unit)), ("approve", approve_bytes(hg, s)),
+                     ("apply", ap), ("rebalance_targets", rb), ("rebalance_select", selection_bytes(work)),
+                     ("objective", objective_bytes(hg, k, unit))):
+            fam_bytes[f] += b
     prof = jet.jet_profile_read(ctx, reset=True)
     if args.eager:
         prof = prof_eager_timed
@@ -288,7 +329,7 @@ def run_gpu(args, rank, world):
     sched = schedule_timing(jet, ctx, st, stream, dev)
 
     result = {"ms": ms, "prof": prof, "prof_timed": prof_timed, "model_bytes": model_bytes, "rb_bytes": rb_bytes,
-              "apply_bytes": apply_bytes,
+              "apply_bytes": apply_bytes, "fam_bytes": fam_bytes, "workload": args.workload,
               "trace": trace, "schedule": sched,
               "clocks": clk.summary(), "hg": hg, "k": k, "part0": part0, "desc": desc, "dev": dev}
     ctx.close()
@@ -318,36 +359,62 @@ def schedule_timing(jet, ctx, st, stream, dev):
                     "(jet_quotient_schedule, Section 5): device time of the kernels; call_ms with the host copies"}
 
 
-def run_e2e(args, hg, k, part0, dev):
-    """jet_refine_host on pinned host buffers: H2D of the hypergraph and partition, the whole temperature
-    schedule, D2H of the refined partition, per call."""
+def pinned_hypergraph(hg):
+    """The hypergraph's arrays copied into pinned host memory (the fastest host->device copies)."""
     import torch
-
-    from paper_2504_12013_gb300 import jet
     pinned = {}
     for name in ("eptr", "pins", "vptr", "inc", "vwgt", "ewgt"):
         a = getattr(hg, name)
         t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True)
         t.numpy()[:] = a
         pinned[name] = t.numpy()
-    hp = synth.Hypergraph(hg.n, hg.m, **pinned)
+    return synth.Hypergraph(hg.n, hg.m, **pinned)
+
+
+def run_e2e(args, hg, k, part0, dev):
+    """End to end through the C ABI on pinned host buffers, the same K iterations as the device-timed value:
+    jet_rounds_host copies the hypergraph and the partition to the device, creates the context (validation,
+    size classes), builds phi, runs K iterations at tau = 3/4 and copies the partition back, per call.  Also
+    the whole temperature schedule through jet_refine_host (e2e_schedule)."""
+    import torch
+
+    from paper_2504_12013_gb300 import jet
+    hp = pinned_hypergraph(hg)
     part_t = torch.empty(hg.n, dtype=torch.int32, pin_memory=True)
     part = part_t.numpy()
     part[:] = part0
-    jet.jet_refine_host(hp, jet.params(k), SCHEDULE, LIMIT, part)  # warm-up (allocator pools, module load)
-    times, iters = [], []
+    jet.jet_rounds_host(hp, jet.params(k), TAU, args.steps, part)  # warm-up (allocator pools, module load)
+    times = []
     for _ in range(args.e2e_steps):
         part[:] = part0
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        res = jet.jet_refine_host(hp, jet.params(k), SCHEDULE, LIMIT, part)
+        st = jet.jet_rounds_host(hp, jet.params(k), TAU, args.steps, part)
         times.append(time.perf_counter() - t0)
-        iters.append(res["iterations"])
     bi = hg.nbytes() + 4 * hg.n
     bo = 4 * hg.n
-    return {"value": hg.P * sum(iters) / sum(times), "unit": "pins/s", "h2d_bytes_per_step": bi,
-            "d2h_bytes_per_step": bo, "iterations_per_call": iters[-1], "seconds_per_call": min(times),
-            "objective": res["objective"]}
+    out = {"value": hg.P * args.steps / (sum(times) / len(times)), "unit": "pins/s", "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": bo, "iterations_per_call": args.steps, "seconds_per_call": sum(times) / len(times),
+           "objective": st["objective"],
+           "what": "jet_rounds_host on pinned host buffers: upload, context set-up, pin counts, the same K iterations "
+                   "at tau 3/4 as value, download of the partition; wall time per call, mean of the calls"}
+    if not args.no_e2e_schedule:
+        part[:] = part0
+        jet.jet_refine_host(hp, jet.params(k), SCHEDULE, LIMIT, part)  # warm-up
+        stimes, iters = [], []
+        for _ in range(args.e2e_steps):
+            part[:] = part0
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            res = jet.jet_refine_host(hp, jet.params(k), SCHEDULE, LIMIT, part)
+            stimes.append(time.perf_counter() - t0)
+            iters.append(res["iterations"])
+        out["e2e_schedule"] = {"value": hg.P * sum(iters) / sum(stimes), "unit": "pins/s",
+                               "iterations_per_call": iters[-1], "seconds_per_call": min(stimes),
+                               "objective": res["objective"],
+                               "what": "jet_refine_host: the whole temperature schedule (Algorithm 1 to convergence, "
+                                       "later iterations are cheap), copies and set-up included"}
+    return out
 
 
 def run_batched(args, dev):
@@ -391,6 +458,41 @@ def run_batched(args, dev):
     ms_batch = ev0.elapsed_time(ev1) / args.batch_steps
     pin_rounds = sum(p * r["iterations"] for p, r in zip(pins, res))
     parts_batch = [st.part[: h.n].cpu().numpy().copy() for st, (h, _, _) in zip(states, insts)]
+
+    # persistent form: one kernel, teams chosen by the autotuner from short trials on a sample
+    restore()
+    t_tune = time.perf_counter()
+    shape, trials = jet.jet_batch_autotune(b, SCHEDULE, LIMIT, states, sample=args.tune_sample,
+                                           trial_iterations=args.tune_iterations)
+    tune_s = time.perf_counter() - t_tune
+    for _ in range(max(args.warmup, 1)):
+        restore()
+        jet.jet_batch_refine(b, SCHEDULE, LIMIT, states)
+    torch.cuda.synchronize(dev)
+    tms = []
+    for _ in range(args.batch_steps):
+        restore()
+        ev0.record(stream)
+        res_team = jet.jet_batch_refine(b, SCHEDULE, LIMIT, states)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        tms.append(ev0.elapsed_time(ev1))
+    ms_team = sum(tms) / len(tms)
+    same_team = all(a["iterations"] == r["iterations"] and a["objective"] == r["objective"]
+                    for a, r in zip(res_team, res))
+    same_team = same_team and all(np.array_equal(st.part[: h.n].cpu().numpy(), pb)
+                                  for st, (h, _, _), pb in zip(states, insts, parts_batch))
+    persistent = {"value": pin_rounds / (ms_team / 1e3), "unit": "pins/s", "ms_per_step": ms_team,
+                  "team": {"blocks": shape[0], "threads": shape[1]},
+                  "autotuner": {"sample_instances": args.tune_sample, "trial_iterations": args.tune_iterations,
+                                "seconds": tune_s,
+                                "trials": [{"blocks": c, "threads": t, "ms": ms, "pin_iterations_per_s": rate}
+                                           for (c, t), (ms, rate) in trials.items()]},
+                  "results_identical_to_branch_graph": bool(same_team),
+                  "how": "jet_batch_refine with jet_batch_set_team: ONE persistent kernel in a CUDA graph; teams "
+                         "(thread-block clusters) take instances from a device queue, largest first, and run all "
+                         "of Algorithm 1 with cluster barriers between phases"}
+    jet.jet_batch_set_team(b, 0)
     b.close()
 
     # plain path: one jet_refine (device-side loop, one graph launch and one synchronization) per instance
@@ -439,13 +541,16 @@ def run_batched(args, dev):
     d2h = sum(4 * h.n for h, _, _ in insts)
     for c in ctxs:
         c.close()
-    return {"metric": "Jet-round pins/s, batched (256 instances to convergence, one graph launch per step)",
+    return {"metric": "Jet-round pins/s, batched (256 instances to convergence, one graph launch per step: the "
+                      "branch graph in value, the persistent kernel in persistent)",
             "value": pin_rounds / (ms_batch / 1e3), "unit": "pins/s", "ms_per_step": ms_batch,
             "steps": args.batch_steps, "instances": len(insts), "pins": sum(pins),
             "jet_iterations": sum(r["iterations"] for r in res),
             "plain": {"value": pin_rounds / (ms_plain / 1e3), "unit": "pins/s", "ms_per_step": ms_plain,
                       "how": "jet_refine on each instance in turn (one graph launch + synchronization each)"},
             "speedup_vs_plain": ms_plain / ms_batch, "results_identical_to_plain": bool(same),
+            "persistent": persistent, "persistent_speedup_vs_plain": ms_plain / ms_team,
+            "persistent_speedup_vs_branch_graph": ms_batch / ms_team,
             "work_split": {"chosen": split, "tuned_ms": tune_ms},
             "e2e": {"value": pin_rounds / e2e_s, "unit": "pins/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -464,7 +569,8 @@ def run_multilevel(args, hg, k, dev, coarsen_only=False, graph_path=False):
     from paper_2504_12013_gb300 import jet
     stream = torch.cuda.current_stream(dev)
     limit = 160 * k
-    cmax = -(-int(hg.vwgt.astype(np.int64).sum()) // limit)
+    # contexts take c(v) <= 32767, and a cluster never exceeds c_max: keep the coarse levels refinable
+    cmax = min(-(-int(hg.vwgt.astype(np.int64).sum()) // limit), 32767)
     orders = {}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -682,16 +788,33 @@ def run_served(args, dev):
         bad = [d for d in done if d["status"] != 0]
         if bad:
             raise RuntimeError(f"served job failed: {bad[0]}")
-        lat = sorted(d["latency_ms"] for d in done)
+        def pct(xs, q):
+            xs = sorted(xs)
+            return xs[min(len(xs) - 1, (q * len(xs)) // 100)]
+
+        lat = [d["latency_ms"] for d in done]
+        serv = [d["service_ms"] for d in done]
         pr = sum(insts[jobs[ids[d["id"]]][1]].P * d["result"]["iterations"] for d in done)
+        spans = sorted((d["device_start_ms"], d["device_end_ms"]) for d in done if d["device_start_ms"] >= 0)
+        conc = 0
+        if spans:  # most jobs in flight on the device at once (from the jobs' GPU-timeline intervals)
+            ev = sorted([(a, 1) for a, _ in spans] + [(b, -1) for _, b in spans], key=lambda x: (x[0], x[1]))
+            cur = 0
+            for _, d_ in ev:
+                cur += d_
+                conc = max(conc, cur)
         out[arm] = {"slots": slots, "jobs": len(done), "seconds": wall, "jobs_per_s": len(done) / wall,
                     "pin_rounds_per_s": pr / wall,
-                    "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, (99 * len(lat)) // 100)],
-                    "queue_ms_mean": sum(d["queue_ms"] for d in done) / len(done)}
+                    "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
+                    "service_ms_p50": pct(serv, 50), "service_ms_p99": pct(serv, 99),
+                    "queue_ms_mean": sum(d["queue_ms"] for d in done) / len(done),
+                    "max_jobs_in_flight_on_device": conc}
         finals[arm] = parts
         torch.cuda.synchronize(dev)
     same = all(np.array_equal(a, b) for a, b in zip(finals["served"], finals["serial"]))
     return {"metric": "served refinement: throughput and p50/p99 latency, continuous batching vs serial queue",
+            "latency": "arrival to refined partition in host memory (queueing included); service: admission to "
+                       "completion",
             "served": out["served"], "serial": out["serial"],
             "p99_speedup": out["serial"]["latency_ms_p99"] / out["served"]["latency_ms_p99"],
             "throughput_speedup": out["served"]["jobs_per_s"] / out["serial"]["jobs_per_s"],
@@ -701,8 +824,30 @@ def run_served(args, dev):
                       f"random partitions, memory budget {args.serve_budget_gb} GB"}
 
 
+def host_cpu():
+    """The host the oracle ran on: its logical CPU count and model name."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
 def cpu_baseline(hg, k, part0, budget_s):
-    """The oracle as it stands (single thread), rounds at tau = 3/4 from the same start until budget_s."""
+    """The oracle as it stands (single thread), iterations at tau = 3/4 from the same start until budget_s (at
+    least one)."""
     import oracle
     orc = oracle.Oracle(hg)
     st = oracle.State(orc, k, part0)
@@ -714,8 +859,74 @@ def cpu_baseline(hg, k, part0, budget_s):
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return {"value": hg.P * rounds / el, "unit": "pins/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {rounds} Jet iteration(s) at tau=3/4 of the same workload, {el:.1f} s"}
+    return dict({"value": hg.P * rounds / el, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                 "sample": f"first {rounds} Jet iteration(s) at tau=3/4 of the same workload, {el:.1f} s"},
+                **host_cpu())
+
+
+def roofline_block(args, r, hbm, peak_src):
+    """The roofline object of one measured workload: the dominant kernel family's (the larger device time per
+    step of the rebalancing-target kernels and the apply kernels, from the kernel-by-kernel replay), the others
+    beside it, and `round`: the algorithmic bytes of every family of the iteration over the timed ms per step."""
+    prof = r["prof"]
+    fam_ms = {f: v["ms"] for f, v in prof.items()}
+    total_fam = sum(fam_ms.values())
+    dom = max(fam_ms, key=fam_ms.get)
+    cand_ms = r["prof_timed"]["candidates"]["ms"]  # measured inside the timed region
+    achieved = r["model_bytes"] / (cand_ms / 1e3) / 1e9 if cand_ms > 0 else None
+    replay_note = ("CUDA events around each launch in the kernel-by-kernel replay of the timed steps (these kernels "
+                   "also run inside conditional graph bodies, which cannot hold event nodes)")
+    workload = r["workload"]
+
+    def family_roofline(fam, kernel, nbytes, traffic_kernel):
+        fms, fl = prof[fam]["ms"], prof[fam]["launches"]
+        ach = nbytes / (fms / 1e3) / 1e9 if fms > 0 else None
+        return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": (ach / hbm) if ach else None,
+                "traffic": ncu_traffic(workload, traffic_kernel) if traffic_kernel else None,
+                "traffic_note": (f"mean DRAM bytes per launch, cold L2 (profiles/{traffic_kernel}.md); null when the "
+                                 "kernel source changed since that capture" if traffic_kernel
+                                 else "no capture for this kernel"),
+                "bytes_per_step": nbytes / args.steps, "ms_per_step": fms / args.steps,
+                "launches_per_step": fl / args.steps, "timing": replay_note, "peak_source": peak_src}
+
+    fam_roof = {"rebalance_targets": family_roofline("rebalance_targets",
+                                                     "rebalancing targets (k_rbcand_light/k_rbcand_heavy)",
+                                                     r["rb_bytes"], "k_rbcand_light"),
+                "apply": family_roofline("apply", "apply moves (k_apply, k_rb_apply, k_apply_edges)",
+                                         r["apply_bytes"], "k_apply")}
+    dom_kernel = max(fam_roof, key=lambda f: prof[f]["ms"])  # the kernel with the most device time per step
+    launches = sum(v["launches"] for v in prof.values())
+    ms_step = r["ms"] / args.steps
+    fb = r["fam_bytes"]
+    b_round = sum(fb.values()) / args.steps
+    fams = {}
+    for f, b in fb.items():
+        fms = prof[f]["ms"] / args.steps
+        ach = (b / args.steps) / (fms / 1e3) / 1e9 if fms > 0 else None
+        fams[f] = {"bytes_per_step": b / args.steps, "ms_per_step_replay": fms,
+                   "achieved": ach, "frac": ach / hbm if ach else None}
+    round_ach = b_round / (ms_step / 1e3) / 1e9
+    roof = dict(fam_roof[dom_kernel], **{
+        "others": {f: v for f, v in fam_roof.items() if f != dom_kernel},
+        "candidates": {"kernel": "k_cand_light/k_cand_heavy", "achieved": achieved,
+                       "frac": (achieved / hbm) if achieved else None,
+                       "traffic": ncu_traffic(workload),
+                       "traffic_note": "DRAM bytes of the first timed launch (profiles/k_cand_light.md)",
+                       "timing": "event-record nodes around the kernels inside the timed graphs",
+                       "ms_per_step": cand_ms / args.steps,
+                       "bytes_per_step": r["model_bytes"] / args.steps},
+        "round": {"bound": "hbm", "achieved": round_ach, "peak": hbm, "unit": "GB/s", "frac": round_ach / hbm,
+                  "bytes_per_step": b_round, "ms_per_step": ms_step, "peak_source": peak_src,
+                  "what": "sum of every family's algorithmic bytes per iteration (candidates, afterburner, approval, "
+                          "apply, rebalancing targets and selection, objective) over the timed ms per step (graph "
+                          "form, CUDA events); per family: its bytes over its replay time",
+                  "families": fams},
+        "dominant_family": dom, "family_share": {f: round(v / total_fam, 4) for f, v in fam_ms.items()}
+        if total_fam > 0 else {},
+        "family_ms_per_step_replay": {f: round(v / args.steps, 4) for f, v in fam_ms.items()},
+        "family_times": "kernel-by-kernel replay of the timed steps (identical work)"})
+    return roof, launches
 
 
 def main():
@@ -724,15 +935,21 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="vlsi_2m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rownet_4m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-second", action="store_true", help="skip the vlsi_2m object beside the headline")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e-schedule", action="store_true", help="skip the whole-schedule end-to-end figure")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds of oracle iterations in the reference arm (at least one iteration)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--tune-sample", type=int, default=24, help="instances in each autotuner trial")
+    ap.add_argument("--tune-iterations", type=int, default=6, help="Jet iterations per instance in a trial")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--no-served", action="store_true")
@@ -776,42 +993,24 @@ def main():
     graph = None if args.no_graph else run_graph(args, r["dev"])
     cpu = None if args.no_cpu_baseline else cpu_baseline(hg, k, r["part0"], args.cpu_budget)
 
-    import json as _j
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = _j.load(open(pk))
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-
+    hbm, peak_src = hbm_peak()
     ms = r["ms"]
     value = job_throughput(hg.P * args.steps, world, ms)
-    prof = r["prof"]
-    fam_ms = {f: v["ms"] for f, v in prof.items()}
-    total_fam = sum(fam_ms.values())
-    dom = max(fam_ms, key=fam_ms.get)
-    cand_ms = r["prof_timed"]["candidates"]["ms"]  # measured inside the timed region
-    achieved = r["model_bytes"] / (cand_ms / 1e3) / 1e9 if cand_ms > 0 else None
-    replay_note = ("CUDA events around each launch in the kernel-by-kernel replay of the timed steps (these kernels "
-                   "also run inside conditional graph bodies, which cannot hold event nodes)")
-
-    def family_roofline(fam, kernel, nbytes, traffic_kernel):
-        fms, fl = prof[fam]["ms"], prof[fam]["launches"]
-        ach = nbytes / (fms / 1e3) / 1e9 if fms > 0 else None
-        return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": (ach / hbm) if ach else None,
-                "traffic": ncu_traffic(args.workload, traffic_kernel) if traffic_kernel else None,
-                "traffic_note": (f"mean DRAM bytes per launch, cold L2 (profiles/{traffic_kernel}.md)"
-                                 if traffic_kernel else "no capture for this kernel"),
-                "bytes_per_step": nbytes / args.steps, "ms_per_step": fms / args.steps,
-                "launches_per_step": fl / args.steps, "timing": replay_note, "peak_source": peak_src}
-
-    fam_roof = {"rebalance_targets": family_roofline("rebalance_targets",
-                                                     "rebalancing targets (k_rbcand_light/k_rbcand_heavy)",
-                                                     r["rb_bytes"], "k_rbcand_light"),
-                "apply": family_roofline("apply", "apply moves (k_apply, k_rb_apply)", r["apply_bytes"], "k_apply")}
-    dom_kernel = max(fam_roof, key=lambda f: prof[f]["ms"])  # the kernel with the most device time per step
-    launches = sum(v["launches"] for v in prof.values())
+    roof, launches = roofline_block(args, r, hbm, peak_src)
+    second = None
+    if not args.no_second and args.workload != "vlsi_2m":
+        import copy
+        a2 = copy.copy(args)
+        a2.workload = "vlsi_2m"
+        r2 = run_gpu(a2, rank, 1)
+        roof2, launches2 = roofline_block(a2, r2, hbm, peak_src)
+        second = {"value": r2["hg"].P * args.steps / (r2["ms"] / 1e3), "unit": "pins/s",
+                  "ms_per_step": r2["ms"] / args.steps, "steps": args.steps,
+                  "config": {"workload": r2["desc"], "n": r2["hg"].n, "m": r2["hg"].m, "pins": r2["hg"].P,
+                             "k": r2["k"], "tau": "3/4"},
+                  "roofline": roof2, "gpu_launches": launches2, "clocks": r2["clocks"], "trace_first_steps": r2["trace"][:3],
+                  "what": "the VLSI-shaped workload measured exactly like the headline (first K iterations at tau "
+                          "3/4, one CUDA graph per iteration, CUDA events)"}
     line = {
         "metric": "Jet-round pins/s (bit-exact vs oracle)",
         "value": value,
@@ -824,26 +1023,14 @@ def main():
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int32",
-        "data": "synthetic (seeded generator shaped like the paper's VLSI benchmark instances)",
+        "data": "synthetic (seeded generator shaped like the paper's sparse-matrix and VLSI benchmark instances)",
         "config": {"workload": r["desc"], "n": hg.n, "m": hg.m, "pins": hg.P, "k": k, "tau": "3/4",
                    "step": "one Jet iteration (candidates, afterburner, apply, rebalancing, objective)",
                    "execution": "kernel by kernel" if args.eager else "one CUDA graph per iteration (device-side "
                                                                           "rebalancing loop)",
                    "l2": "inputs larger than L2 (phi %d MB)" % (hg.m * k * 4 // 2 ** 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": dict(fam_roof[dom_kernel], **{
-                     "others": {f: v for f, v in fam_roof.items() if f != dom_kernel},
-                     "candidates": {"kernel": "k_cand_light/k_cand_heavy", "achieved": achieved,
-                                    "frac": (achieved / hbm) if achieved else None,
-                                    "traffic": ncu_traffic(args.workload),
-                                    "traffic_note": "DRAM bytes of the first timed launch (profiles/k_cand_light.md)",
-                                    "timing": "event-record nodes around the kernels inside the timed graphs",
-                                    "ms_per_step": cand_ms / args.steps,
-                                    "bytes_per_step": r["model_bytes"] / args.steps},
-                     "dominant_family": dom, "family_share": {f: round(v / total_fam, 4) for f, v in fam_ms.items()}
-                     if total_fam > 0 else {},
-                     "family_ms_per_step_replay": {f: round(v / args.steps, 4) for f, v in fam_ms.items()},
-                     "family_times": "kernel-by-kernel replay of the timed steps (identical work)"}),
+        "roofline": roof,
         "clocks": r["clocks"],
         "gpu_launches": launches,
         "e2e": e2e,
@@ -852,6 +1039,7 @@ def main():
         "served": served,
         "multilevel": multilevel,
         "graph": graph,
+        "vlsi_2m": second,
         "matching_schedule": r["schedule"],
         "trace_first_steps": r["trace"][:3],
     }
@@ -890,7 +1078,10 @@ def run_graph_only(args, rank):
 
 
 def run_reference(args, rank, world):
-    """The oracle (single thread) as the reference arm: each step one oracle Jet iteration."""
+    """The oracle (single thread) as the reference arm: each step one oracle Jet iteration at tau = 3/4 on the
+    same workload, from the same start.  A CPU program has no device state to warm, so the warm-up steps are
+    not run; and since one oracle iteration of the row-net workload takes most of a minute, the timed steps
+    stop once --ref-budget seconds have passed (at least one step), and the line reports how many ran."""
     if rank != 0:
         return
     import oracle
@@ -899,22 +1090,25 @@ def run_reference(args, rank, world):
     orc = oracle.Oracle(hg)
     st = oracle.State(orc, k, part0)
     prm = oracle.Params(k)
-    for _ in range(args.warmup):
-        orc.refine_round(prm, TAU, st.part, st.phi, st.bw, st.locked)
-    st = oracle.State(orc, k, part0)
+    done = 0
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    while done < args.steps:
         orc.refine_round(prm, TAU, st.part, st.phi, st.bw, st.locked)
+        done += 1
+        if time.perf_counter() - t0 >= args.ref_budget:
+            break
     el = time.perf_counter() - t0
-    value = hg.P * args.steps / el
+    value = hg.P * done / el
     line = {"impl": "reference", "metric": "Jet-round pins/s (bit-exact vs oracle)", "value": value,
-            "unit": "pins/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "unit": "pins/s", "n_gpus": world, "steps": done, "steps_requested": args.steps, "warmup": 0,
+            "warmup_requested": args.warmup,
+            "ms_per_step": el * 1e3 / done, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": desc, "n": hg.n, "m": hg.m, "pins": hg.P, "k": k, "tau": "3/4"},
-            "cpu_baseline": {"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {args.steps} Jet iterations at tau=3/4 (after {args.warmup} "
-                                       "warm-up iterations from the same start)"},
+            "cpu_baseline": dict({"value": value, "unit": "pins/s", "cores": 1, "kind": "oracle",
+                                  "sample": f"the first {done} of the {args.steps} requested Jet iterations at "
+                                            f"tau=3/4 from the seeded start ({el:.1f} s; time budget "
+                                            f"{args.ref_budget:.0f} s, no warm-up)"}, **host_cpu()),
             "e2e": {"value": value, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

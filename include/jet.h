@@ -149,8 +149,12 @@ int jet_connectivity(jet_ctx *ctx, const int32_t *phi, int64_t *objective_out);
  * jet_rebalance.  part[n], phi[m*k], block_w[k], locked[n] (uint8) are
  * updated in place and must describe one consistent state (as left by
  * jet_build_pincounts or a previous call).  stats (device, may be NULL)
- * receives the iteration's statistics.  See jet_set_graph_mode for whether
- * it synchronizes.
+ * receives the iteration's statistics.
+ * Synchronization: in graph mode (the default, see jet_set_graph_mode) the
+ * call does NOT synchronize (one graph launch; the first call with a new
+ * argument set also captures and instantiates the graph).  In the
+ * kernel-by-kernel mode it SYNCHRONIZES the stream once after ApplyMoves
+ * (to learn whether a block is overloaded) and once per rebalancing round.
  * Errors: JET_ERR_INVALID_ARG for tau outside [0,1) or NULL state arrays.
  */
 int jet_refine_round(jet_ctx *ctx, int32_t tau_num, int32_t tau_den, int32_t *part, int32_t *phi,
@@ -198,8 +202,10 @@ int jet_set_graph_path(jet_ctx *ctx, int enable);
  * block the minimal prefix of that order whose weight reaches the excess
  * moves, all at once.  Locks are ignored and unchanged.  stats (device, may
  * be NULL) receives rebalance_rounds, rebalance_moves, objective,
- * max_block_weight and imbalanced (other fields 0).  Synchronizes once per
- * round.
+ * max_block_weight and imbalanced (other fields 0).  SYNCHRONIZES the
+ * stream once before the first round (to learn whether a block is
+ * overloaded) and once per round (the stop rule is read on the host); it is
+ * the only call of the round's steps that always synchronizes.
  */
 int jet_rebalance(jet_ctx *ctx, int32_t *part, int32_t *phi, int64_t *block_w, jet_round_stats *stats);
 
@@ -258,6 +264,37 @@ int jet_batch_get_split(const jet_batch *batch);
 int jet_batch_tune(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
                    int32_t *const *phi, int64_t *const *block_w, const int32_t *splits, int32_t n_splits,
                    float *ms_out);
+
+/*
+ * Persistent form of a batch (the north star's "one persistent launch"):
+ * jet_batch_set_team(batch, ctas, threads) with ctas in {1, 2, 4, 8} and
+ * threads a multiple of 32 in [128, 1024] makes jet_batch_refine run ONE
+ * persistent kernel (captured in a CUDA graph with the reset of its work
+ * queue and the copy of the summaries): teams of `ctas` thread blocks (a
+ * thread-block cluster when ctas > 1) of `threads` threads each take the next
+ * instance from a device work queue (instances grouped by ceil(k/32), largest
+ * first) and run all of Algorithm 1 on it, with the team's barrier between
+ * phases, so every instance advances at its own pace.  ctas = 0 returns to
+ * the branch-graph form.  Results are identical to jet_refine on each
+ * instance alone.  Every context must be on the hypergraph path
+ * (JET_ERR_INVALID_ARG otherwise); a partition value outside [0, k) is
+ * JET_ERR_DATA for that instance (naming it in jet_batch_last_error), and
+ * that instance is not refined.
+ *
+ * jet_batch_autotune chooses the team shape: for each of the n_shapes
+ * (ctas, threads) pairs of `shapes` (HOST) it runs the persistent kernel on
+ * `sample` instances spread over the sizes of the batch, each stopped after
+ * trial_iterations Jet iterations, from the same partitions (restored before
+ * each trial and at the end), and keeps the shape with the most
+ * (pins x iterations) per second; ms_out and rate_out (HOST, n_shapes
+ * entries, may be NULL) receive each trial's device time and rate.  The
+ * arguments are those of jet_batch_refine.  Synchronizes.
+ */
+int jet_batch_set_team(jet_batch *batch, int32_t ctas, int32_t threads);
+int jet_batch_get_team(const jet_batch *batch, int32_t *ctas, int32_t *threads);
+int jet_batch_autotune(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
+                       int32_t *const *phi, int64_t *const *block_w, const int32_t *shapes, int32_t n_shapes,
+                       int32_t sample, int32_t trial_iterations, float *ms_out, double *rate_out);
 
 /*
  * Uncoarsening (the refinement phase of the multilevel scheme, §7.2: the
@@ -321,6 +358,13 @@ int jet_uncoarsen(jet_ctx *const *levels, int32_t n_levels, const int32_t *const
  * Both allocate stream-ordered scratch and free it before returning; both
  * report errors through jet_last_error(NULL); `stream` is a cudaStream_t.
  */
+/*
+ * max_cluster_weight also bounds the coarse vertex weights of the next level
+ * (a cluster of several vertices never exceeds it; a single vertex keeps its
+ * own weight).  jet_ctx_create accepts c(v) <= 32767 only (JET_ERR_OVERFLOW
+ * otherwise), so a hierarchy meant for jet_uncoarsen should use
+ * max_cluster_weight <= 32767.
+ */
 typedef struct {
   int64_t max_cluster_weight; /* bound on the weight of a cluster              */
   int32_t rating_max_edge;    /* edges with more pins add nothing to a rating  */
@@ -360,9 +404,15 @@ int jet_contract(const jet_hypergraph *hg, const int32_t *label, int32_t *map, c
  *
  * jet_server_wait moves up to max_done finished jobs into done (HOST) and
  * sets *n_done; it blocks until at least one job is done or timeout_ms
- * passes (0: no wait, < 0: no limit).  A job's own failure is in its status.
- * latency_ms runs from submission to the partition being back in host
- * memory; queue_ms from submission to admission.
+ * passes (0: no wait, < 0: no limit).  A job's own failure is in its status
+ * and its message.  latency_ms runs from submission to the partition being
+ * back in host memory; queue_ms from submission to admission (so the
+ * service time is latency_ms - queue_ms).  device_start_ms / device_end_ms
+ * place the job on the GPU timeline: CUDA events recorded on the job's
+ * stream before its first upload and after its partition's download,
+ * measured from an event recorded when the server was created; two jobs
+ * whose intervals intersect had work in flight on the device at the same
+ * time.
  *
  * jet_server_load reports the jobs waiting for admission, the jobs admitted
  * or running, and the reserved bytes.  jet_server_destroy waits for every
@@ -374,11 +424,14 @@ typedef struct jet_server jet_server;
 
 typedef struct {
   int64_t id;
-  int32_t status;            /* JET_OK or the job's error code       */
+  int32_t status;            /* JET_OK or the job's error code              */
   int32_t reserved;
-  double latency_ms;         /* submission -> result in host memory   */
-  double queue_ms;           /* submission -> admission               */
-  jet_refine_result result;  /* summary of the job's refinement       */
+  double latency_ms;         /* submission -> result in host memory          */
+  double queue_ms;           /* submission -> admission                      */
+  double device_start_ms;    /* GPU timeline: before the first upload        */
+  double device_end_ms;      /* GPU timeline: after the partition's download */
+  jet_refine_result result;  /* summary of the job's refinement              */
+  char message[128];         /* reason of a failed job ("" on success)       */
 } jet_job_done;
 
 size_t jet_job_footprint(int32_t n, int32_t m, int64_t P, int32_t k);
@@ -416,6 +469,20 @@ int jet_afterburner(jet_ctx *ctx, const int32_t *part, const int32_t *phi, int32
  */
 int jet_refine_host(const jet_hypergraph *hg_host, const jet_params *params, const int32_t *tau_pairs,
                     int32_t n_tau, int32_t limit, int32_t *part, jet_refine_result *result);
+
+/*
+ * End-to-end call on HOST buffers for a fixed number of iterations: copies
+ * the hypergraph (as for jet_refine_host) and part[n] to the device, builds
+ * phi and the block weights (jet_build_pincounts), clears the locks, runs
+ * n_rounds iterations of jet_refine_round at tau = tau_num/tau_den (the body
+ * of Algorithm 1, Section 4.1, without the loop control), and copies the
+ * partition back into part.  *stats (HOST, may be NULL) gets the last
+ * iteration's statistics.  Allocates and frees its own device memory.
+ * Synchronizes.  Errors as jet_ctx_create and jet_refine_round, and
+ * JET_ERR_INVALID_ARG for n_rounds < 0.
+ */
+int jet_rounds_host(const jet_hypergraph *hg_host, const jet_params *params, int32_t tau_num, int32_t tau_den,
+                    int32_t n_rounds, int32_t *part, jet_round_stats *stats);
 
 /*
  * Profiling.  The library's kernels fall into JET_PROF_FAMILIES families:
@@ -458,10 +525,12 @@ int jet_quotient_schedule(jet_ctx *ctx, const int32_t *phi, int32_t *pairs, int3
 /*
  * Work counts of the last jet_refine_round or jet_rebalance call (for byte
  * models of the kernels; always counted, no events).  Synchronizes.  Writes
- * up to n (<= 4) entries of out (HOST): [0] vertices of overloaded blocks
+ * up to n (<= 5) entries of out (HOST): [0] vertices of overloaded blocks
  * met by the rebalancing target passes, summed over the rounds; [1] vertices
  * they evaluated (one record each); [2] the incidences of those vertices;
- * [3] incidences of all moved vertices (Jet and rebalancing moves).
+ * [3] incidences of all moved vertices (Jet and rebalancing moves); [4] the
+ * levels of the rebalancing selection's radix select (a property of the
+ * context: every record is read once per level after the first).
  */
 int jet_profile_work(jet_ctx *ctx, int64_t *out, int32_t n);
 
@@ -479,12 +548,16 @@ int jet_profile_work(jet_ctx *ctx, int64_t *out, int32_t n);
  * Scratch: a file-scope device array of 1.25 KiB per GPU, resident until
  * process exit, limits k to [2, 256] (JET_ERR_INVALID_ARG otherwise).  The
  * first call on each device looks up the array's device address with that
- * device current (cudaGetSymbolAddress) and caches it; make that first call
- * before any stream capture.  Every call clears the array first; calls that
- * overlap on the GPU share it and race.  Allocates nothing (no cudaMalloc,
- * cudaFree or allocating library call).  Synchronizes the stream to read the
- * data-error flag: a value of part outside [0,k) returns JET_ERR_DATA.
- * Errors are reported by jet_last_error(NULL).
+ * device current (cudaGetSymbolAddress) and caches it for the rest of the
+ * process, so do not keep calling it across a cudaDeviceReset of that device
+ * (the cached address would be stale).  Every call clears the array first;
+ * calls that overlap on the GPU share it and race.  Allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library call).  SYNCHRONIZES the stream
+ * (it copies the data-error flag to the host and waits), so it must not be
+ * called while that stream is being captured into a CUDA graph.  A value of
+ * part outside [0,k) or a weight vwgt[v] < 1 returns JET_ERR_DATA (block_w
+ * and block_count are then not meaningful).  Errors are reported by
+ * jet_last_error(NULL).
  */
 int jet_block_weights_noalloc(const int32_t *part, const int32_t *vwgt, int32_t n, int32_t k, int64_t *block_w,
                               int32_t *block_count, void *stream);

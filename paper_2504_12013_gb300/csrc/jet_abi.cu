@@ -732,10 +732,13 @@ int jet_quotient_schedule(jet_ctx *c, const int32_t *phi, int32_t *pairs, int32_
 int jet_profile_work(jet_ctx *c, int64_t *out, int32_t n) {
   int rc = check_ctx(c);
   if (rc) return rc;
-  if (n < 0 || n > 4 || (n > 0 && !out)) return fail(c, JET_ERR_INVALID_ARG, "n must be in [0, 4]");
-  unsigned long long w[4];
-  CK(cudaMemcpyAsync(w, &c->cnt->w_over, sizeof(w), cudaMemcpyDeviceToHost, c->stream), "work counts");
+  if (n < 0 || n > 5 || (n > 0 && !out)) return fail(c, JET_ERR_INVALID_ARG, "n must be in [0, 5]");
+  unsigned long long w[5];
+  CK(cudaMemcpyAsync(w, &c->cnt->w_over, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream),
+     "work counts");
   CK(cudaStreamSynchronize(c->stream), "synchronize");
+  const int tb = c->rb_hbits + c->rb_vbits;
+  w[4] = (unsigned long long)((tb + c->rb_digit - 1) / c->rb_digit);  // radix-select levels per round
   for (int i = 0; i < n; ++i) out[i] = (int64_t)w[i];
   return JET_OK;
 }
@@ -748,6 +751,26 @@ int jet_refine_host(const jet_hypergraph *hh, const jet_params *p, const int32_t
   cudaStream_t s = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e != cudaSuccess) return fail(nullptr, JET_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+  const int rc = jet::refine_host_on(hh, p, tau_pairs, n_tau, limit, part, result, s, nullptr, nullptr);
+  cudaStreamDestroy(s);
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+// A job on host buffers: uploads the hypergraph and part to device buffers of
+// its own (stream-ordered on s), creates a context, runs body(ctx, part, phi,
+// block_w), downloads part, and frees everything.  ev_start / ev_end (may be
+// NULL) are recorded before the first upload and after the download.
+template <class Body>
+int host_job(const jet_hypergraph *hh, const jet_params *p, int32_t *part, cudaStream_t s, cudaEvent_t ev_start,
+             cudaEvent_t ev_end, Body body) {
+  if (!hh || !p || !part) return fail(nullptr, JET_ERR_INVALID_ARG, "NULL argument");
+  if (hh->n < 0 || hh->m < 0 || hh->P < 0 || p->k < 2 || p->k > kMaxK)
+    return fail(nullptr, JET_ERR_INVALID_ARG, "bad sizes or k");
+  cudaError_t e = ev_start ? cudaEventRecord(ev_start, s) : cudaSuccess;
   const size_t n = (size_t)hh->n, m = (size_t)hh->m, P = (size_t)hh->P, k = (size_t)p->k;
   int64_t *eptr = nullptr, *vptr = nullptr, *bw = nullptr;
   int32_t *pins = nullptr, *inc = nullptr, *vw = nullptr, *ew = nullptr, *pt = nullptr, *phi = nullptr;
@@ -771,22 +794,59 @@ int jet_refine_host(const jet_hypergraph *hh, const jet_params *p, const int32_t
     jet_hypergraph dh{hh->n, hh->m, hh->P, eptr, pins, vptr, inc, vw, ew};
     rc = jet_ctx_create(&c, &dh, p, s);
   }
-  jet_refine_result local;
   if (rc == JET_OK) {
-    rc = jet_refine(c, tau_pairs, n_tau, limit, pt, phi, bw, result ? result : &local);
+    rc = body(c, pt, phi, bw);
     if (rc != JET_OK) snprintf(g_err, sizeof(g_err), "%s", c->err);
   }
   if (rc == JET_OK && n) {
     e = cudaMemcpyAsync(part, pt, 4 * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && ev_end) e = cudaEventRecord(ev_end, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = fail(nullptr, JET_ERR_CUDA, "download: %s", cudaGetErrorString(e));
+  } else if (rc == JET_OK && ev_end) {
+    cudaEventRecord(ev_end, s);
   }
   if (c) jet_ctx_destroy(c);
   for (int i = 0; i < 9; ++i)
     if (*bufs[i]) cudaFreeAsync(*bufs[i], s);
   cudaStreamSynchronize(s);
-  cudaStreamDestroy(s);
   return rc;
 }
 
-}  // extern "C"
+}  // namespace
+
+// jet_refine_host on a caller's stream; ev_start / ev_end (may be NULL) are
+// recorded before the first upload and after the partition's download.
+int jet::refine_host_on(const jet_hypergraph *hh, const jet_params *p, const int32_t *tau_pairs, int32_t n_tau,
+                        int32_t limit, int32_t *part, jet_refine_result *result, cudaStream_t s, cudaEvent_t ev_start,
+                        cudaEvent_t ev_end) {
+  jet_refine_result local;
+  return host_job(hh, p, part, s, ev_start, ev_end, [&](jet_ctx *c, int32_t *pt, int32_t *phi, int64_t *bw) {
+    return jet_refine(c, tau_pairs, n_tau, limit, pt, phi, bw, result ? result : &local);
+  });
+}
+
+extern "C" int jet_rounds_host(const jet_hypergraph *hh, const jet_params *p, int32_t tau_num, int32_t tau_den,
+                               int32_t n_rounds, int32_t *part, jet_round_stats *stats) {
+  if (n_rounds < 0) return fail(nullptr, JET_ERR_INVALID_ARG, "n_rounds = %d is negative", n_rounds);
+  if (tau_den <= 0 || tau_num < 0 || tau_num >= tau_den)
+    return fail(nullptr, JET_ERR_INVALID_ARG, "temperature %d/%d is outside [0, 1)", tau_num, tau_den);
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return fail(nullptr, JET_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+  const int rc = host_job(hh, p, part, s, nullptr, nullptr, [&](jet_ctx *c, int32_t *pt, int32_t *phi, int64_t *bw) {
+    int r = jet_build_pincounts(c, pt, phi, bw);
+    if (r) return r;
+    if (c->n > 0) CK(cudaMemsetAsync(c->locked_ws, 0, c->n, c->stream), "locks");
+    for (int32_t i = 0; i < n_rounds && r == JET_OK; ++i)
+      r = jet_refine_round(c, tau_num, tau_den, pt, phi, bw, c->locked_ws, c->stats_scratch);
+    if (r) return r;
+    if (stats) {
+      CK(cudaMemcpyAsync(stats, c->stats_scratch, sizeof(jet_round_stats), cudaMemcpyDeviceToHost, c->stream),
+         "stats");
+    }
+    return sync_counters(c);
+  });
+  cudaStreamDestroy(s);
+  return rc;
+}

@@ -256,6 +256,15 @@ struct jet_batch {
   jet_refine_result *res_host = nullptr;
   int split = 0;        // 0: every instance sizes its grids for all SMs; s > 0: see jet_batch_set_split
   int built_split = -1;
+  // persistent form (team_ctas > 0): one kernel whose teams of team_ctas blocks of team_threads threads each
+  // refine one instance at a time from a device queue
+  int team_ctas = 0, team_threads = 0;
+  jet::TeamPlan *plan = nullptr;
+  std::vector<const void *> plan_args;  // part, phi, block_w of every instance, the schedule and the limit the
+  std::vector<int32_t> plan_tau;        // plan and its graph were built for
+  int32_t plan_limit = 0;
+  cudaGraphExec_t team_exec = nullptr;
+  int team_exec_ctas = 0, team_exec_threads = 0;
   char err[256] = {0};
 };
 
@@ -357,6 +366,72 @@ int check_batch_args(jet_batch *b, const int32_t *tau, int32_t n_tau, int32_t li
   return JET_OK;
 }
 
+// The device plan of the persistent form for this schedule and these state arrays (rebuilt when they change).
+int ensure_plan(jet_batch *b, const int32_t *tau, int32_t n_tau, int32_t limit, int32_t *const *part,
+                int32_t *const *phi, int64_t *const *block_w) {
+  std::vector<const void *> args;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    args.push_back(part[i]);
+    args.push_back(phi[i]);
+    args.push_back(block_w[i]);
+  }
+  std::vector<int32_t> t(tau, tau + 2 * n_tau);
+  if (b->plan && args == b->plan_args && t == b->plan_tau && limit == b->plan_limit) return JET_OK;
+  if (b->team_exec) cudaGraphExecDestroy(b->team_exec);
+  b->team_exec = nullptr;
+  if (b->plan) jet::team_plan_destroy(b->plan, b->stream);
+  b->plan = nullptr;
+  for (jet_ctx *c : b->ctx) {
+    if (c->graph_path) return bfail(b, JET_ERR_INVALID_ARG, "the persistent form needs every instance on the hypergraph path");
+    cudaStreamSynchronize(c->stream);
+  }
+  int rc = jet::team_plan_build(&b->plan, b->ctx.data(), (int32_t)b->ctx.size(), part, phi, block_w, tau, n_tau,
+                                b->stream);
+  if (rc) return bfail(b, rc, jet_last_error(nullptr));
+  b->plan_args = args;
+  b->plan_tau = t;
+  b->plan_limit = limit;
+  return JET_OK;
+}
+
+// The persistent form: one graph (queue reset, the persistent launches, the summaries to the host), launched on
+// b->stream; waits and reports.
+int run_team(jet_batch *b, int32_t limit, jet_refine_result *results) {
+  if (!b->team_exec || b->team_exec_ctas != b->team_ctas || b->team_exec_threads != b->team_threads) {
+    if (b->team_exec) cudaGraphExecDestroy(b->team_exec);
+    b->team_exec = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t ec = jet::team_launch(b->plan, b->team_ctas, b->team_threads, limit, 0, b->origin, nullptr, 0);
+      if (ec == cudaSuccess) ec = jet::team_results(b->plan, b->res_host, b->origin);
+      e = cudaStreamEndCapture(b->origin, &g);
+      if (ec != cudaSuccess) e = ec;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->team_exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->team_exec = nullptr;
+      return bfail(b, JET_ERR_CUDA, "persistent batch graph", e);
+    }
+    b->team_exec_ctas = b->team_ctas;
+    b->team_exec_threads = b->team_threads;
+  }
+  cudaError_t e = cudaGraphLaunch(b->team_exec, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, JET_ERR_CUDA, "persistent batch launch", e);
+  const int bad = jet::team_first_error(b->plan, b->stream);
+  if (bad == -2) return bfail(b, JET_ERR_CUDA, "persistent batch error check");
+  if (bad >= 0) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "instance %d: a partition value is outside [0, k)", bad);
+    return bfail(b, JET_ERR_DATA, msg);
+  }
+  for (size_t i = 0; i < b->ctx.size(); ++i) b->ctx[i]->phi_owner = static_cast<const int32_t *>(b->plan_args[3 * i + 1]);
+  if (results) memcpy(results, b->res_host, sizeof(jet_refine_result) * b->ctx.size());
+  return JET_OK;
+}
+
 // Launch the batch graph on b->stream and wait; report per-instance errors.
 int run_batch(jet_batch *b, jet_refine_result *results) {
   cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
@@ -407,6 +482,8 @@ void jet_batch_destroy(jet_batch *b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->team_exec) cudaGraphExecDestroy(b->team_exec);
+  if (b->plan) jet::team_plan_destroy(b->plan, b->stream);
   for (jet_ctx *c : b->ctx) c->launch_sms = c->num_sms;
   if (b->origin) cudaStreamDestroy(b->origin);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -426,10 +503,109 @@ int jet_batch_set_split(jet_batch *b, int32_t split) {
 
 int jet_batch_get_split(const jet_batch *b) { return b ? b->split : -1; }
 
+int jet_batch_set_team(jet_batch *b, int32_t ctas, int32_t threads) {
+  if (!b) return bfail(nullptr, JET_ERR_INVALID_ARG, "batch is NULL");
+  if (ctas == 0) {
+    b->team_ctas = b->team_threads = 0;
+    return JET_OK;
+  }
+  if (!(ctas == 1 || ctas == 2 || ctas == 4 || ctas == 8))
+    return bfail(b, JET_ERR_INVALID_ARG, "team blocks must be 1, 2, 4 or 8");
+  if (threads < 128 || threads > 1024 || threads % 32)
+    return bfail(b, JET_ERR_INVALID_ARG, "team threads must be a multiple of 32 in [128, 1024]");
+  for (jet_ctx *c : b->ctx)
+    if (c->graph_path) return bfail(b, JET_ERR_INVALID_ARG, "the persistent form needs every instance on the hypergraph path");
+  b->team_ctas = ctas;
+  b->team_threads = threads;
+  return JET_OK;
+}
+
+int jet_batch_get_team(const jet_batch *b, int32_t *ctas, int32_t *threads) {
+  if (!b || !ctas || !threads) return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL argument");
+  *ctas = b->team_ctas;
+  *threads = b->team_threads;
+  return JET_OK;
+}
+
+int jet_batch_autotune(jet_batch *b, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
+                       int32_t *const *phi, int64_t *const *block_w, const int32_t *shapes, int32_t n_shapes,
+                       int32_t sample, int32_t trial_iterations, float *ms_out, double *rate_out) {
+  int rc = check_batch_args(b, tau_pairs, n_tau, limit, part, phi, block_w);
+  if (rc) return rc;
+  if (n_shapes < 1 || !shapes) return bfail(b, JET_ERR_INVALID_ARG, "no team shapes to try");
+  if (sample < 1 || trial_iterations < 1) return bfail(b, JET_ERR_INVALID_ARG, "sample and trial_iterations must be >= 1");
+  for (int i = 0; i < n_shapes; ++i) {
+    const int c = shapes[2 * i], t = shapes[2 * i + 1];
+    if (!(c == 1 || c == 2 || c == 4 || c == 8) || t < 128 || t > 1024 || t % 32)
+      return bfail(b, JET_ERR_INVALID_ARG, "a team shape is outside {1,2,4,8} x [128, 1024] (multiples of 32)");
+  }
+  if ((rc = ensure_plan(b, tau_pairs, n_tau, limit, part, phi, block_w))) return rc;
+  const std::vector<int32_t> smp = jet::team_sample(b->plan, sample);
+  // every trial starts from the sample's partitions: keep device copies
+  std::vector<int32_t *> saved(smp.size(), nullptr);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < smp.size() && e == cudaSuccess; ++i) {
+    const jet_ctx *c = b->ctx[smp[i]];
+    if (c->n == 0) continue;
+    e = cudaMalloc(reinterpret_cast<void **>(&saved[i]), sizeof(int32_t) * c->n);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(saved[i], part[smp[i]], sizeof(int32_t) * c->n, cudaMemcpyDeviceToDevice, b->stream);
+  }
+  auto restore = [&]() {
+    for (size_t i = 0; i < smp.size() && e == cudaSuccess; ++i)
+      if (saved[i])
+        e = cudaMemcpyAsync(part[smp[i]], saved[i], sizeof(int32_t) * b->ctx[smp[i]]->n, cudaMemcpyDeviceToDevice,
+                            b->stream);
+  };
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  std::vector<jet_refine_result> res(b->ctx.size());
+  int best = -1;
+  double best_rate = 0.0;
+  for (int t = 0; t < n_shapes && e == cudaSuccess; ++t) {
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) {  // an untimed run (first launch of this shape), a timed one
+      restore();
+      if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+      if (e == cudaSuccess)
+        e = jet::team_launch(b->plan, shapes[2 * t], shapes[2 * t + 1], limit, trial_iterations, b->stream,
+                             smp.data(), (int32_t)smp.size());
+      if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+      if (e == cudaSuccess) e = jet::team_results(b->plan, res.data(), b->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+    double work = 0.0;
+    for (int32_t i : smp) work += (double)jet::team_pins(b->plan, i) * (double)res[i].iterations;
+    const double rate = ms > 0.f ? work / (ms * 1e-3) : 0.0;
+    if (ms_out) ms_out[t] = ms;
+    if (rate_out) rate_out[t] = rate;
+    if (e == cudaSuccess && (best < 0 || rate > best_rate)) {
+      best = t;
+      best_rate = rate;
+    }
+  }
+  restore();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  for (int32_t *q : saved)
+    if (q) cudaFree(q);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return bfail(b, JET_ERR_CUDA, "persistent batch tuning", e);
+  b->team_ctas = shapes[2 * best];
+  b->team_threads = shapes[2 * best + 1];
+  return JET_OK;
+}
+
 int jet_batch_refine(jet_batch *b, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
                      int32_t *const *phi, int64_t *const *block_w, jet_refine_result *results) {
   int rc = check_batch_args(b, tau_pairs, n_tau, limit, part, phi, block_w);
   if (rc) return rc;
+  if (b->team_ctas > 0) {
+    if ((rc = ensure_plan(b, tau_pairs, n_tau, limit, part, phi, block_w))) return rc;
+    return run_team(b, limit, results);
+  }
   if (!batch_key_matches(b, tau_pairs, n_tau, limit, part, phi, block_w) &&
       (rc = build_batch(b, tau_pairs, n_tau, limit, part, phi, block_w)))
     return rc;

@@ -278,6 +278,24 @@ __device__ __forceinline__ unsigned long long block_append(bool sel, unsigned lo
   return pos;
 }
 
+// jet_refine_host on the caller's stream s (not destroyed); ev_start / ev_end (may be NULL) are recorded on s
+// before the first upload and after the partition's download (the job's interval on the GPU timeline).
+int refine_host_on(const jet_hypergraph *hh, const jet_params *p, const int32_t *tau_pairs, int32_t n_tau,
+                   int32_t limit, int32_t *part, jet_refine_result *result, cudaStream_t s, cudaEvent_t ev_start,
+                   cudaEvent_t ev_end);
+
+// ---- batched form as one persistent kernel (k_batch.cu)
+struct TeamPlan;  // device descriptors of a batch's instances, their queue order and summaries
+int team_plan_build(TeamPlan **out, jet_ctx *const *ctxs, int32_t count, int32_t *const *part, int32_t *const *phi,
+                    int64_t *const *block_w, const int32_t *tau_pairs, int32_t n_tau, cudaStream_t s);
+void team_plan_destroy(TeamPlan *p, cudaStream_t s);
+cudaError_t team_launch(TeamPlan *p, int ctas, int threads, int32_t limit, int32_t iter_cap, cudaStream_t s,
+                        const int32_t *sub_order, int32_t n_sub);
+cudaError_t team_results(TeamPlan *p, jet_refine_result *dst, cudaStream_t s);
+int team_first_error(TeamPlan *p, cudaStream_t s);
+std::vector<int32_t> team_sample(TeamPlan *p, int32_t n);
+long long team_pins(TeamPlan *p, int32_t i);
+
 // Sets the message returned by jet_last_error(NULL) (for entry points without a context).
 void set_global_error(const char *fmt, ...);
 

@@ -50,13 +50,18 @@ struct jet_server {
   std::deque<jet_job_done> done;
   std::vector<std::thread> workers;
   int device = 0;
+  cudaEvent_t ev_ref = nullptr;     // origin of the jobs' GPU-timeline intervals
+  std::mutex err_mu;                // guards err (calls from several threads may fail at once)
   char err[256] = {0};
 };
 
 namespace {
 
 int sfail(jet_server *s, int code, const char *msg) {
-  if (s) snprintf(s->err, sizeof(s->err), "%s", msg);
+  if (s) {
+    std::lock_guard<std::mutex> lk(s->err_mu);
+    snprintf(s->err, sizeof(s->err), "%s", msg);
+  }
   jet::set_global_error("%s", msg);
   return code;
 }
@@ -77,12 +82,17 @@ void admit_locked(jet_server *s) {
 
 void worker_main(jet_server *s) {
   cudaSetDevice(s->device);
+  // one stream and one pair of timing events per worker, reused by its jobs
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  const bool timed = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess;
   for (;;) {
     Job j;
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_work.wait(lk, [&] { return s->stopping || !s->admitted.empty(); });
-      if (s->admitted.empty()) return;  // stopping and nothing left
+      if (s->admitted.empty()) break;  // stopping and nothing left
       j = std::move(s->admitted.front());
       s->admitted.pop_front();
       s->active += 1;
@@ -90,11 +100,27 @@ void worker_main(jet_server *s) {
     jet_job_done d;
     memset(&d, 0, sizeof(d));
     d.id = j.id;
-    d.status = jet_refine_host(&j.hg, &j.params, j.tau.data(), (int32_t)(j.tau.size() / 2), j.limit, j.part,
-                               &d.result);
+    if (timed) {
+      d.status = jet::refine_host_on(&j.hg, &j.params, j.tau.data(), (int32_t)(j.tau.size() / 2), j.limit, j.part,
+                                     &d.result, stream, ev0, ev1);
+    } else {
+      d.status = jet_refine_host(&j.hg, &j.params, j.tau.data(), (int32_t)(j.tau.size() / 2), j.limit, j.part,
+                                 &d.result);
+    }
     const Clock::time_point t_end = Clock::now();
     d.latency_ms = std::chrono::duration<double, std::milli>(t_end - j.t_submit).count();
     d.queue_ms = std::chrono::duration<double, std::milli>(j.t_admit - j.t_submit).count();
+    d.device_start_ms = d.device_end_ms = -1.0;
+    if (d.status != JET_OK) {
+      snprintf(d.message, sizeof(d.message), "%s", jet_last_error(nullptr));  // this worker thread's error text
+    } else if (timed && s->ev_ref) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, s->ev_ref, ev0) == cudaSuccess &&
+          cudaEventElapsedTime(&b, s->ev_ref, ev1) == cudaSuccess) {
+        d.device_start_ms = a;
+        d.device_end_ms = b;
+      }
+    }
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->active -= 1;
@@ -104,6 +130,9 @@ void worker_main(jet_server *s) {
     }
     s->cv_done.notify_all();
   }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (stream) cudaStreamDestroy(stream);
 }
 
 }  // namespace
@@ -133,6 +162,14 @@ int jet_server_create(jet_server **out, size_t hbm_budget, int32_t max_active) {
   s->budget = hbm_budget;
   s->max_active = max_active;
   cudaGetDevice(&s->device);
+  if (cudaEventCreate(&s->ev_ref) == cudaSuccess) {  // the origin of the jobs' GPU-timeline intervals
+    if (cudaEventRecord(s->ev_ref, nullptr) != cudaSuccess || cudaEventSynchronize(s->ev_ref) != cudaSuccess) {
+      cudaEventDestroy(s->ev_ref);
+      s->ev_ref = nullptr;
+    }
+  } else {
+    s->ev_ref = nullptr;
+  }
   try {
     for (int i = 0; i < max_active; ++i) s->workers.emplace_back(worker_main, s);
   } catch (...) {
@@ -207,6 +244,7 @@ void jet_server_destroy(jet_server *s) {
   s->cv_work.notify_all();
   for (std::thread &t : s->workers)
     if (t.joinable()) t.join();
+  if (s->ev_ref) cudaEventDestroy(s->ev_ref);
   delete s;
 }
 

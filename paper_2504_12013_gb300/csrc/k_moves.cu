@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(256) k_rb_level(RbArgs a, int lo, int w) {
         c = (unsigned)(ct >> 16);
       }
     }
+    if (!__any_sync(kFull, m)) continue;  // after the first level few records still match: skip the grouping
     const int code = m ? (b << 16) | d : -1 - lane;
     const unsigned grp = __match_any_sync(kFull, code);
     const unsigned sum = __reduce_add_sync(grp, c);

@@ -23,6 +23,8 @@ namespace {
 constexpr int kNoAllocMaxK = 256;                   // largest k the static scratch holds
 constexpr int kScratchInts = kNoAllocMaxK + 64;     // counts[256], error flag at [256], padding
 constexpr int kErrSlot = kNoAllocMaxK;
+constexpr int kErrBadPart = 1;    // error-slot bit: a partition value outside [0, k)
+constexpr int kErrBadWeight = 2;  // error-slot bit: a vertex weight below 1
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kScratchInts];
@@ -40,11 +42,14 @@ __global__ void k_block_weights_static(const int32_t *part, const int32_t *vwgt,
   int err = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int b = part[v];
-    if ((unsigned)b < (unsigned)k) {
-      atomicAdd(reinterpret_cast<unsigned long long *>(&s_bw[b]), (unsigned long long)vwgt[v]);
+    const int32_t c = vwgt[v];
+    if (c < 1) {
+      err |= kErrBadWeight;  // c(v) >= 1 is required, as jet_ctx_create requires it
+    } else if ((unsigned)b < (unsigned)k) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(&s_bw[b]), (unsigned long long)c);
       atomicAdd(&s_cnt[b], 1);
     } else {
-      err = 1;
+      err |= kErrBadPart;
     }
   }
   __syncthreads();
@@ -52,7 +57,7 @@ __global__ void k_block_weights_static(const int32_t *part, const int32_t *vwgt,
     if (s_bw[b]) atomicAdd(reinterpret_cast<unsigned long long *>(&bw[b]), (unsigned long long)s_bw[b]);
     if (s_cnt[b]) atomicAdd(&scratch[b], s_cnt[b]);
   }
-  if (err) atomicOr(&scratch[kErrSlot], 1);
+  if (err) atomicOr(&scratch[kErrSlot], err);
 }
 
 // Device address of the scratch array for the current device, looked up once
@@ -117,6 +122,10 @@ extern "C" int jet_block_weights_noalloc(const int32_t *part, const int32_t *vwg
   if (e != cudaSuccess) {
     jet::set_global_error("jet_block_weights_noalloc: %s", cudaGetErrorString(e));
     return JET_ERR_CUDA;
+  }
+  if (flag & kErrBadWeight) {
+    jet::set_global_error("jet_block_weights_noalloc: a vertex weight c(v) is below 1");
+    return JET_ERR_DATA;
   }
   if (flag) {
     jet::set_global_error("jet_block_weights_noalloc: a partition value is outside [0, %d)", k);

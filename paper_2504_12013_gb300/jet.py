@@ -28,7 +28,8 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_batch_refine", "jet_batch_set_split", "jet_batch_get_split", "jet_batch_tune",
            "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
            "jet_server_last_error", "jet_server_destroy", "jet_profile_work", "jet_quotient_schedule",
-           "jet_uncoarsen", "jet_cluster", "jet_contract", "jet_set_graph_path")
+           "jet_uncoarsen", "jet_cluster", "jet_contract", "jet_set_graph_path", "jet_rounds_host",
+           "jet_batch_set_team", "jet_batch_get_team", "jet_batch_autotune")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -76,7 +77,9 @@ class JetRefineResult(ctypes.Structure):
 
 class JetJobDone(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("result", JetRefineResult)]
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("device_start_ms", ctypes.c_double), ("device_end_ms", ctypes.c_double),
+                ("result", JetRefineResult), ("message", ctypes.c_char * 128)]
 
 
 class JetError(RuntimeError):
@@ -113,6 +116,7 @@ def load_library():
             lib.jet_afterburner.argtypes = [_P, _P, _P, _P, _P]
             lib.jet_refine_host.argtypes = [pp(JetHypergraph), pp(JetParams), pp(i32), i32, i32, _P,
                                             pp(JetRefineResult)]
+            lib.jet_rounds_host.argtypes = [pp(JetHypergraph), pp(JetParams), i32, i32, i32, _P, pp(JetRoundStats)]
             lib.jet_profile_enable.argtypes = [_P, ctypes.c_int]
             lib.jet_profile_read.argtypes = [_P, pp(ctypes.c_double), pp(i64), pp(i64), ctypes.c_int]
             lib.jet_block_weights_noalloc.argtypes = [_P, _P, i32, i32, _P, _P, _P]
@@ -135,6 +139,10 @@ def load_library():
             lib.jet_batch_get_split.argtypes = [_P]
             lib.jet_batch_tune.argtypes = [_P, pp(i32), i32, i32, pp(_P), pp(_P), pp(_P), pp(i32), i32,
                                            pp(ctypes.c_float)]
+            lib.jet_batch_set_team.argtypes = [_P, i32, i32]
+            lib.jet_batch_get_team.argtypes = [_P, pp(i32), pp(i32)]
+            lib.jet_batch_autotune.argtypes = [_P, pp(i32), i32, i32, pp(_P), pp(_P), pp(_P), pp(i32), i32, i32, i32,
+                                               pp(ctypes.c_float), pp(ctypes.c_double)]
             sz = ctypes.c_size_t
             lib.jet_job_footprint.argtypes = [i32, i32, i64, i32]
             lib.jet_job_footprint.restype = sz
@@ -368,6 +376,18 @@ def jet_refine_host(hg, p: JetParams, schedule, limit, part: np.ndarray) -> dict
     return res.as_dict()
 
 
+def jet_rounds_host(hg, p: JetParams, tau, n_rounds, part: np.ndarray) -> dict:
+    """Host buffers in and out: n_rounds Jet iterations at temperature tau from ``part`` (int32[n], updated in
+    place); returns the last iteration's statistics."""
+    assert part.dtype == np.int32 and part.flags.c_contiguous
+    arrs = [np.ascontiguousarray(a) for a in (hg.eptr, hg.pins, hg.vptr, hg.inc, hg.vwgt, hg.ewgt)]
+    ch = JetHypergraph(hg.n, hg.m, hg.P, *[a.ctypes.data for a in arrs])
+    st = JetRoundStats()
+    _check(load_library().jet_rounds_host(ctypes.byref(ch), ctypes.byref(p), int(tau[0]), int(tau[1]),
+                                          int(n_rounds), part.ctypes.data, ctypes.byref(st)))
+    return {f: int(getattr(st, f)) for f in STATS_FIELDS[:7]}
+
+
 def jet_set_graph_mode(ctx: Ctx, enable: bool = True):
     _check(load_library().jet_set_graph_mode(ctx.handle, 1 if enable else 0), ctx)
 
@@ -422,12 +442,12 @@ def jet_quotient_schedule(ctx: Ctx, phi):
     return pairs[: 2 * p].cpu().numpy().reshape(-1, 2), rnd[:p].cpu().numpy(), nr.value
 
 
-WORK_FIELDS = ("rebalance_over", "rebalance_evaluated", "rebalance_evaluated_pins", "moved_pins")
+WORK_FIELDS = ("rebalance_over", "rebalance_evaluated", "rebalance_evaluated_pins", "moved_pins", "select_levels")
 
 
 def jet_profile_work(ctx: Ctx) -> dict:
-    out = (ctypes.c_int64 * 4)()
-    _check(load_library().jet_profile_work(ctx.handle, out, 4), ctx)
+    out = (ctypes.c_int64 * 5)()
+    _check(load_library().jet_profile_work(ctx.handle, out, 5), ctx)
     return dict(zip(WORK_FIELDS, [int(x) for x in out]))
 
 
@@ -516,6 +536,33 @@ def jet_batch_tune(batch: Batch, schedule, limit, states, splits) -> tuple:
     return jet_batch_get_split(batch), {int(s): float(t) for s, t in zip(splits, ms)}
 
 
+# team shapes (blocks per team, threads per block) the persistent form's autotuner tries by default
+TEAM_SHAPES = ((1, 256), (1, 512), (1, 1024), (2, 512), (2, 1024), (4, 1024), (8, 1024))
+
+
+def jet_batch_set_team(batch: Batch, ctas: int, threads: int = 1024):
+    """Persistent form with teams of `ctas` blocks of `threads` threads (ctas = 0: the branch-graph form)."""
+    _batch_check(load_library().jet_batch_set_team(batch.handle, int(ctas), int(threads)), batch)
+
+
+def jet_batch_get_team(batch: Batch) -> tuple:
+    c, t = ctypes.c_int32(), ctypes.c_int32()
+    _batch_check(load_library().jet_batch_get_team(batch.handle, ctypes.byref(c), ctypes.byref(t)), batch)
+    return c.value, t.value
+
+
+def jet_batch_autotune(batch: Batch, schedule, limit, states, shapes=TEAM_SHAPES, sample=24, trial_iterations=8):
+    """Choose the persistent form's team shape from short trials on a sample; returns (shape, {shape: (ms, rate)})."""
+    part, phi, bw = _state_arrays(states)
+    sh = (ctypes.c_int32 * (2 * len(shapes)))(*[int(x) for p in shapes for x in p])
+    ms = (ctypes.c_float * len(shapes))()
+    rate = (ctypes.c_double * len(shapes))()
+    _batch_check(load_library().jet_batch_autotune(batch.handle, _pairs(schedule), len(schedule), int(limit), part, phi,
+                                                   bw, sh, len(shapes), int(sample), int(trial_iterations), ms, rate),
+                 batch)
+    return jet_batch_get_team(batch), {tuple(p): (float(m), float(r)) for p, m, r in zip(shapes, ms, rate)}
+
+
 def jet_job_footprint(n, m, P, k) -> int:
     return int(load_library().jet_job_footprint(int(n), int(m), int(P), int(k)))
 
@@ -571,7 +618,8 @@ def jet_server_submit(server: Server, hg, p: JetParams, schedule, limit, part: n
 
 
 def jet_server_wait(server: Server, max_done: int = 64, timeout_ms: int = -1) -> list:
-    """Finished jobs as dicts (id, status, latency_ms, queue_ms, result)."""
+    """Finished jobs as dicts (id, status, latency_ms, queue_ms, service_ms, device_start_ms, device_end_ms,
+    message, result)."""
     buf = (JetJobDone * max_done)()
     nd = ctypes.c_int32()
     _server_check(load_library().jet_server_wait(server.handle, buf, max_done, ctypes.byref(nd), int(timeout_ms)),
@@ -580,6 +628,8 @@ def jet_server_wait(server: Server, max_done: int = 64, timeout_ms: int = -1) ->
     for d in buf[: nd.value]:
         server.keep.pop(d.id, None)
         out.append({"id": d.id, "status": d.status, "latency_ms": d.latency_ms, "queue_ms": d.queue_ms,
+                    "service_ms": d.latency_ms - d.queue_ms, "device_start_ms": d.device_start_ms,
+                    "device_end_ms": d.device_end_ms, "message": d.message.decode(errors="replace"),
                     "result": d.result.as_dict()})
     return out
 

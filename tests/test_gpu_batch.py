@@ -114,3 +114,62 @@ def test_batch_argument_errors():
     with pytest.raises(jet.JetError) as ei:
         jet.jet_batch_refine(b, [(1, 1)], 8, [st])
     assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("shape", [(1, 256), (1, 1024), (2, 512), (4, 1024), (8, 256)])
+def test_persistent_batch_matches_oracle(shape):
+    """The persistent form (one kernel, teams of `shape` blocks x threads, a device work queue): every instance
+    equals the oracle's Algorithm 1 on it alone, also on a second launch of the cached graph."""
+    ctxs = _contexts()
+    states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST)]
+    b = jet.jet_batch_create(ctxs)
+    jet.jet_batch_set_team(b, *shape)
+    assert jet.jet_batch_get_team(b) == shape
+    for _ in range(2):
+        for st, (_, _, p) in zip(states, INST):
+            st.part.copy_(torch.as_tensor(p))
+        res = jet.jet_batch_refine(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states)
+        for i, (r, st) in enumerate(zip(res, states)):
+            _check(i, r, st)
+    b.close()
+
+
+def test_persistent_autotune_restores_partitions_and_picks_a_shape():
+    ctxs = _contexts()
+    states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST)]
+    b = jet.jet_batch_create(ctxs)
+    shapes = ((1, 256), (1, 1024), (2, 512))
+    chosen, trials = jet.jet_batch_autotune(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states, shapes,
+                                            sample=5, trial_iterations=3)
+    assert chosen in shapes and set(trials) == set(shapes)
+    assert all(ms > 0 and rate > 0 for ms, rate in trials.values())
+    for st, (hg, _, p) in zip(states, INST):
+        assert np.array_equal(st.part.cpu().numpy()[: hg.n], p)
+    res = jet.jet_batch_refine(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states)
+    for i, (r, st) in enumerate(zip(res, states)):
+        _check(i, r, st)
+    b.close()
+
+
+def test_persistent_batch_errors():
+    ctxs = _contexts()[:3]
+    states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST[:3])]
+    b = jet.jet_batch_create(ctxs)
+    for ctas, threads in ((3, 256), (1, 100), (1, 2048)):
+        with pytest.raises(jet.JetError) as ei:
+            jet.jet_batch_set_team(b, ctas, threads)
+        assert ei.value.code == -1
+    jet.jet_batch_set_team(b, 1, 256)
+    bad = INST[1][2].copy()
+    bad[7] = INST[1][1]  # block id k: outside [0, k)
+    states[1].part.copy_(torch.as_tensor(bad))
+    with pytest.raises(jet.JetError) as ei:
+        jet.jet_batch_refine(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states)
+    assert ei.value.code == -5 and "instance 1" in str(ei.value)
+    # the batch stays usable (the other instances were refined by the failed launch: start them over)
+    for st, (_, _, p) in zip(states, INST[:3]):
+        st.part.copy_(torch.as_tensor(p))
+    res = jet.jet_batch_refine(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states)
+    for i, (r, st) in enumerate(zip(res, states)):
+        _check(i, r, st)
+    b.close()

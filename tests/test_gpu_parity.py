@@ -224,6 +224,24 @@ def test_host_buffer_entry_point():
     assert res["iterations"] == iters and res["objective"] == obj and np.array_equal(p, p_ref)
 
 
+@pytest.mark.parametrize("name", ["vlsi_k64", "heavy_k128"])
+def test_rounds_host_entry_point(name):
+    """jet_rounds_host (host buffers, a fixed number of iterations) equals the same iterations of the oracle."""
+    hg, k, part = INSTANCES[name]
+    p = part.copy()
+    st = jet.jet_rounds_host(hg, jet.params(k), (3, 4), 3, p)
+    orc = oracle.Oracle(hg)
+    ost = oracle.State(orc, k, part)
+    for _ in range(3):
+        want = orc.refine_round(oracle.Params(k), (3, 4), ost.part, ost.phi, ost.bw, ost.locked)
+    assert np.array_equal(p, ost.part)
+    assert all(st[f] == want[f] for f in ("candidates", "approved", "rebalance_rounds", "rebalance_moves",
+                                          "objective", "max_block_weight", "imbalanced")), (st, want)
+    with pytest.raises(jet.JetError) as ei:
+        jet.jet_rounds_host(hg, jet.params(k), (3, 4), -1, p)
+    assert ei.value.code == -1
+
+
 def test_errors_are_reported():
     hg, k, part, ctx = setup("random10k_k8")
     st = jet.JetState(ctx, part)

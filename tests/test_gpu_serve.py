@@ -56,6 +56,15 @@ def test_jobs_match_alone_and_oracle():
         assert np.array_equal(alone[i], p), f"job {i}: alone run differs from the oracle"
         assert dm[i]["result"]["iterations"] == iters and dm[i]["result"]["objective"] == obj
         assert dm[i]["latency_ms"] >= dm[i]["queue_ms"] >= 0
+        assert dm[i]["message"] == ""
+        assert 0 <= dm[i]["device_start_ms"] <= dm[i]["device_end_ms"]
+    # continuous batching: jobs admitted together had work in flight on the GPU at the same time
+    spans = sorted((d["device_start_ms"], d["device_end_ms"]) for d in dm.values())
+    overlaps = sum(1 for (a0, a1), (b0, b1) in zip(spans, spans[1:]) if b0 < a1)
+    assert overlaps >= 1, f"no two jobs overlapped on the device: {spans}"
+    # one slot: the jobs ran one after another
+    spans = sorted((d["device_start_ms"], d["device_end_ms"]) for d in da.values())
+    assert all(b0 >= a1 for (a0, a1), (b0, b1) in zip(spans, spans[1:])), spans
 
 
 def test_submit_errors():
@@ -69,3 +78,22 @@ def test_submit_errors():
     assert ei.value.code == -2
     assert jet.jet_server_load(server) == {"pending": 0, "running": 0, "reserved_bytes": 0}
     server.close()
+
+
+def test_failed_job_reports_its_reason():
+    """A job whose partition holds a block id outside [0, k) fails with JET_ERR_DATA, and its report carries the
+    reason; the jobs around it are unaffected."""
+    server = jet.jet_server_create(1 << 34, 2)
+    parts = [p.copy() for _, _, p in JOBS[:3]]
+    parts[1][5] = JOBS[1][1]  # block id k: out of range
+    ids = {jet.jet_server_submit(server, h, jet.params(k), oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, parts[i]): i
+           for i, (h, k, _) in enumerate(JOBS[:3])}
+    done = []
+    while len(done) < 3:
+        done += jet.jet_server_wait(server, timeout_ms=10_000)
+    server.close()
+    by = {ids[d["id"]]: d for d in done}
+    assert by[1]["status"] == -5 and "partition" in by[1]["message"], by[1]
+    for i in (0, 2):
+        assert by[i]["status"] == 0 and by[i]["message"] == ""
+        assert np.array_equal(parts[i], EXPECTED[i][2])

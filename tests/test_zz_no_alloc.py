@@ -48,6 +48,9 @@ def test_noalloc_matches_context_path_on_two_calls(k):
         rc = _noalloc(lib, part, vwgt, k, bw, cnt)
         assert rc == 0, jet.jet_last_error(None)
         assert np.array_equal(bw.cpu().numpy(), ref), f"call {call}"
+        # and against the definition c(V_i) = sum of c(v) over Pi(v) = i, computed on the host
+        want = np.bincount(part_np, weights=hg.vwgt.astype(np.float64), minlength=k).astype(np.int64)
+        assert np.array_equal(bw.cpu().numpy(), want), f"call {call}"
         assert np.array_equal(cnt.cpu().numpy(), np.bincount(part_np, minlength=k)), f"call {call}"
     ctx.close()
 
@@ -72,3 +75,20 @@ def test_noalloc_reports_bad_partition_then_recovers():
     assert _noalloc(lib, torch.from_numpy(bad).cuda(), vw, k, bw, None) == -5
     assert _noalloc(lib, torch.from_numpy(part_np).cuda(), vw, k, bw, None) == 0
     assert np.array_equal(bw.cpu().numpy(), np.bincount(part_np, minlength=k))
+
+
+def test_noalloc_reports_weight_below_one_then_recovers():
+    """c(v) >= 1 is required (jet_ctx_create rejects such inputs too): a zero weight is a data error."""
+    lib = jet.load_library()
+    n, k = 1000, 8
+    part_np = synth.part_hash(4, n, k)
+    vw_np = np.arange(n, dtype=np.int32) % 5 + 1
+    bad = vw_np.copy()
+    bad[77] = 0
+    part = torch.from_numpy(part_np).cuda()
+    bw = torch.zeros(k, dtype=torch.int64, device="cuda")
+    assert _noalloc(lib, part, torch.from_numpy(bad).cuda(), k, bw, None) == -5
+    assert "weight" in jet.jet_last_error(None)
+    assert _noalloc(lib, part, torch.from_numpy(vw_np).cuda(), k, bw, None) == 0
+    want = np.bincount(part_np, weights=vw_np.astype(np.float64), minlength=k).astype(np.int64)
+    assert np.array_equal(bw.cpu().numpy(), want)
