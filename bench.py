@@ -558,6 +558,45 @@ def run_batched(args, dev):
                       "k from {2, 8, 32}, unit weights, eps = 3/100, hash partitions"}
 
 
+def run_convergence_10k(args, dev):
+    """The plain configuration to convergence: random_10k (n 10,000, m 12,000, k 8), Algorithm 1 with the
+    schedule 3/4, 3/8, 0 and limit 8 as one graph launch (jet_refine), against the oracle's Algorithm 1 on the
+    same input (one host core); the partitions must be identical."""
+    import torch
+
+    import oracle
+    from paper_2504_12013_gb300 import jet
+    hg, k, part0 = synth.config_random_10k(args.seed)
+    stream = torch.cuda.current_stream(dev)
+    ctx = jet.jet_ctx_create(jet.DeviceHypergraph(hg, dev), jet.params(k), stream)
+    st = jet.JetState(ctx, part0)
+    jet.jet_refine(ctx, SCHEDULE, LIMIT, st.part, st.phi, st.block_w)  # warm-up: graph capture
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(5):
+        st.part.copy_(torch.as_tensor(part0))
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        res = jet.jet_refine(ctx, SCHEDULE, LIMIT, st.part, st.phi, st.block_w)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(ev0.elapsed_time(ev1))
+    gpu_part = st.part.cpu().numpy()[: hg.n].copy()
+    ctx.close()
+    p = part0.copy()
+    t0 = time.perf_counter()
+    iters, obj, _ = oracle.Oracle(hg).refine(oracle.Params(k), p)
+    osec = time.perf_counter() - t0
+    return {"ms": sorted(times)[len(times) // 2], "iterations": res["iterations"], "objective": res["objective"],
+            "initial_objective": res["initial_objective"], "pins": hg.P,
+            "pin_iterations_per_s": hg.P * res["iterations"] / (sorted(times)[len(times) // 2] / 1e3),
+            "oracle_seconds": osec, "oracle_iterations": iters, "oracle_objective": obj,
+            "identical_to_oracle": bool(iters == res["iterations"] and obj == res["objective"]
+                                        and np.array_equal(gpu_part, p)),
+            "what": "random_10k to convergence (jet_refine, one graph launch, median of 5) and the oracle's "
+                    "Algorithm 1 on one host core"}
+
+
 def run_multilevel(args, hg, k, dev, coarsen_only=False, graph_path=False):
     """The multilevel pass of the paper (Sections 6 and 7.2) on the workload: deterministic coarsening on the
     GPU (jet_cluster + jet_contract per level; c_max = ceil(c(V) / (160 k)), until at most 160 k vertices
@@ -954,9 +993,12 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-multilevel", action="store_true")
+    ap.add_argument("--no-convergence", action="store_true", help="skip the random_10k convergence object")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--graph-only", action="store_true",
                     help="time only the graph workload on both paths (with --eager: kernel by kernel) and print its line")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="time only the batched workload (branch graph, persistent kernel, plain launches)")
     ap.add_argument("--coarsen-only", action="store_true",
                     help="time only the GPU coarsening of the workload (Section 6) and print its JSON line")
     ap.add_argument("--eager", action="store_true",
@@ -972,6 +1014,8 @@ def main():
         return run_coarsen_only(args, rank)
     if args.graph_only:
         return run_graph_only(args, rank)
+    if args.batched_only:
+        return run_batched_only(args, rank)
 
     if world > 1:
         import torch
@@ -990,6 +1034,7 @@ def main():
     batched = None if args.no_batched else run_batched(args, r["dev"])
     served = None if args.no_served else run_served(args, r["dev"])
     multilevel = None if args.no_multilevel else run_multilevel(args, hg, k, r["dev"])
+    conv10k = None if args.no_convergence else run_convergence_10k(args, r["dev"])
     graph = None if args.no_graph else run_graph(args, r["dev"])
     cpu = None if args.no_cpu_baseline else cpu_baseline(hg, k, r["part0"], args.cpu_budget)
 
@@ -1040,6 +1085,7 @@ def main():
         "multilevel": multilevel,
         "graph": graph,
         "vlsi_2m": second,
+        "random_10k_convergence": conv10k,
         "matching_schedule": r["schedule"],
         "trace_first_steps": r["trace"][:3],
     }
@@ -1063,6 +1109,17 @@ def run_coarsen_only(args, rank):
     print(json.dumps({"metric": "coarsening pins/s (all levels)", "value": c["pins_per_s"], "unit": "pins/s",
                       "config": {"workload": desc, "n": hg.n, "m": hg.m, "pins": hg.P, "k": k},
                       "coarsening": c}), flush=True)
+
+
+def run_batched_only(args, rank):
+    """The batched workload alone (for profiling and tuning)."""
+    import torch
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    b = run_batched(args, dev)
+    print(json.dumps({"metric": b["metric"], "value": b["value"], "unit": "pins/s", "batched": b}), flush=True)
 
 
 def run_graph_only(args, rank):

@@ -421,7 +421,7 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
       int vb = 1;
       while (vb < 31 && (1ll << vb) < (long long)c->n) ++vb;  // vertex ids need vb bits
       c->rb_vbits = vb;
-      // fewest levels of <= 16 bits, but histograms (k rows of 2^digit) no larger than max(4n, 2048k) bins
+      // fewest levels of <= kRbMaxDigit bits, histograms (k rows of 2^digit) no larger than max(4n, 2048k) bins
       const int tb = c->rb_hbits + c->rb_vbits;
       int levels = (tb + kRbMaxDigit - 1) / kRbMaxDigit;
       int digit = (tb + levels - 1) / levels;

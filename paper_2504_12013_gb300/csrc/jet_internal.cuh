@@ -90,7 +90,7 @@ struct RefineState {
   jet_refine_result res;  // the summary returned to the caller
 };
 
-constexpr int kRbMaxDigit = 16;  // widest radix-select digit (bins per block row <= 65536)
+constexpr int kRbMaxDigit = 11;  // widest radix-select digit (bins per block row <= 2048)
 
 }  // namespace jet
 

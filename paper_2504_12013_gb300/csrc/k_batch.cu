@@ -16,8 +16,8 @@
 // jet_refine on it alone.
 //
 // Memory written by one block of a team and read by another is read with
-// ld.global.cg (L2, not the non-coherent L1) and published by a fence before
-// each team barrier.  The state of an instance lives in its context's
+// ld.global.cg (L2, not the non-coherent L1), ordered by the release/acquire
+// cluster barrier.  The state of an instance lives in its context's
 // workspace and the caller's part/phi/block_w arrays; the kernel allocates
 // nothing.
 #include <algorithm>
@@ -103,10 +103,11 @@ __device__ __forceinline__ T ldm(const T *p) {
   else return *p;
 }
 
+// The team barrier.  For a cluster, arrive has release and wait has acquire semantics at cluster scope, which
+// orders every thread's earlier global and shared writes before the other blocks' later reads.
 template <bool MULTI>
 __device__ __forceinline__ void team_sync() {
   if constexpr (MULTI) {
-    __threadfence();
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
   } else {

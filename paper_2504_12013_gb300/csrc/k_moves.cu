@@ -98,8 +98,9 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 // block with a valid target has a record with the key
 // K(v) = hi(v) << vb | v  (priority descending, then id ascending, as one
 // ascending number of hb + vb bits; 64-bit when it fits, else 128-bit).
-// Per level (rb_digit <= 16 bits, from the top; two levels cover keys of up
-// to 32 bits) a grid-wide pass adds c(v) of every record that matches its
+// Per level (rb_digit <= kRbMaxDigit = 11 bits, from the top, so a pick scans
+// at most 2048 bins per block; three levels cover keys of up to 33 bits) a
+// grid-wide pass adds c(v) of every record that matches its
 // block's fixed prefix into the (block, digit) histogram -- for the first
 // level the target kernels do this while they write the records -- and one
 // small kernel per overloaded block picks the digit at which the cumulative
