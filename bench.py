@@ -932,7 +932,7 @@ def roofline_block(args, r, hbm, peak_src):
     fam_roof = {"rebalance_targets": family_roofline("rebalance_targets",
                                                      "rebalancing targets (k_rbcand_light/k_rbcand_heavy)",
                                                      r["rb_bytes"], "k_rbcand_light"),
-                "apply": family_roofline("apply", "apply moves (k_apply, k_rb_apply, k_apply_edges)",
+                "apply": family_roofline("apply", "apply moves (k_apply, k_rb_apply)",
                                          r["apply_bytes"], "k_apply")}
     dom_kernel = max(fam_roof, key=lambda f: prof[f]["ms"])  # the kernel with the most device time per step
     launches = sum(v["launches"] for v in prof.values())
