@@ -483,15 +483,17 @@ def run_batched(args, dev):
     same_team = same_team and all(np.array_equal(st.part[: h.n].cpu().numpy(), pb)
                                   for st, (h, _, _), pb in zip(states, insts, parts_batch))
     persistent = {"value": pin_rounds / (ms_team / 1e3), "unit": "pins/s", "ms_per_step": ms_team,
-                  "team": {"blocks": shape[0], "threads": shape[1]},
+                  "team": {"blocks": shape[0], "threads": shape[1], "split_pins": shape[2]},
                   "autotuner": {"sample_instances": args.tune_sample, "trial_iterations": args.tune_iterations,
                                 "seconds": tune_s,
-                                "trials": [{"blocks": c, "threads": t, "ms": ms, "pin_iterations_per_s": rate}
-                                           for (c, t), (ms, rate) in trials.items()]},
+                                "trials": [{"blocks": c, "threads": t, "split_pins": sp, "ms": ms,
+                                            "pin_iterations_per_s": rate}
+                                           for (c, t, sp), (ms, rate) in trials.items()]},
                   "results_identical_to_branch_graph": bool(same_team),
                   "how": "jet_batch_refine with jet_batch_set_team: ONE persistent kernel in a CUDA graph; teams "
                          "(thread-block clusters) take instances from a device queue, largest first, and run all "
-                         "of Algorithm 1 with cluster barriers between phases"}
+                         "of Algorithm 1 with cluster barriers between phases; below split_pins pins every block "
+                         "of a cluster takes instances on its own"}
     jet.jet_batch_set_team(b, 0)
     b.close()
 

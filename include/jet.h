@@ -267,31 +267,34 @@ int jet_batch_tune(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, in
 
 /*
  * Persistent form of a batch (the north star's "one persistent launch"):
- * jet_batch_set_team(batch, ctas, threads) with ctas in {1, 2, 4, 8} and
- * threads a multiple of 32 in [128, 1024] makes jet_batch_refine run ONE
- * persistent kernel (captured in a CUDA graph with the reset of its work
+ * jet_batch_set_team(batch, ctas, threads, split_pins) with ctas in {1, 2, 4,
+ * 8} and threads a multiple of 32 in [128, 1024] makes jet_batch_refine run
+ * ONE persistent kernel (captured in a CUDA graph with the reset of its work
  * queue and the copy of the summaries): teams of `ctas` thread blocks (a
  * thread-block cluster when ctas > 1) of `threads` threads each take the next
  * instance from a device work queue (instances grouped by ceil(k/32), largest
  * first) and run all of Algorithm 1 on it, with the team's barrier between
- * phases, so every instance advances at its own pace.  ctas = 0 returns to
- * the branch-graph form.  Results are identical to jet_refine on each
- * instance alone.  Every context must be on the hypergraph path
- * (JET_ERR_INVALID_ARG otherwise); a partition value outside [0, k) is
- * JET_ERR_DATA for that instance (naming it in jet_batch_last_error), and
- * that instance is not refined.
+ * phases, so every instance advances at its own pace.  With ctas > 1 and
+ * split_pins > 0, once the queue reaches instances of fewer than split_pins
+ * pins, each block of a cluster takes instances on its own (small instances
+ * are bound by barrier latency, which a single block pays least).  ctas = 0
+ * returns to the branch-graph form.  Results are identical to jet_refine on
+ * each instance alone, whatever the shape.  Every context must be on the
+ * hypergraph path (JET_ERR_INVALID_ARG otherwise); a partition value outside
+ * [0, k) is JET_ERR_DATA for that instance (naming it in
+ * jet_batch_last_error), and that instance is not refined.
  *
  * jet_batch_autotune chooses the team shape: for each of the n_shapes
- * (ctas, threads) pairs of `shapes` (HOST) it runs the persistent kernel on
- * `sample` instances spread over the sizes of the batch, each stopped after
- * trial_iterations Jet iterations, from the same partitions (restored before
- * each trial and at the end), and keeps the shape with the most
- * (pins x iterations) per second; ms_out and rate_out (HOST, n_shapes
- * entries, may be NULL) receive each trial's device time and rate.  The
- * arguments are those of jet_batch_refine.  Synchronizes.
+ * (ctas, threads, split_pins) triples of `shapes` (HOST) it runs the
+ * persistent kernel on `sample` instances spread over the sizes of the batch,
+ * each stopped after trial_iterations Jet iterations, from the same
+ * partitions (restored before each trial and at the end), and keeps the
+ * shape with the most (pins x iterations) per second; ms_out and rate_out
+ * (HOST, n_shapes entries, may be NULL) receive each trial's device time and
+ * rate.  The arguments are those of jet_batch_refine.  Synchronizes.
  */
-int jet_batch_set_team(jet_batch *batch, int32_t ctas, int32_t threads);
-int jet_batch_get_team(const jet_batch *batch, int32_t *ctas, int32_t *threads);
+int jet_batch_set_team(jet_batch *batch, int32_t ctas, int32_t threads, int32_t split_pins);
+int jet_batch_get_team(const jet_batch *batch, int32_t *ctas, int32_t *threads, int32_t *split_pins);
 int jet_batch_autotune(jet_batch *batch, const int32_t *tau_pairs, int32_t n_tau, int32_t limit, int32_t *const *part,
                        int32_t *const *phi, int64_t *const *block_w, const int32_t *shapes, int32_t n_shapes,
                        int32_t sample, int32_t trial_iterations, float *ms_out, double *rate_out);

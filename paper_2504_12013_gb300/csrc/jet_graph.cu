@@ -259,12 +259,13 @@ struct jet_batch {
   // persistent form (team_ctas > 0): one kernel whose teams of team_ctas blocks of team_threads threads each
   // refine one instance at a time from a device queue
   int team_ctas = 0, team_threads = 0;
+  int32_t team_split = 0;  // instances of fewer pins run on single blocks of a cluster
   jet::TeamPlan *plan = nullptr;
   std::vector<const void *> plan_args;  // part, phi, block_w of every instance, the schedule and the limit the
   std::vector<int32_t> plan_tau;        // plan and its graph were built for
   int32_t plan_limit = 0;
   cudaGraphExec_t team_exec = nullptr;
-  int team_exec_ctas = 0, team_exec_threads = 0;
+  int team_exec_ctas = 0, team_exec_threads = 0, team_exec_split = -1;
   char err[256] = {0};
 };
 
@@ -397,13 +398,15 @@ int ensure_plan(jet_batch *b, const int32_t *tau, int32_t n_tau, int32_t limit, 
 // The persistent form: one graph (queue reset, the persistent launches, the summaries to the host), launched on
 // b->stream; waits and reports.
 int run_team(jet_batch *b, int32_t limit, jet_refine_result *results) {
-  if (!b->team_exec || b->team_exec_ctas != b->team_ctas || b->team_exec_threads != b->team_threads) {
+  if (!b->team_exec || b->team_exec_ctas != b->team_ctas || b->team_exec_threads != b->team_threads ||
+      b->team_exec_split != b->team_split) {
     if (b->team_exec) cudaGraphExecDestroy(b->team_exec);
     b->team_exec = nullptr;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      cudaError_t ec = jet::team_launch(b->plan, b->team_ctas, b->team_threads, limit, 0, b->origin, nullptr, 0);
+      cudaError_t ec =
+          jet::team_launch(b->plan, b->team_ctas, b->team_threads, b->team_split, limit, 0, b->origin, nullptr, 0);
       if (ec == cudaSuccess) ec = jet::team_results(b->plan, b->res_host, b->origin);
       e = cudaStreamEndCapture(b->origin, &g);
       if (ec != cudaSuccess) e = ec;
@@ -416,6 +419,7 @@ int run_team(jet_batch *b, int32_t limit, jet_refine_result *results) {
     }
     b->team_exec_ctas = b->team_ctas;
     b->team_exec_threads = b->team_threads;
+    b->team_exec_split = b->team_split;
   }
   cudaError_t e = cudaGraphLaunch(b->team_exec, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -503,12 +507,13 @@ int jet_batch_set_split(jet_batch *b, int32_t split) {
 
 int jet_batch_get_split(const jet_batch *b) { return b ? b->split : -1; }
 
-int jet_batch_set_team(jet_batch *b, int32_t ctas, int32_t threads) {
+int jet_batch_set_team(jet_batch *b, int32_t ctas, int32_t threads, int32_t split_pins) {
   if (!b) return bfail(nullptr, JET_ERR_INVALID_ARG, "batch is NULL");
   if (ctas == 0) {
-    b->team_ctas = b->team_threads = 0;
+    b->team_ctas = b->team_threads = b->team_split = 0;
     return JET_OK;
   }
+  if (split_pins < 0) return bfail(b, JET_ERR_INVALID_ARG, "split_pins must be >= 0");
   if (!(ctas == 1 || ctas == 2 || ctas == 4 || ctas == 8))
     return bfail(b, JET_ERR_INVALID_ARG, "team blocks must be 1, 2, 4 or 8");
   if (threads < 128 || threads > 1024 || threads % 32)
@@ -517,13 +522,15 @@ int jet_batch_set_team(jet_batch *b, int32_t ctas, int32_t threads) {
     if (c->graph_path) return bfail(b, JET_ERR_INVALID_ARG, "the persistent form needs every instance on the hypergraph path");
   b->team_ctas = ctas;
   b->team_threads = threads;
+  b->team_split = split_pins;
   return JET_OK;
 }
 
-int jet_batch_get_team(const jet_batch *b, int32_t *ctas, int32_t *threads) {
-  if (!b || !ctas || !threads) return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL argument");
+int jet_batch_get_team(const jet_batch *b, int32_t *ctas, int32_t *threads, int32_t *split_pins) {
+  if (!b || !ctas || !threads || !split_pins) return bfail(nullptr, JET_ERR_INVALID_ARG, "NULL argument");
   *ctas = b->team_ctas;
   *threads = b->team_threads;
+  *split_pins = b->team_split;
   return JET_OK;
 }
 
@@ -535,9 +542,10 @@ int jet_batch_autotune(jet_batch *b, const int32_t *tau_pairs, int32_t n_tau, in
   if (n_shapes < 1 || !shapes) return bfail(b, JET_ERR_INVALID_ARG, "no team shapes to try");
   if (sample < 1 || trial_iterations < 1) return bfail(b, JET_ERR_INVALID_ARG, "sample and trial_iterations must be >= 1");
   for (int i = 0; i < n_shapes; ++i) {
-    const int c = shapes[2 * i], t = shapes[2 * i + 1];
-    if (!(c == 1 || c == 2 || c == 4 || c == 8) || t < 128 || t > 1024 || t % 32)
-      return bfail(b, JET_ERR_INVALID_ARG, "a team shape is outside {1,2,4,8} x [128, 1024] (multiples of 32)");
+    const int c = shapes[3 * i], t = shapes[3 * i + 1];
+    if (!(c == 1 || c == 2 || c == 4 || c == 8) || t < 128 || t > 1024 || t % 32 || shapes[3 * i + 2] < 0)
+      return bfail(b, JET_ERR_INVALID_ARG,
+                   "a team shape is outside {1,2,4,8} x [128, 1024] (multiples of 32) x [0, 2^31)");
   }
   if ((rc = ensure_plan(b, tau_pairs, n_tau, limit, part, phi, block_w))) return rc;
   const std::vector<int32_t> smp = jet::team_sample(b->plan, sample);
@@ -568,8 +576,8 @@ int jet_batch_autotune(jet_batch *b, const int32_t *tau_pairs, int32_t n_tau, in
       restore();
       if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
       if (e == cudaSuccess)
-        e = jet::team_launch(b->plan, shapes[2 * t], shapes[2 * t + 1], limit, trial_iterations, b->stream,
-                             smp.data(), (int32_t)smp.size());
+        e = jet::team_launch(b->plan, shapes[3 * t], shapes[3 * t + 1], shapes[3 * t + 2], limit, trial_iterations,
+                             b->stream, smp.data(), (int32_t)smp.size());
       if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
       if (e == cudaSuccess) e = jet::team_results(b->plan, res.data(), b->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -593,8 +601,9 @@ int jet_batch_autotune(jet_batch *b, const int32_t *tau_pairs, int32_t n_tau, in
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);
   if (e != cudaSuccess) return bfail(b, JET_ERR_CUDA, "persistent batch tuning", e);
-  b->team_ctas = shapes[2 * best];
-  b->team_threads = shapes[2 * best + 1];
+  b->team_ctas = shapes[3 * best];
+  b->team_threads = shapes[3 * best + 1];
+  b->team_split = shapes[3 * best + 2];
   return JET_OK;
 }
 

@@ -289,8 +289,8 @@ struct TeamPlan;  // device descriptors of a batch's instances, their queue orde
 int team_plan_build(TeamPlan **out, jet_ctx *const *ctxs, int32_t count, int32_t *const *part, int32_t *const *phi,
                     int64_t *const *block_w, const int32_t *tau_pairs, int32_t n_tau, cudaStream_t s);
 void team_plan_destroy(TeamPlan *p, cudaStream_t s);
-cudaError_t team_launch(TeamPlan *p, int ctas, int threads, int32_t limit, int32_t iter_cap, cudaStream_t s,
-                        const int32_t *sub_order, int32_t n_sub);
+cudaError_t team_launch(TeamPlan *p, int ctas, int threads, long long split_pins, int32_t limit, int32_t iter_cap,
+                        cudaStream_t s, const int32_t *sub_order, int32_t n_sub);
 cudaError_t team_results(TeamPlan *p, jet_refine_result *dst, cudaStream_t s);
 int team_first_error(TeamPlan *p, cudaStream_t s);
 std::vector<int32_t> team_sample(TeamPlan *p, int32_t n);

@@ -86,6 +86,7 @@ struct TeamArgs {
   const int32_t *tau;     // schedule pairs
   int32_t n_tau, limit;
   int32_t iter_cap;       // > 0: stop each instance after this many iterations (autotuner trials)
+  long long split_pins;   // multi-block teams: instances with fewer pins run on single blocks of the cluster
 };
 
 struct Team {
@@ -216,7 +217,8 @@ __device__ void team_objective(const TeamInst &I, const Team &tm, long long *s_r
 }
 
 // ------------------------------------------------------------ gains (Section 4.1, 4.3)
-// Bit planes of conn(v, .) over I(v), the union of Lambda(e), and A(v) for a light vertex in block s.
+// Bit planes of conn(v, .) over I(v), the union of Lambda(e), and A(v) for a light vertex in block s.  The
+// incidences go four at a time: their edge ids, then their bitmask rows and weights, are loaded together.
 template <bool MULTI, int KWP>
 __device__ __forceinline__ int32_t light_planes(const TeamInst &I, int v, int s, uint32_t (&pl)[kLightPlanes][KWP],
                                                 uint32_t (&any)[KWP]) {
@@ -227,17 +229,33 @@ __device__ __forceinline__ int32_t light_planes(const TeamInst &I, int v, int s,
     for (int p = 0; p < kLightPlanes; ++p) pl[p][q] = 0;
   }
   int32_t A = 0;
-  const int64_t j1 = I.vptr[v + 1];
-  for (int64_t j = I.vptr[v]; j < j1; ++j) {
-    const int e = I.inc[j];
-    const int w = I.unit_ewgt ? 1 : I.ewgt[e];
-    uint32_t M[KWP], M2[KWP];
-    load_rows_m<MULTI, KWP>(I.mask + (int64_t)e * 2 * KWP, M, M2);
-    if (mask_bit<KWP>(M2, s)) A += w;  // phi_e[s] >= 2
+  const int64_t j0 = I.vptr[v], j1 = I.vptr[v + 1];
+  for (int64_t jb = j0; jb < j1; jb += 4) {
+    int e[4];
 #pragma unroll
-    for (int q = 0; q < KWP; ++q) any[q] |= M[q];
-    if (I.unit_ewgt) add_one<KWP, kLightPlanes>(pl, M);
-    else add_weighted<KWP, kLightPlanes>(pl, M, (uint32_t)w);
+    for (int u = 0; u < 4; ++u) e[u] = jb + u < j1 ? I.inc[jb + u] : -1;
+    uint32_t M[4][KWP], M2[4][KWP];
+    int w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (e[u] >= 0) {
+        load_rows_m<MULTI, KWP>(I.mask + (int64_t)e[u] * 2 * KWP, M[u], M2[u]);
+        w[u] = I.unit_ewgt ? 1 : I.ewgt[e[u]];
+      } else {
+#pragma unroll
+        for (int q = 0; q < KWP; ++q) M[u][q] = M2[u][q] = 0u;
+        w[u] = 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (e[u] < 0) continue;
+      if (mask_bit<KWP>(M2[u], s)) A += w[u];  // phi_e[s] >= 2
+#pragma unroll
+      for (int q = 0; q < KWP; ++q) any[q] |= M[u][q];
+      if (I.unit_ewgt) add_one<KWP, kLightPlanes>(pl, M[u]);
+      else add_weighted<KWP, kLightPlanes>(pl, M[u], (uint32_t)w[u]);
+    }
   }
   return A;
 }
@@ -286,11 +304,17 @@ __device__ __forceinline__ int32_t heavy_conn(const TeamInst &I, int v, int s, i
 template <bool MULTI, int KWP>
 __device__ void team_candidates(const TeamInst &I, const Team &tm, int32_t tn, int32_t td, long long *s_red) {
   long long cnt = 0;
+  // the next vertex's id, lock and block are loaded while the current one is evaluated
+  int nv = tm.tid < I.n_light ? I.v_light[tm.tid] : -1;
+  int nlk = nv >= 0 ? ldm<MULTI>(I.locked + nv) : 1, ns = nv >= 0 ? ldm<MULTI>(I.part + nv) : 0;
   for (long long i = tm.tid; i < I.n_light; i += tm.nthr) {
-    const int v = I.v_light[i];
+    const int v = nv, lk = nlk, sv = ns;
+    nv = i + tm.nthr < I.n_light ? I.v_light[i + tm.nthr] : -1;
+    nlk = nv >= 0 ? ldm<MULTI>(I.locked + nv) : 1;
+    ns = nv >= 0 ? ldm<MULTI>(I.part + nv) : 0;
     uint64_t rec = 0;
-    if (!ldm<MULTI>(I.locked + v)) {
-      const int s = ldm<MULTI>(I.part + v);
+    if (!lk) {
+      const int s = sv;
       uint32_t pl[kLightPlanes][KWP], any[KWP];
       const int32_t A = light_planes<MULTI, KWP>(I, v, s, pl, any);
       uint32_t C[KWP], nz = 0;
@@ -351,10 +375,38 @@ __device__ void team_candidates(const TeamInst &I, const Team &tm, int32_t tn, i
 // shared memory (only the entries of blocks the candidates touch are used).
 template <bool MULTI, int KWP>
 __device__ void team_afterburner(const TeamInst &I, const Team &tm, unsigned long long *s_tab) {
-  for (long long i = tm.tid; i < I.n_tiny; i += tm.nthr) {
-    const int e = I.e_tiny[i];
-    const int64_t p0 = I.eptr[e];
-    const int sz = (int)(I.eptr[e + 1] - p0);
+  // software pipeline over the thread's edges: while edge i is decided, the pins of edge i+1, the offsets
+  // of edge i+2 and the id of edge i+3 are in flight
+  auto edge_at = [&](long long i) -> int { return i < I.n_tiny ? I.e_tiny[i] : -1; };
+  const long long st0 = tm.tid, stride = tm.nthr;
+  int e3 = edge_at(st0 + 2 * stride);
+  int e2 = edge_at(st0 + stride);
+  int64_t p2 = e2 >= 0 ? I.eptr[e2] : 0;
+  int sz2 = e2 >= 0 ? (int)(I.eptr[e2 + 1] - p2) : 0;
+  int e1 = edge_at(st0), sz1 = 0;
+  int pins1[kTinyEdge];
+  {
+    const int64_t p1 = e1 >= 0 ? I.eptr[e1] : 0;
+    sz1 = e1 >= 0 ? (int)(I.eptr[e1 + 1] - p1) : 0;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q) pins1[q] = q < sz1 ? I.pins[p1 + q] : 0;
+  }
+  for (long long i = st0; i < I.n_tiny; i += stride) {
+    const int e = e1, sz = sz1;
+    int pin[kTinyEdge];
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q) pin[q] = pins1[q];
+    const int e4 = edge_at(i + 3 * stride);
+    const int64_t p3 = e3 >= 0 ? I.eptr[e3] : 0;
+    const int sz3 = e3 >= 0 ? (int)(I.eptr[e3 + 1] - p3) : 0;
+#pragma unroll
+    for (int q = 0; q < kTinyEdge; ++q) pins1[q] = q < sz2 ? I.pins[p2 + q] : 0;
+    e1 = e2;
+    sz1 = sz2;
+    e2 = e3;
+    p2 = p3;
+    sz2 = sz3;
+    e3 = e4;
     uint64_t key[kTinyEdge];
     uint32_t st[kTinyEdge];  // s | t << 8 | 1 << 16 for a candidate; block | 1 << 17 for another pin
     int nin = 0;
@@ -363,7 +415,7 @@ __device__ void team_afterburner(const TeamInst &I, const Team &tm, unsigned lon
       key[q] = 0;
       st[q] = 0;
       if (q < sz) {
-        const int v = I.pins[p0 + q];
+        const int v = pin[q];
         const uint64_t r = ldm<MULTI>(I.cand + v);
         if (r) {
           ++nin;
@@ -546,16 +598,21 @@ __device__ __forceinline__ void eligible_set(const long long *s_cap, int k, int3
 template <bool MULTI, int KWP>
 __device__ void team_targets(const TeamInst &I, const Team &tm, const long long *s_cap, const long long *s_bw,
                              const int *s_over, unsigned *s_wc, unsigned long long *s_base) {
+  // the next vertex's id, block and weight are loaded while the current one is evaluated
+  const long long i0 = (long long)tm.rank * blockDim.x + threadIdx.x;
+  int nv = i0 < I.n_light ? I.v_light[i0] : -1;
+  int ns = nv >= 0 ? ldm<MULTI>(I.part + nv) : 0;
+  int32_t nc = nv >= 0 ? I.vwgt[nv] : 0;
   for (long long base = (long long)tm.rank * blockDim.x; base < I.n_light; base += tm.nthr) {
     const long long i = base + threadIdx.x;
     bool rec = false;
-    int v = 0, s = 0, t = 0;
-    int32_t c = 0;
+    int v = nv, s = ns, t = 0;
+    int32_t c = nc;
     uint64_t hi = 0;
+    nv = i + tm.nthr < I.n_light ? I.v_light[i + tm.nthr] : -1;
+    ns = nv >= 0 ? ldm<MULTI>(I.part + nv) : 0;
+    nc = nv >= 0 ? I.vwgt[nv] : 0;
     if (i < I.n_light) {
-      v = I.v_light[i];
-      s = ldm<MULTI>(I.part + v);
-      c = I.vwgt[v];
       if (s_over[s] && 2ll * c <= 3ll * (s_bw[s] - I.A)) {
         uint32_t C[KWP], nz = 0;
         eligible_set<KWP>(s_cap, I.k, c, C);
@@ -878,16 +935,44 @@ __global__ void __launch_bounds__(kTeamMaxThreads) k_batch_teams(TeamArgs a, int
   tm.nwarps = tm.nthr >> 5;
   for (int b = threadIdx.x; b < kmax; b += blockDim.x) sm.s_dw[b] = 0;
   const long long team = blockIdx.x / tm.size;
+  int idx = -1;
   for (;;) {
     if (leader(tm)) {
       const unsigned q = atomicAdd(a.queue, 1u);
       a.team_inst[team] = q < (unsigned)a.count ? a.order[q] : -1;
     }
     team_sync<MULTI>();
-    const int idx = ldm<MULTI>(a.team_inst + team);
+    idx = ldm<MULTI>(a.team_inst + team);
     team_sync<MULTI>();  // every thread has the index before the leader overwrites the slot
-    if (idx < 0) break;
+    if (idx < 0) return;
+    if (MULTI && a.inst[idx].P < a.split_pins) break;  // the queue is largest first: the rest are smaller
     team_refine<MULTI, KWP>(a.inst[idx], tm, a, sm);
+  }
+  if constexpr (MULTI) {
+    // Split: from the first instance below split_pins on, every block of the cluster is a team of its
+    // own (no cluster barrier from here on).  Block 0 takes the instance the cluster just drew; every
+    // block then draws instances on its own until the queue is empty.
+    Team one;
+    one.rank = 0;
+    one.size = 1;
+    one.tid = threadIdx.x;
+    one.nthr = blockDim.x;
+    one.lane = threadIdx.x & 31;
+    one.wid = threadIdx.x >> 5;
+    one.nwarps = blockDim.x >> 5;
+    __shared__ int s_idx;
+    if (tm.rank == 0) team_refine<false, KWP>(a.inst[idx], one, a, sm);
+    for (;;) {
+      if (threadIdx.x == 0) {
+        const unsigned q = atomicAdd(a.queue, 1u);
+        s_idx = q < (unsigned)a.count ? a.order[q] : -1;
+      }
+      __syncthreads();
+      const int j = s_idx;
+      __syncthreads();
+      if (j < 0) return;
+      team_refine<false, KWP>(a.inst[j], one, a, sm);
+    }
   }
 }
 
@@ -1088,9 +1173,10 @@ void team_plan_destroy(TeamPlan *p, cudaStream_t s) {
 
 // The persistent launches of a plan (one per mask-width group), each over its group's instances (or over the
 // n_sub instances of sub_order, a HOST list of instances of the first group, for tuning trials).  iter_cap > 0
-// stops each instance after that many Jet iterations.  Results land in the plan's device summaries.
-cudaError_t team_launch(TeamPlan *p, int ctas, int threads, int32_t limit, int32_t iter_cap, cudaStream_t s,
-                        const int32_t *sub_order, int32_t n_sub) {
+// stops each instance after that many Jet iterations; with ctas > 1, instances of fewer than split_pins pins
+// run on single blocks.  Results land in the plan's device summaries.
+cudaError_t team_launch(TeamPlan *p, int ctas, int threads, long long split_pins, int32_t limit, int32_t iter_cap,
+                        cudaStream_t s, const int32_t *sub_order, int32_t n_sub) {
   const size_t ng = p->group_kwp.size();
   cudaError_t e = cudaMemsetAsync(p->queue, 0, sizeof(unsigned) * ng, s);
   if (e == cudaSuccess && sub_order) {
@@ -1110,6 +1196,7 @@ cudaError_t team_launch(TeamPlan *p, int ctas, int threads, int32_t limit, int32
     a.n_tau = p->n_tau;
     a.limit = limit;
     a.iter_cap = iter_cap;
+    a.split_pins = split_pins;
     const int kwp = sub_order ? p->group_kwp[0] : p->group_kwp[g];
     const int kmax = p->group_kmax[sub_order ? 0 : g];
     const int max_teams = std::min(p->team_slots, a.count);

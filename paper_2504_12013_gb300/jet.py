@@ -139,8 +139,8 @@ def load_library():
             lib.jet_batch_get_split.argtypes = [_P]
             lib.jet_batch_tune.argtypes = [_P, pp(i32), i32, i32, pp(_P), pp(_P), pp(_P), pp(i32), i32,
                                            pp(ctypes.c_float)]
-            lib.jet_batch_set_team.argtypes = [_P, i32, i32]
-            lib.jet_batch_get_team.argtypes = [_P, pp(i32), pp(i32)]
+            lib.jet_batch_set_team.argtypes = [_P, i32, i32, i32]
+            lib.jet_batch_get_team.argtypes = [_P, pp(i32), pp(i32), pp(i32)]
             lib.jet_batch_autotune.argtypes = [_P, pp(i32), i32, i32, pp(_P), pp(_P), pp(_P), pp(i32), i32, i32, i32,
                                                pp(ctypes.c_float), pp(ctypes.c_double)]
             sz = ctypes.c_size_t
@@ -536,31 +536,51 @@ def jet_batch_tune(batch: Batch, schedule, limit, states, splits) -> tuple:
     return jet_batch_get_split(batch), {int(s): float(t) for s, t in zip(splits, ms)}
 
 
-# team shapes (blocks per team, threads per block) the persistent form's autotuner tries by default
-TEAM_SHAPES = ((1, 256), (1, 512), (1, 1024), (2, 512), (2, 1024), (4, 1024), (8, 1024))
+# team shapes (blocks per team, threads per block) the persistent form's autotuner tries; multi-block shapes are
+# tried with no split and with splits at quantiles of the batch's instance sizes
+TEAM_SHAPES = ((1, 256), (1, 512), (1, 1024), (2, 1024), (4, 1024), (8, 1024))
+TEAM_SPLIT_QUANTILES = (0.25, 0.5, 0.75)
 
 
-def jet_batch_set_team(batch: Batch, ctas: int, threads: int = 1024):
-    """Persistent form with teams of `ctas` blocks of `threads` threads (ctas = 0: the branch-graph form)."""
-    _batch_check(load_library().jet_batch_set_team(batch.handle, int(ctas), int(threads)), batch)
+def jet_batch_set_team(batch: Batch, ctas: int, threads: int = 1024, split_pins: int = 0):
+    """Persistent form with teams of `ctas` blocks of `threads` threads; with ctas > 1, instances of fewer than
+    split_pins pins run on single blocks (ctas = 0: the branch-graph form)."""
+    _batch_check(load_library().jet_batch_set_team(batch.handle, int(ctas), int(threads), int(split_pins)), batch)
 
 
 def jet_batch_get_team(batch: Batch) -> tuple:
-    c, t = ctypes.c_int32(), ctypes.c_int32()
-    _batch_check(load_library().jet_batch_get_team(batch.handle, ctypes.byref(c), ctypes.byref(t)), batch)
-    return c.value, t.value
+    c, t, sp = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _batch_check(load_library().jet_batch_get_team(batch.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(sp)),
+                 batch)
+    return c.value, t.value, sp.value
 
 
-def jet_batch_autotune(batch: Batch, schedule, limit, states, shapes=TEAM_SHAPES, sample=24, trial_iterations=8):
-    """Choose the persistent form's team shape from short trials on a sample; returns (shape, {shape: (ms, rate)})."""
+def team_candidates(batch: Batch, shapes=TEAM_SHAPES, quantiles=TEAM_SPLIT_QUANTILES) -> list:
+    """(blocks, threads, split_pins) triples: every shape without a split, and the multi-block shapes of the
+    largest block size with splits at the given quantiles of the instances' pin counts."""
+    pins = sorted(int(c.hg.P) for c in batch.ctxs)
+    out = [(c, t, 0) for c, t in shapes]
+    big = max((s for s in shapes if s[0] > 1), default=None)
+    if big and pins:
+        for q in quantiles:
+            sp = pins[min(len(pins) - 1, int(q * len(pins)))]
+            if sp > 0 and (big[0], big[1], sp) not in out:
+                out.append((big[0], big[1], sp))
+    return out
+
+
+def jet_batch_autotune(batch: Batch, schedule, limit, states, shapes=None, sample=24, trial_iterations=8):
+    """Choose the persistent form's team shape from short trials on a sample; returns
+    ((blocks, threads, split_pins), {shape: (ms, rate)})."""
+    shapes = [tuple(s) if len(s) == 3 else (s[0], s[1], 0) for s in (shapes or team_candidates(batch))]
     part, phi, bw = _state_arrays(states)
-    sh = (ctypes.c_int32 * (2 * len(shapes)))(*[int(x) for p in shapes for x in p])
+    sh = (ctypes.c_int32 * (3 * len(shapes)))(*[int(x) for p in shapes for x in p])
     ms = (ctypes.c_float * len(shapes))()
     rate = (ctypes.c_double * len(shapes))()
     _batch_check(load_library().jet_batch_autotune(batch.handle, _pairs(schedule), len(schedule), int(limit), part, phi,
                                                    bw, sh, len(shapes), int(sample), int(trial_iterations), ms, rate),
                  batch)
-    return jet_batch_get_team(batch), {tuple(p): (float(m), float(r)) for p, m, r in zip(shapes, ms, rate)}
+    return jet_batch_get_team(batch), {p: (float(m), float(r)) for p, m, r in zip(shapes, ms, rate)}
 
 
 def jet_job_footprint(n, m, P, k) -> int:

@@ -116,10 +116,12 @@ def test_batch_argument_errors():
     assert ei.value.code == -1
 
 
-@pytest.mark.parametrize("shape", [(1, 256), (1, 1024), (2, 512), (4, 1024), (8, 256)])
+@pytest.mark.parametrize("shape", [(1, 256, 0), (1, 1024, 0), (2, 512, 0), (4, 1024, 0), (8, 256, 0),
+                                   (8, 256, 8_000), (4, 512, 60_000)])
 def test_persistent_batch_matches_oracle(shape):
-    """The persistent form (one kernel, teams of `shape` blocks x threads, a device work queue): every instance
-    equals the oracle's Algorithm 1 on it alone, also on a second launch of the cached graph."""
+    """The persistent form (one kernel, teams of `shape` blocks x threads, a device work queue; with a split,
+    instances below that many pins run on single blocks of a cluster): every instance equals the oracle's
+    Algorithm 1 on it alone, also on a second launch of the cached graph."""
     ctxs = _contexts()
     states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST)]
     b = jet.jet_batch_create(ctxs)
@@ -138,7 +140,7 @@ def test_persistent_autotune_restores_partitions_and_picks_a_shape():
     ctxs = _contexts()
     states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST)]
     b = jet.jet_batch_create(ctxs)
-    shapes = ((1, 256), (1, 1024), (2, 512))
+    shapes = ((1, 256, 0), (1, 1024, 0), (2, 512, 0), (2, 512, 10_000))
     chosen, trials = jet.jet_batch_autotune(b, oracle.TAU_SCHEDULE, oracle.ITERATION_LIMIT, states, shapes,
                                             sample=5, trial_iterations=3)
     assert chosen in shapes and set(trials) == set(shapes)
@@ -155,9 +157,9 @@ def test_persistent_batch_errors():
     ctxs = _contexts()[:3]
     states = [jet.JetState(c, p) for c, (_, _, p) in zip(ctxs, INST[:3])]
     b = jet.jet_batch_create(ctxs)
-    for ctas, threads in ((3, 256), (1, 100), (1, 2048)):
+    for ctas, threads, split in ((3, 256, 0), (1, 100, 0), (1, 2048, 0), (2, 256, -1)):
         with pytest.raises(jet.JetError) as ei:
-            jet.jet_batch_set_team(b, ctas, threads)
+            jet.jet_batch_set_team(b, ctas, threads, split)
         assert ei.value.code == -1
     jet.jet_batch_set_team(b, 1, 256)
     bad = INST[1][2].copy()
