@@ -386,7 +386,11 @@ int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p,
     c->max_wdeg = (int64_t)hscal[1];
     c->cmax = (int32_t)hscal[2];
     c->unit_ewgt = hscal[3] <= 1 ? 1 : 0;
-    if ((e = prepare_candidate_kernels(c)) != cudaSuccess) { rc = cuda_fail(c, e, "kernel set-up"); break; }
+    if ((e = prepare_candidate_kernels(c)) != cudaSuccess || (e = prepare_move_kernels(c)) != cudaSuccess ||
+        (e = prepare_afterburner_kernels(c)) != cudaSuccess) {
+      rc = cuda_fail(c, e, "kernel set-up");
+      break;
+    }
     if (c->max_wdeg >= (1ll << 31) - 1) {
       rc = fail(c, JET_ERR_OVERFLOW, "a sum of omega over I(v) (%lld) does not fit the int32 gains",
                 (long long)c->max_wdeg);

@@ -30,6 +30,7 @@ constexpr int kLightPlanes = 6;      // thread-per-vertex gain path: weighted de
 constexpr int kTinyEdge = 8;         // thread-per-edge afterburner: |e| <= 8
 constexpr int kWarpEdge = 128;       // warp-per-edge afterburner: 8 < |e| <= 128
 constexpr int kSegPins = 2048;       // block-class edges are cut into segments of at most this many pins
+constexpr int kHalfMidEdge = 16;     // warp-class edges of at most 16 pins: a half warp per edge
 constexpr int kSmallMidEdge = 32;    // warp-class edges of at most 32 pins: one pin per lane, pipelined
 constexpr int kPrioShift = 30;       // exact rebalancing priority encoding (needs c(v) <= 2^15)
 constexpr int kMaxVertexWeight = 32767;
@@ -112,6 +113,12 @@ struct jet_ctx {
   int32_t cmax = 0;
   int unit_ewgt = 0;  // every edge with pins has omega(e) = 1
   int stage_bps[2] = {1, 1};  // resident blocks per SM: staged candidate / rebalancing-target kernels
+  // resident blocks per SM of the grid-stride kernels, so that each grid is whole waves:
+  // k_apply, k_rb_apply (64-bit, 128-bit keys) | k_ab_tiny, k_ab_warp_small<16>, k_ab_warp_small<32>,
+  // k_ab_warp<4>, k_ab_block, k_ab_warp<2> | k_cand_heavy, k_rbcand_heavy
+  int move_bps[3] = {1, 1, 1};
+  int ab_bps[6] = {1, 1, 1, 1, 1, 1};
+  int heavy_bps[2] = {1, 1};
   // compact rebalancing keys: priority gain*c (gain >= 0) or gain*(L/c) (gain < 0), L = lcm(1..cmax),
   // stored as (Pmax - P) << 32 | v when max_wdeg*(cmax + L) < 2^32
   int rb_compact = 0;
@@ -122,8 +129,9 @@ struct jet_ctx {
   int32_t n_light = 0, n_heavy = 0;
   uint8_t *vheavy = nullptr;  // per vertex: 1 if heavy (weighted degree >= 2^kLightPlanes)
   // one array of m edge ids: [tiny by size | mid <= 32 pins | mid > 32 pins, largest first | big]
-  int32_t *e_tiny = nullptr, *e_mid_small = nullptr, *e_mid = nullptr, *e_big = nullptr;
-  int32_t n_tiny = 0, n_mid_small = 0, n_mid = 0, n_big = 0;
+  int32_t *e_tiny = nullptr, *e_mid_half = nullptr, *e_mid_small = nullptr, *e_mid = nullptr, *e_big = nullptr;
+  int32_t n_tiny = 0, n_mid_half = 0, n_mid_small = 0, n_mid = 0, n_big = 0;
+  int32_t n_mid_hi = 0;  // the first n_mid_hi edges of e_mid have 65..128 pins, the rest 33..64
   // block-class edges as segments (largest first): edge, first pin, pins, table slot (-1: the whole edge)
   int4 *ab_seg = nullptr;
   int32_t n_seg = 0;
@@ -237,10 +245,12 @@ cudaError_t launch_candidates(jet_ctx *c, int32_t tau_num, int32_t tau_den, cons
 cudaError_t launch_rebalance_candidates(jet_ctx *c, const int32_t *part, const int32_t *phi);
 // afterburner (k_ab.cu)
 cudaError_t prepare_afterburner(jet_ctx *c);
+cudaError_t prepare_afterburner_kernels(jet_ctx *c);  // ab_bps
 cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *phi);
 cudaError_t launch_approve(jet_ctx *c, uint8_t *locked, int32_t *rg_out, uint8_t *approved_out, bool build_moves);
 cudaError_t launch_export_candidates(jet_ctx *c, int32_t *target, int32_t *gain, uint8_t *in_m);
 // moves, rebalancing, loop control (k_moves.cu)
+cudaError_t prepare_move_kernels(jet_ctx *c);  // move_bps
 cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w);  // applies the move list
 cudaError_t launch_rb_check(jet_ctx *c, const int64_t *block_w, cudaGraphConditionalHandle cond = 0,
                             int use_cond = 0);
@@ -298,6 +308,16 @@ long long team_pins(TeamPlan *p, int32_t i);
 
 // Sets the message returned by jet_last_error(NULL) (for entry points without a context).
 void set_global_error(const char *fmt, ...);
+
+// Resident blocks per SM of `kernel` at this block size and dynamic shared
+// memory (at least 1), for grids sized in whole waves.
+template <class K>
+inline cudaError_t resident_blocks(K kernel, int threads, size_t smem, int *out) {
+  int b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem);
+  *out = b > 0 ? b : 1;
+  return e;
+}
 
 inline int grid_for(int64_t items, int per_block, int num_sms, int blocks_per_sm = 8) {
   int64_t g = (items + per_block - 1) / per_block;

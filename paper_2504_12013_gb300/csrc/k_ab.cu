@@ -22,10 +22,11 @@
 // (gathered from the partition), so the afterburner reads no phi entry.
 //
 // Size classes: |e| <= 8 one thread per edge (pairwise tests in registers);
-// 8 < |e| <= 128 one warp per edge (<= 32 pins: software-pipelined over the
-// warp's edges; larger: largest edges first) and > 128 one thread block per
-// segment of <= 2048 pins, each with a per-block max / min table and a
-// non-candidate bitmask in shared memory.
+// 8 < |e| <= 16 a half warp per edge and 16 < |e| <= 128 one warp per edge
+// (<= 32 pins: software-pipelined over the group's edges; larger: up to four
+// pins per lane in registers, largest edges first) and > 128 one thread block per segment of <= 2048 pins, each
+// with a per-block max / min table and a non-candidate bitmask in shared
+// memory.
 #include <algorithm>
 #include <vector>
 
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(256) k_ab_tiny(AbArgs a) {
 
 constexpr int kAbWarps = 8;
 
-// Warp per edge (32 < |e| <= 128): the per-block form of the replay in
+// Warp per edge (32 < |e| <= 32 PPL): the per-block form of the replay in
 // shared memory, one table per warp: max key of the departures and min key
 // of the arrivals of every block, and the blocks holding a non-candidate pin.
 // A key is never 0 (its high word is INT32_MAX - gain >= 1), so max = 0 means
@@ -146,7 +147,11 @@ constexpr int kAbWarps = 8;
 // words) of blocks some candidate of the edge leaves or enters are reset and
 // read, so the cost is O(|e|) and not O(k) per edge: pass 1 resets them,
 // pass 2 adds the departures, arrivals and non-candidate blocks, pass 3 lets
-// the last departure and the first arrival of each block decide.
+// the last departure and the first arrival of each block decide.  Each lane
+// holds PPL pins (their records and blocks) in registers for the three
+// passes, loaded together, and the next edge's offsets are loaded while the
+// current edge is decided.
+template <int PPL>
 __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
   extern __shared__ unsigned long long s_tab[];  // per warp: maxd[k], mina[k]
   __shared__ uint32_t s_nm[kAbWarps][kMaxK / 32];
@@ -156,49 +161,32 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
   uint32_t *nm = s_nm[w];
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  int en = gw < a.nlist ? a.elist[gw] : -1;
+  int64_t p0n = en >= 0 ? a.eptr[en] : 0, p1n = en >= 0 ? a.eptr[en + 1] : 0;
   for (int i = gw; i < a.nlist; i += nw) {
-    const int e = a.elist[i];
-    const int64_t p0 = a.eptr[e], p1 = a.eptr[e + 1];
-    if (p1 - p0 <= 32) {  // one pin per lane: the pin's data stays in registers for the three passes
-      const bool has = lane < p1 - p0;
-      const int v = has ? a.pins[p0 + lane] : 0;
-      const uint64_t r = has ? a.cand[v] : 0ull;
-      const int b = (has && !r) ? (a.part[v] & 255) : -1;
-      const int s = cand_s(r), t = cand_t(r);
-      if (r) {
-        maxd[s] = 0ull;
-        mina[s] = ~0ull;
-        maxd[t] = 0ull;
-        mina[t] = ~0ull;
-        nm[s >> 5] = 0u;
-        nm[t >> 5] = 0u;
-      }
-      if (!__any_sync(kFull, r != 0)) continue;
-      __syncwarp();
-      const uint64_t K = cand_key(r, v);
-      if (r) {
-        atomicMax(&maxd[s], (unsigned long long)K);
-        atomicMin(&mina[t], (unsigned long long)K);
-      } else if (b >= 0) {
-        atomicOr(&nm[b >> 5], 1u << (b & 31));
-      }
-      __syncwarp();
-      if (r) {
-        const int wt = a.ewgt[e];
-        int delta = 0;
-        if (maxd[s] == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina[s] == ~0ull || K < mina[s])) delta += wt;
-        if (mina[t] == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd[t] < K) delta -= wt;
-        if (delta) atomicAdd(&a.rg[v], delta);
-      }
-      __syncwarp();
-      continue;
+    const int e = en;
+    const int64_t p0 = p0n, p1 = p1n;
+    en = i + nw < a.nlist ? a.elist[i + nw] : -1;  // first used in the next iteration
+    if (en >= 0) {
+      p0n = a.eptr[en];
+      p1n = a.eptr[en + 1];
     }
+    int v[PPL], b[PPL];
+    uint64_t r[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+      const int64_t p = p0 + lane + 32 * q;
+      v[q] = p < p1 ? a.pins[p] : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) r[q] = v[q] >= 0 ? a.cand[v[q]] : 0ull;
     bool any = false;
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
-      const uint64_t r = a.cand[a.pins[p]];
-      if (r) {
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+      b[q] = (v[q] >= 0 && !r[q]) ? (a.part[v[q]] & 255) : -1;  // block of a non-candidate pin
+      if (r[q]) {
         any = true;
-        const int s = cand_s(r), t = cand_t(r);
+        const int s = cand_s(r[q]), t = cand_t(r[q]);
         maxd[s] = 0ull;
         mina[s] = ~0ull;
         maxd[t] = 0ull;
@@ -209,52 +197,53 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
     }
     if (!__any_sync(kFull, any)) continue;
     __syncwarp();
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
-      const int v = a.pins[p];
-      const uint64_t r = a.cand[v];
-      if (r) {
-        const uint64_t K = cand_key(r, v);
-        atomicMax(&maxd[cand_s(r)], (unsigned long long)K);
-        atomicMin(&mina[cand_t(r)], (unsigned long long)K);
-      } else {
-        const int b = a.part[v] & 255;
-        atomicOr(&nm[b >> 5], 1u << (b & 31));
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+      if (r[q]) {
+        const uint64_t K = cand_key(r[q], v[q]);
+        atomicMax(&maxd[cand_s(r[q])], (unsigned long long)K);
+        atomicMin(&mina[cand_t(r[q])], (unsigned long long)K);
+      } else if (b[q] >= 0) {
+        atomicOr(&nm[b[q] >> 5], 1u << (b[q] & 31));
       }
     }
     __syncwarp();
     const int wt = a.ewgt[e];
-    for (int64_t p = p0 + lane; p < p1; p += 32) {
-      const int v = a.pins[p];
-      const uint64_t r = a.cand[v];
-      if (!r) continue;
-      const uint64_t K = cand_key(r, v);
-      const int s = cand_s(r), t = cand_t(r);
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+      if (!r[q]) continue;
+      const uint64_t K = cand_key(r[q], v[q]);
+      const int s = cand_s(r[q]), t = cand_t(r[q]);
       int delta = 0;
       // last departure from s, no arrival to s before it, no pin of e staying in s
       if (maxd[s] == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina[s] == ~0ull || K < mina[s])) delta += wt;
       // first arrival to t, every departure from t before it, no pin of e staying in t
       if (mina[t] == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd[t] < K) delta -= wt;
-      if (delta) atomicAdd(&a.rg[v], delta);
+      if (delta) atomicAdd(&a.rg[v[q]], delta);
     }
     __syncwarp();
   }
 }
 
-// Warp per edge for 8 < |e| <= 32 (one pin per lane), software-pipelined
-// over the warp's edges: while edge j is evaluated, the candidate records and
-// blocks of edge j+1, the pins of edge j+2, the offsets of edge j+3 and the
-// id of edge j+4 are in flight, so the chain list -> offsets -> pins ->
-// records costs one memory latency per edge instead of four.  The evaluation
-// is the same three passes as in k_ab_warp.
+// G lanes per edge (G = 16 for 8 < |e| <= 16, two edges per warp; G = 32 for
+// 16 < |e| <= 32), one pin per lane, software-pipelined over the group's
+// edges: while edge j is evaluated, the candidate records and blocks of edge
+// j+1, the pins of edge j+2, the offsets of edge j+3 and the id of edge j+4
+// are in flight, so the chain list -> offsets -> pins -> records costs one
+// memory latency per edge instead of four.  The evaluation is the same three
+// passes as in k_ab_warp, on one table per group.
+template <int G>
 __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp_small(AbArgs a) {
-  extern __shared__ unsigned long long s_tab[];  // per warp: maxd[k], mina[k]
-  __shared__ uint32_t s_nm[kAbWarps][kMaxK / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long *maxd = s_tab + (size_t)w * 2 * a.k;
+  static_assert(G == 16 || G == 32, "a group is a half warp or a warp");
+  constexpr int kGroups = kAbWarps * (32 / G);
+  extern __shared__ unsigned long long s_tab[];  // per group: maxd[k], mina[k]
+  __shared__ uint32_t s_nm[kGroups][kMaxK / 32];
+  const int li = threadIdx.x % G, grp = threadIdx.x / G;
+  unsigned long long *maxd = s_tab + (size_t)grp * 2 * a.k;
   unsigned long long *mina = maxd + a.k;
-  uint32_t *nm = s_nm[w];
-  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
+  uint32_t *nm = s_nm[grp];
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const long long nw = (gridDim.x * (long long)blockDim.x) / G;
   auto edge_at = [&](long long i) -> int { return i < a.nlist ? a.elist[i] : -1; };
   // stage registers, named by how many edges ahead of the evaluated one they are
   int e4 = edge_at(gw + 4 * nw);
@@ -265,15 +254,15 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp_small(AbArgs a) {
   int v2 = -1;
   if (e2 >= 0) {
     const int64_t q = a.eptr[e2];
-    if (lane < a.eptr[e2 + 1] - q) v2 = a.pins[q + lane];
+    if (li < a.eptr[e2 + 1] - q) v2 = a.pins[q + li];
   }
   int e1 = edge_at(gw + nw), v1 = -1;
   uint64_t r1 = 0;
   int b1 = 0;
   if (e1 >= 0) {
     const int64_t q = a.eptr[e1];
-    if (lane < a.eptr[e1 + 1] - q) {
-      v1 = a.pins[q + lane];
+    if (li < a.eptr[e1 + 1] - q) {
+      v1 = a.pins[q + li];
       r1 = a.cand[v1];
       b1 = a.part[v1];
     }
@@ -283,18 +272,22 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp_small(AbArgs a) {
   int b0 = 0;
   if (e0 >= 0) {
     const int64_t q = a.eptr[e0];
-    if (lane < a.eptr[e0 + 1] - q) {
-      v0 = a.pins[q + lane];
+    if (li < a.eptr[e0 + 1] - q) {
+      v0 = a.pins[q + li];
       r0 = a.cand[v0];
       b0 = a.part[v0];
     }
   }
-  for (long long i = gw; i < a.nlist; i += nw) {
+  // The groups of a warp run in lockstep: the loop bound is the warp's first
+  // group (a group past the end of the list has e0 = -1 and no pins), so the
+  // warp-wide votes and barriers below see every lane.
+  const long long wfirst = (blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31)) / G;
+  for (long long i = gw, iw = wfirst; iw < a.nlist; i += nw, iw += nw) {
     // advance the pipeline: every load below is first used one iteration later
     const int e5 = edge_at(i + 5 * nw);
     const int64_t p4 = e4 >= 0 ? a.eptr[e4] : 0;
     const int sz4 = e4 >= 0 ? (int)(a.eptr[e4 + 1] - p4) : 0;
-    const int v3 = lane < sz3 ? a.pins[p3 + lane] : -1;
+    const int v3 = li < sz3 ? a.pins[p3 + li] : -1;
     const uint64_t r2 = v2 >= 0 ? a.cand[v2] : 0ull;
     const int b2 = v2 >= 0 ? a.part[v2] : 0;
     // evaluate edge e0 with v0 / r0 / b0
@@ -621,23 +614,41 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
   if (c->n_tiny > 0) {
     a.elist = c->e_tiny;
     a.nlist = c->n_tiny;
-    k_ab_tiny<<<grid_for(c->n_tiny, 256, c->launch_sms), 256, 0, c->stream>>>(a);
+    k_ab_tiny<<<grid_for(c->n_tiny, 256, c->launch_sms, c->ab_bps[0]), 256, 0, c->stream>>>(a);
+    ++c->kernel_launches;
+  }
+  if (c->n_mid_half > 0) {
+    a.elist = c->e_mid_half;
+    a.nlist = c->n_mid_half;
+    const size_t smem = (size_t)kAbWarps * 2 * 2 * c->k * sizeof(unsigned long long);
+    k_ab_warp_small<16><<<grid_for((int64_t)c->n_mid_half * 16, kAbWarps * 32, c->launch_sms, c->ab_bps[1]),
+                          kAbWarps * 32, smem, c->stream>>>(a);
     ++c->kernel_launches;
   }
   if (c->n_mid_small > 0) {
     a.elist = c->e_mid_small;
     a.nlist = c->n_mid_small;
     const size_t smem = (size_t)kAbWarps * 2 * c->k * sizeof(unsigned long long);
-    k_ab_warp_small<<<grid_for((int64_t)c->n_mid_small * 32, kAbWarps * 32, c->launch_sms), kAbWarps * 32, smem,
-                      c->stream>>>(a);
+    k_ab_warp_small<32><<<grid_for((int64_t)c->n_mid_small * 32, kAbWarps * 32, c->launch_sms, c->ab_bps[2]),
+                          kAbWarps * 32, smem, c->stream>>>(a);
     ++c->kernel_launches;
   }
-  if (c->n_mid > 0) {
-    a.elist = c->e_mid;
-    a.nlist = c->n_mid;
+  if (c->n_mid > 0) {  // 65..128 pins first, then 33..64
     const size_t smem = (size_t)kAbWarps * 2 * c->k * sizeof(unsigned long long);
-    k_ab_warp<<<grid_for((int64_t)c->n_mid * 32, kAbWarps * 32, c->launch_sms), kAbWarps * 32, smem, c->stream>>>(a);
-    ++c->kernel_launches;
+    if (c->n_mid_hi > 0) {
+      a.elist = c->e_mid;
+      a.nlist = c->n_mid_hi;
+      k_ab_warp<4><<<grid_for((int64_t)c->n_mid_hi * 32, kAbWarps * 32, c->launch_sms, c->ab_bps[3]), kAbWarps * 32,
+                     smem, c->stream>>>(a);
+      ++c->kernel_launches;
+    }
+    if (c->n_mid > c->n_mid_hi) {
+      a.elist = c->e_mid + c->n_mid_hi;
+      a.nlist = c->n_mid - c->n_mid_hi;
+      k_ab_warp<2><<<grid_for((int64_t)a.nlist * 32, kAbWarps * 32, c->launch_sms, c->ab_bps[5]), kAbWarps * 32, smem,
+                     c->stream>>>(a);
+      ++c->kernel_launches;
+    }
   }
   if (c->n_seg > 0) {
     SegArgs sa{};
@@ -649,7 +660,7 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
     sa.nmw = c->ab_nm;
     sa.nslots = c->n_slots;
     const size_t smem = (size_t)c->k * 2 * sizeof(unsigned long long);
-    k_ab_block<<<grid_for(c->n_seg, 1, c->launch_sms, 8), kSegThreads, smem, c->stream>>>(sa);
+    k_ab_block<<<grid_for(c->n_seg, 1, c->launch_sms, c->ab_bps[4]), kSegThreads, smem, c->stream>>>(sa);
     ++c->kernel_launches;
     if (c->n_slots > 0) {
       k_ab_slots<<<grid_for((int64_t)c->n_slots * c->k, 256, c->launch_sms), 256, 0, c->stream>>>(sa);
@@ -659,6 +670,23 @@ cudaError_t launch_afterburner(jet_ctx *c, const int32_t *part, const int32_t *p
     }
   }
   return cudaGetLastError();
+}
+
+// Resident blocks per SM of the afterburner kernels at this context's k.
+cudaError_t prepare_afterburner_kernels(jet_ctx *c) {
+  const size_t warp_tab = (size_t)kAbWarps * 2 * c->k * sizeof(unsigned long long);
+  // The half-warp kernel holds two tables per warp: above 48 KB for k > 192.  The limit is a property
+  // of the kernel, shared by every context, so it is set for the largest k, not for this context's.
+  cudaError_t e = cudaFuncSetAttribute(k_ab_warp_small<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)kAbWarps * 2 * 2 * kMaxK * sizeof(unsigned long long)));
+  if (e == cudaSuccess) e = resident_blocks(k_ab_tiny, 256, 0, &c->ab_bps[0]);
+  if (e == cudaSuccess) e = resident_blocks(k_ab_warp_small<16>, kAbWarps * 32, 2 * warp_tab, &c->ab_bps[1]);
+  if (e == cudaSuccess) e = resident_blocks(k_ab_warp_small<32>, kAbWarps * 32, warp_tab, &c->ab_bps[2]);
+  if (e == cudaSuccess) e = resident_blocks(k_ab_warp<4>, kAbWarps * 32, warp_tab, &c->ab_bps[3]);
+  if (e == cudaSuccess) e = resident_blocks(k_ab_warp<2>, kAbWarps * 32, warp_tab, &c->ab_bps[5]);
+  if (e == cudaSuccess)
+    e = resident_blocks(k_ab_block, kSegThreads, (size_t)c->k * 2 * sizeof(unsigned long long), &c->ab_bps[4]);
+  return e;
 }
 
 // Cuts the block-class edges into segments (largest first) and sets up the

@@ -1006,7 +1006,14 @@ cudaError_t launch_group(const TeamArgs &a, int kmax, int ctas, int threads, int
   auto kern = k_batch_teams<MULTI, KWP>;
   const size_t smem = (size_t)kmax * (8 + 8 + 8 + 4) + 8 * (size_t)(kmax & 1) +
                       (size_t)(threads / 32) * (2 * kmax + (KWP + 1) / 2) * 8;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // The limit is a property of the kernel, shared by every batch and graph that launches it: set it for
+  // the largest instance this mask width allows (k = 32 KWP) and 1,024 threads, so it never shrinks
+  // under an earlier launch.
+  constexpr size_t kSmemMax =
+      (size_t)(32 * KWP) * (8 + 8 + 8 + 4) + 8 + (size_t)32 * (2 * 32 * KWP + (KWP + 1) / 2) * 8;
+  static_assert(kSmemMax <= 227 * 1024, "the team kernel's shared memory must fit one block");
+  if (smem > kSmemMax) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
   if (e != cudaSuccess) return e;
   if (MULTI && ctas > 8) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

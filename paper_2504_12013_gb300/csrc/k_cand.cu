@@ -674,7 +674,8 @@ cudaError_t launch_cand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_heavy > 0) {
     a.vlist = c->v_heavy;
     a.nlist = c->n_heavy;
-    k_cand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->launch_sms), 256, 0, c->stream>>>(a);
+    k_cand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->launch_sms, c->heavy_bps[0]), 256, 0,
+                            c->stream>>>(a);
     ++c->kernel_launches;
   }
   return cudaGetLastError();
@@ -694,7 +695,8 @@ cudaError_t launch_rbcand_kwp(jet_ctx *c, const CandArgs &base) {
   if (c->n_heavy > 0) {
     a.vlist = c->v_heavy;
     a.nlist = c->n_heavy;
-    k_rbcand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->launch_sms), 256, 0, c->stream>>>(a);
+    k_rbcand_heavy<KWP><<<grid_for((int64_t)c->n_heavy * 32, 256, c->launch_sms, c->heavy_bps[1]), 256, 0,
+                              c->stream>>>(a);
     ++c->kernel_launches;
   }
   return cudaGetLastError();
@@ -744,6 +746,8 @@ cudaError_t prepare_stage(jet_ctx *c) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->stage_bps[1], k_rbcand_light<KWP, UNIT>, 256, bytes);
   for (int i = 0; i < 2; ++i)
     if (c->stage_bps[i] < 1) c->stage_bps[i] = 1;
+  if (e == cudaSuccess) e = resident_blocks(k_cand_heavy<KWP>, 256, 0, &c->heavy_bps[0]);
+  if (e == cudaSuccess) e = resident_blocks(k_rbcand_heavy<KWP>, 256, 0, &c->heavy_bps[1]);
   return e;
 }
 

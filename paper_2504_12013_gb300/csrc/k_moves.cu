@@ -34,6 +34,51 @@ struct MoveArgs {
 // short (rebalancing rounds).
 constexpr int kMoveLanes = 8;
 
+// The phi and bitmask updates of one move s -> t over the incidences j,
+// j + kMoveLanes, ... below j1 (one lane's share of I(v)).  kMoveIlp
+// incidences are loaded first and their atomics issued together, so that
+// several atomics with return are in flight per lane before the first result
+// is needed.
+constexpr int kMoveIlp = 4;
+// Grids of the apply kernels: this many waves of resident blocks.  The moves
+// are dealt to blocks round-robin but their costs differ (degree, hub rows
+// shared with other moves), and blocks that finish early take the next wave.
+// A block with no move (or record) to take returns at once, so short move
+// lists (late rebalancing rounds) do not pay for the large grid.
+constexpr int kMoveWaves = 4;
+constexpr int kRbMoveWaves = 4;  // the same for the rebalancing apply
+
+__device__ __forceinline__ void move_incidences(const MoveArgs &a, int64_t j, int64_t j1, int s, int t) {
+  const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
+  for (; j < j1; j += kMoveIlp * kMoveLanes) {
+    int64_t e[kMoveIlp];
+#pragma unroll
+    for (int q = 0; q < kMoveIlp; ++q) {
+      const int64_t jj = j + q * kMoveLanes;
+      e[q] = jj < j1 ? a.inc[jj] : -1;
+    }
+    int os[kMoveIlp], ot[kMoveIlp];
+#pragma unroll
+    for (int q = 0; q < kMoveIlp; ++q) {
+      os[q] = 0;  // no crossing for an absent incidence
+      ot[q] = 2;
+      if (e[q] >= 0) {
+        os[q] = atomicSub(&a.phi[e[q] * a.k + s], 1);  // os -> os - 1
+        ot[q] = atomicAdd(&a.phi[e[q] * a.k + t], 1);  // ot -> ot + 1
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kMoveIlp; ++q) {
+      if (e[q] < 0) continue;
+      uint32_t *row = a.mask + e[q] * 2 * a.kwp;
+      if (os[q] == 1) atomicXor(&row[s >> 5], sbit);           // 1 -> 0
+      if (os[q] == 2) atomicXor(&row[a.kwp + (s >> 5)], sbit);  // 2 -> 1
+      if (ot[q] == 0) atomicXor(&row[t >> 5], tbit);           // 0 -> 1
+      if (ot[q] == 1) atomicXor(&row[a.kwp + (t >> 5)], tbit);  // 1 -> 2
+    }
+  }
+}
+
 // Pi(v) <- t and phi_e[s]--, phi_e[t]++ for every e in I(v); c(V_s), c(V_t)
 // and |V_s|, |V_t| through shared-memory partial sums; and both bitmasks of
 // every touched edge, exactly, without a second pass: the atomic updates of
@@ -44,9 +89,10 @@ constexpr int kMoveLanes = 8;
 __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   __shared__ long long s_dw[kMaxK];
   __shared__ int s_dc[kMaxK];
+  const long long nm = (long long)a.cnt->n_moves;
+  if ((long long)blockIdx.x * (blockDim.x / kMoveLanes) >= nm) return;  // no move for this block
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) { s_dw[b] = 0; s_dc[b] = 0; }
   __syncthreads();
-  const long long nm = (long long)a.cnt->n_moves;
   unsigned long long pins = 0;  // incidences moved by this thread's moves (work count)
   const int sub = threadIdx.x % kMoveLanes;
   const long long g0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kMoveLanes;
@@ -63,20 +109,10 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
       atomicSub(&s_dc[s], 1);
       atomicAdd(&s_dc[t], 1);
     }
-    const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
     const int64_t j1 = a.vptr[v + 1];
     if (sub == 0) pins += (unsigned long long)(j1 - a.vptr[v]);
     if (a.graph) continue;
-    for (int64_t j = a.vptr[v] + sub; j < j1; j += kMoveLanes) {
-      const int64_t e = a.inc[j];
-      const int os = atomicSub(&a.phi[e * a.k + s], 1);  // os -> os - 1
-      const int ot = atomicAdd(&a.phi[e * a.k + t], 1);  // ot -> ot + 1
-      uint32_t *row = a.mask + e * 2 * a.kwp;
-      if (os == 1) atomicXor(&row[s >> 5], sbit);           // 1 -> 0
-      if (os == 2) atomicXor(&row[a.kwp + (s >> 5)], sbit);  // 2 -> 1
-      if (ot == 0) atomicXor(&row[t >> 5], tbit);           // 0 -> 1
-      if (ot == 1) atomicXor(&row[a.kwp + (t >> 5)], tbit);  // 1 -> 2
-    }
+    move_incidences(a, a.vptr[v] + sub, j1, s, t);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) pins += __shfl_xor_sync(kFull, pins, o);
@@ -277,10 +313,11 @@ __global__ void __launch_bounds__(256) k_rb_apply(RbArgs r, MoveArgs a) {
   __shared__ long long s_dw[kMaxK];
   __shared__ int s_dc[kMaxK];
   __shared__ unsigned long long s_moves, s_pins;
+  const long long nrec = (long long)r.cnt->n_rec;
+  if ((long long)blockIdx.x * blockDim.x >= nrec) return;  // no record for this block
   for (int b = threadIdx.x; b < a.k; b += blockDim.x) { s_dw[b] = 0; s_dc[b] = 0; }
   if (threadIdx.x == 0) { s_moves = 0; s_pins = 0; }
   __syncthreads();
-  const long long nrec = (long long)r.cnt->n_rec;
   unsigned long long moves = 0, pins = 0;
   const int lane = threadIdx.x & 31, grp = lane / kMoveLanes, sub = lane % kMoveLanes;
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -318,17 +355,7 @@ __global__ void __launch_bounds__(256) k_rb_apply(RbArgs r, MoveArgs a) {
           ++moves;
           pins += (unsigned long long)(j1 - j0);
         }
-        const uint32_t sbit = 1u << (s & 31), tbit = 1u << (t & 31);
-        for (int64_t j = a.graph ? j1 : j0 + sub; j < j1; j += kMoveLanes) {
-          const int64_t e = a.inc[j];
-          const int os = atomicSub(&a.phi[e * a.k + s], 1);  // os -> os - 1
-          const int ot = atomicAdd(&a.phi[e * a.k + t], 1);  // ot -> ot + 1
-          uint32_t *row = a.mask + e * 2 * a.kwp;
-          if (os == 1) atomicXor(&row[s >> 5], sbit);           // 1 -> 0
-          if (os == 2) atomicXor(&row[a.kwp + (s >> 5)], sbit);  // 2 -> 1
-          if (ot == 0) atomicXor(&row[t >> 5], tbit);           // 0 -> 1
-          if (ot == 1) atomicXor(&row[a.kwp + (t >> 5)], tbit);  // 1 -> 2
-        }
+        if (!a.graph) move_incidences(a, j0 + sub, j1, s, t);
       }
       // drop the (up to) 32 / kMoveLanes records just applied
       for (int q = 0; q < 32 / kMoveLanes && bal; ++q) bal &= bal - 1;
@@ -468,10 +495,18 @@ RbArgs rb_args(jet_ctx *c, const int64_t *block_w, const int32_t *part) {
 
 }  // namespace
 
+cudaError_t prepare_move_kernels(jet_ctx *c) {
+  cudaError_t e = resident_blocks(k_apply, 256, 0, &c->move_bps[0]);
+  if (e == cudaSuccess) e = resident_blocks(k_rb_apply<unsigned long long>, 256, 0, &c->move_bps[1]);
+  if (e == cudaSuccess) e = resident_blocks(k_rb_apply<u128>, 256, 0, &c->move_bps[2]);
+  return e;
+}
+
 cudaError_t launch_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *block_w) {
   if (c->n == 0) return cudaSuccess;
   const MoveArgs a = move_args(c, part, phi, block_w);
-  k_apply<<<grid_for((int64_t)c->n * kMoveLanes, 256, c->launch_sms, 8), 256, 0, c->stream>>>(a);
+  k_apply<<<grid_for((int64_t)c->n * kMoveLanes, 256, c->launch_sms, kMoveWaves * c->move_bps[0]), 256, 0,
+            c->stream>>>(a);
   ++c->kernel_launches;
   return cudaGetLastError();
 }
@@ -510,9 +545,11 @@ cudaError_t launch_rb_apply(jet_ctx *c, int32_t *part, int32_t *phi, int64_t *bl
   if (c->n == 0) return cudaSuccess;
   const RbArgs r = rb_args(c, block_w, part);
   const MoveArgs a = move_args(c, part, phi, block_w);
-  const int g = grid_for(c->n, 256, c->launch_sms, 8);
-  if (r.tbits <= 64) k_rb_apply<unsigned long long><<<g, 256, 0, c->stream>>>(r, a);
-  else k_rb_apply<u128><<<g, 256, 0, c->stream>>>(r, a);
+  if (r.tbits <= 64)
+    k_rb_apply<unsigned long long><<<grid_for(c->n, 256, c->launch_sms, kRbMoveWaves * c->move_bps[1]), 256, 0,
+                                     c->stream>>>(r, a);
+  else
+    k_rb_apply<u128><<<grid_for(c->n, 256, c->launch_sms, kRbMoveWaves * c->move_bps[2]), 256, 0, c->stream>>>(r, a);
   ++c->kernel_launches;
   return cudaGetLastError();
 }

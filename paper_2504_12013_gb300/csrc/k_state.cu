@@ -142,17 +142,19 @@ __global__ void k_vertex_codes(const int64_t *wdeg, int32_t n, uint8_t *code) {
 
 // Edge classes: code = |e| for |e| <= kTinyEdge (so the tiny list comes out
 // ordered by size and a warp's edges tend to share one size); then the warp
-// class split into kSmallMidEdge-pin edges (one code) and larger ones by
-// size bucket, largest first, so the warps that get the longest edges start
-// first; then the block class.
+// class split into edges of at most kHalfMidEdge and of at most
+// kSmallMidEdge pins (one code each) and larger ones by size bucket, largest
+// first, so the warps that get the longest edges start first; then the block
+// class.
 __global__ void k_edge_codes(const int64_t *eptr, int32_t m, uint8_t *code) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sz = eptr[e + 1] - eptr[e];
     int c;
     if (sz <= kTinyEdge) c = (int)sz;
-    else if (sz <= kSmallMidEdge) c = kTinyEdge + 1;
-    else if (sz <= kWarpEdge) c = sz > 64 ? kTinyEdge + 2 : kTinyEdge + 3;  // 65..128 first, then 33..64
-    else c = kTinyEdge + 4;
+    else if (sz <= kHalfMidEdge) c = kTinyEdge + 1;
+    else if (sz <= kSmallMidEdge) c = kTinyEdge + 2;
+    else if (sz <= kWarpEdge) c = sz > 64 ? kTinyEdge + 3 : kTinyEdge + 4;  // 65..128 first, then 33..64
+    else c = kTinyEdge + 5;
     code[e] = (uint8_t)c;
   }
 }
@@ -405,10 +407,13 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
   if (e == cudaSuccess) {
     c->n_tiny = 0;
     for (int cl = 0; cl <= kTinyEdge; ++cl) c->n_tiny += t[cl];
-    c->n_mid_small = t[kTinyEdge + 1];
-    c->n_mid = t[kTinyEdge + 2] + t[kTinyEdge + 3];
-    c->n_big = t[kTinyEdge + 4];
-    c->e_mid_small = c->e_tiny + c->n_tiny;
+    c->n_mid_half = t[kTinyEdge + 1];
+    c->n_mid_small = t[kTinyEdge + 2];
+    c->n_mid = t[kTinyEdge + 3] + t[kTinyEdge + 4];
+    c->n_mid_hi = t[kTinyEdge + 3];
+    c->n_big = t[kTinyEdge + 5];
+    c->e_mid_half = c->e_tiny + c->n_tiny;
+    c->e_mid_small = c->e_mid_half + c->n_mid_half;
     c->e_mid = c->e_mid_small + c->n_mid_small;
     c->e_big = c->e_mid + c->n_mid;
   }
