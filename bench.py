@@ -43,6 +43,11 @@ WORKLOADS = {
                   "c in 1..4, k=64, eps=3/100",
                   lambda seed: (lambda h: (h, 64, synth.part_perm(seed, h.n, 64)))(
                       synth.vlsi(seed, 500_000, 550_000, window=5_000))),
+    # the row-net shape at a quarter of the size (phi 512 MB), for multi-pass ncu captures
+    "rownet_1m": ("sparse-matrix row-net n=m=1,000,000, log-normal(2,1) rows + 50 hubs of 50k-200k pins, k=128, "
+                  "eps=3/100",
+                  lambda seed: (lambda h: (h, 128, synth.part_perm(seed, h.n, 128)))(
+                      synth.rownet(seed, 1_000_000, 1_000_000, n_hubs=50))),
 }
 TAU = (3, 4)
 SCHEDULE = ((3, 4), (3, 8), (0, 1))

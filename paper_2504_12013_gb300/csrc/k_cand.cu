@@ -208,10 +208,17 @@ __device__ __forceinline__ void eligible_words(const long long *s_cap, int k, in
 // Slot t of lane l is row t*32 + l of a buffer, so the lanes' reads of the
 // stage are bank-conflict free.  Lanes never read each other's slots.
 
+// Minimum resident blocks per SM of the staged light kernels: the register
+// budget per thread is 65,536 / (256 x blocks).  At k <= 128 (KWP = 4) three
+// blocks leave 85 registers, so the rebalancing-target kernel does not spill
+// (at four blocks, 64 registers, it did, and its rounds took 9 % longer).
+template <int KWP>
+constexpr int kLightBlocks = KWP >= 8 ? 2 : (KWP == 4 ? 3 : 4);
+
 template <int KWP>
 struct Stage {
   static constexpr int kRow = 2 * KWP;                          // words of one mask row
-  static constexpr int kBatch = KWP <= 2 ? 4 : (KWP == 4 ? 3 : 2);  // rows per lane per batch
+  static constexpr int kBatch = KWP <= 2 ? 4 : 2;  // rows per lane per batch
   // per-warp stage: 2 buffers x kBatch x 32 rows | the same for omega (weighted only)
   template <bool UNIT>
   static constexpr int bytes() {
@@ -449,7 +456,7 @@ __device__ __forceinline__ void cand_batch(const CandArgs &a, uint8_t *stage, co
 }
 
 template <int KWP, bool UNIT>
-__global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_cand_light(CandArgs a) {
+__global__ void __launch_bounds__(256, kLightBlocks<KWP>) k_cand_light(CandArgs a) {
   extern __shared__ __align__(16) uint8_t dyn_smem[];
   __shared__ WarpQueue s_q[8];
   const int w = threadIdx.x >> 5;
@@ -530,7 +537,7 @@ __device__ __forceinline__ void rb_batch(const CandArgs &a, uint8_t *stage, cons
 }
 
 template <int KWP, bool UNIT>
-__global__ void __launch_bounds__(256, KWP >= 8 ? 2 : 4) k_rbcand_light(CandArgs a) {
+__global__ void __launch_bounds__(256, kLightBlocks<KWP>) k_rbcand_light(CandArgs a) {
   constexpr int kTab = 32;  // eligibility words tabulated for c(v) <= 32
   __shared__ long long s_cap[kMaxK], s_bw[kMaxK];
   __shared__ int s_over[kMaxK];
