@@ -488,6 +488,20 @@ int jet_rounds_host(const jet_hypergraph *hg_host, const jet_params *params, int
                     int32_t n_rounds, int32_t *part, jet_round_stats *stats);
 
 /*
+ * Device memory of the library (no counterpart in the paper).  The library's
+ * stream-ordered allocations (context workspace, the device copies of the
+ * host-buffer calls above, batch plans, coarsening pools) come from a memory
+ * pool of its own, one per device, that keeps what the library frees for its
+ * next calls instead of returning it to the driver at every synchronization:
+ * a call on host buffers would otherwise map its gigabytes afresh each time.
+ * So after a call the process keeps up to the largest working set the library
+ * has needed on that device.  jet_release_memory returns the kept memory of
+ * every device's pool to the driver (cudaMemPoolTrimTo); call it when no
+ * library work is in flight.  Returns JET_OK or JET_ERR_CUDA.
+ */
+int jet_release_memory(void);
+
+/*
  * Profiling.  The library's kernels fall into JET_PROF_FAMILIES families:
  *   0 pin counts and bitmasks    1 move candidates         2 afterburner
  *   3 approval and locks         4 apply moves             5 rebalancing targets

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -15,6 +16,11 @@ using namespace jet;
 
 namespace {
 thread_local char g_err[256] = {0};
+
+// The library's device memory pools, one per device (created on first use).
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
 }  // namespace
 
 namespace jet {
@@ -26,6 +32,32 @@ int fail(jet_ctx *c, int code, const char *fmt, ...) {
   vsnprintf(dst, 256, fmt, ap);
   va_end(ap);
   return code;
+}
+
+cudaError_t pool_alloc_bytes(void **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+      uint64_t keep = ~0ull;  // never release at synchronization; jet_release_memory trims
+      if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+      }
+      g_pools[dev] = pool;
+    }
+    pool = g_pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 int cuda_fail(jet_ctx *c, cudaError_t e, const char *where) {
@@ -41,7 +73,7 @@ int cuda_fail(jet_ctx *c, cudaError_t e, const char *where) {
 
 template <class T>
 cudaError_t dalloc(jet_ctx *c, T **p, size_t count) {
-  return cudaMallocAsync(reinterpret_cast<void **>(p), sizeof(T) * (count > 0 ? count : 1), c->stream);
+  return jet::pool_alloc(reinterpret_cast<void **>(p), sizeof(T) * (count > 0 ? count : 1), c->stream);
 }
 
 void dfree(jet_ctx *c, void *p) {
@@ -323,6 +355,16 @@ void jet::set_global_error(const char *fmt, ...) {
 extern "C" {
 
 const char *jet_last_error(const jet_ctx *ctx) { return ctx ? ctx->err : g_err; }
+
+int jet_release_memory(void) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  for (int d = 0; d < kMaxDevices; ++d) {
+    if (!g_pools[d]) continue;
+    const cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+    if (e != cudaSuccess) return fail(nullptr, JET_ERR_CUDA, "memory pool of device %d: %s", d, cudaGetErrorString(e));
+  }
+  return JET_OK;
+}
 
 int jet_ctx_create(jet_ctx **out, const jet_hypergraph *hg, const jet_params *p, void *stream) {
   if (!out) return fail(nullptr, JET_ERR_INVALID_ARG, "out is NULL");
@@ -783,7 +825,7 @@ int host_job(const jet_hypergraph *hh, const jet_params *p, int32_t *part, cudaS
   size_t sizes[] = {8 * (m + 1), 8 * (n + 1), 8 * k, 4 * (P ? P : 1), 4 * (P ? P : 1),
                     4 * (n ? n : 1), 4 * (m ? m : 1), 4 * (n ? n : 1), 4 * (m * k > 0 ? m * k : 1)};
   int rc = JET_OK;
-  for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaMallocAsync(bufs[i], sizes[i], s);
+  for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = jet::pool_alloc(bufs[i], sizes[i], s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(eptr, hh->eptr, 8 * (m + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(vptr, hh->vptr, 8 * (n + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && P) e = cudaMemcpyAsync(pins, hh->pins, 4 * P, cudaMemcpyHostToDevice, s);

@@ -309,6 +309,17 @@ long long team_pins(TeamPlan *p, int32_t i);
 // Sets the message returned by jet_last_error(NULL) (for entry points without a context).
 void set_global_error(const char *fmt, ...);
 
+// Device memory of the library: stream-ordered allocations from a pool of its
+// own, one per device, which keeps the memory the library frees for its next
+// calls instead of returning it to the driver at each synchronization (a
+// call on host buffers maps gigabytes afresh otherwise).  jet_release_memory
+// returns it.
+cudaError_t pool_alloc_bytes(void **p, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t pool_alloc(T **p, size_t bytes, cudaStream_t s) {
+  return pool_alloc_bytes(reinterpret_cast<void **>(p), bytes, s);
+}
+
 // Resident blocks per SM of `kernel` at this block size and dynamic shared
 // memory (at least 1), for grids sized in whole waves.
 template <class K>

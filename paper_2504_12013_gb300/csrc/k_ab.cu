@@ -700,7 +700,7 @@ cudaError_t prepare_afterburner(jet_ctx *c) {
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
   std::vector<int64_t> sz(c->n_big);
   int64_t *dsz = nullptr;
-  if ((e = cudaMallocAsync(reinterpret_cast<void **>(&dsz), sizeof(int64_t) * c->n_big, c->stream)) != cudaSuccess)
+  if ((e = jet::pool_alloc(reinterpret_cast<void **>(&dsz), sizeof(int64_t) * c->n_big, c->stream)) != cudaSuccess)
     return e;
   k_edge_sizes<<<grid_for(c->n_big, 256, c->launch_sms), 256, 0, c->stream>>>(c->eptr, c->e_big, c->n_big, dsz);
   e = cudaGetLastError();
@@ -720,18 +720,18 @@ cudaError_t prepare_afterburner(jet_ctx *c) {
   std::stable_sort(seg.begin(), seg.end(), [](const int4 &x, const int4 &y) { return x.z > y.z; });
   c->n_seg = (int32_t)seg.size();
   c->n_slots = (int32_t)slot_edge.size();
-  if ((e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_seg), sizeof(int4) * seg.size(), c->stream)) != cudaSuccess)
+  if ((e = jet::pool_alloc(reinterpret_cast<void **>(&c->ab_seg), sizeof(int4) * seg.size(), c->stream)) != cudaSuccess)
     return e;
   if ((e = cudaMemcpyAsync(c->ab_seg, seg.data(), sizeof(int4) * seg.size(), cudaMemcpyHostToDevice, c->stream)) !=
       cudaSuccess)
     return e;
   if (c->n_slots > 0) {
     const size_t ns = (size_t)c->n_slots;
-    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_slot_edge), sizeof(int32_t) * ns, c->stream)) !=
+    if ((e = jet::pool_alloc(reinterpret_cast<void **>(&c->ab_slot_edge), sizeof(int32_t) * ns, c->stream)) !=
             cudaSuccess ||
-        (e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_tab), sizeof(unsigned long long) * ns * 2 * c->k,
+        (e = jet::pool_alloc(reinterpret_cast<void **>(&c->ab_tab), sizeof(unsigned long long) * ns * 2 * c->k,
                              c->stream)) != cudaSuccess ||
-        (e = cudaMallocAsync(reinterpret_cast<void **>(&c->ab_nm), sizeof(uint32_t) * ns * 8, c->stream)) !=
+        (e = jet::pool_alloc(reinterpret_cast<void **>(&c->ab_nm), sizeof(uint32_t) * ns * 8, c->stream)) !=
             cudaSuccess)
       return e;
     if ((e = cudaMemcpyAsync(c->ab_slot_edge, slot_edge.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice,

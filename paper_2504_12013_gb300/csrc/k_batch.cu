@@ -1132,19 +1132,19 @@ int team_plan_build(TeamPlan **out, jet_ctx *const *ctxs, int32_t count, int32_t
   p->group_start.push_back(count);
   const size_t ng = p->group_kwp.size();
   p->team_slots = 4096;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&p->dev), sizeof(TeamInst) * count, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&p->counts), sizeof(TeamCount) * count, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&p->res), sizeof(jet_refine_result) * count, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&p->order), sizeof(int32_t) * count, s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&p->sample), sizeof(int32_t) * count, s);
+  cudaError_t e = jet::pool_alloc(reinterpret_cast<void **>(&p->dev), sizeof(TeamInst) * count, s);
+  if (e == cudaSuccess) e = jet::pool_alloc(reinterpret_cast<void **>(&p->counts), sizeof(TeamCount) * count, s);
+  if (e == cudaSuccess) e = jet::pool_alloc(reinterpret_cast<void **>(&p->res), sizeof(jet_refine_result) * count, s);
+  if (e == cudaSuccess) e = jet::pool_alloc(reinterpret_cast<void **>(&p->order), sizeof(int32_t) * count, s);
+  if (e == cudaSuccess) e = jet::pool_alloc(reinterpret_cast<void **>(&p->sample), sizeof(int32_t) * count, s);
   if (e == cudaSuccess)
-    e = cudaMallocAsync(reinterpret_cast<void **>(&p->tau), sizeof(int32_t) * (2 * n_tau > 0 ? 2 * n_tau : 1), s);
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&p->queue), sizeof(unsigned) * ng, s);
+    e = jet::pool_alloc(reinterpret_cast<void **>(&p->tau), sizeof(int32_t) * (2 * n_tau > 0 ? 2 * n_tau : 1), s);
+  if (e == cudaSuccess) e = jet::pool_alloc(reinterpret_cast<void **>(&p->queue), sizeof(unsigned) * ng, s);
   if (e == cudaSuccess)
-    e = cudaMallocAsync(reinterpret_cast<void **>(&p->team_inst), sizeof(int32_t) * p->team_slots, s);
+    e = jet::pool_alloc(reinterpret_cast<void **>(&p->team_inst), sizeof(int32_t) * p->team_slots, s);
   size_t nbins = 0;
   for (int i = 0; i < count; ++i) nbins += (size_t)p->host[i].k * 256;
-  if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&p->hist), sizeof(unsigned long long) * nbins, s);
+  if (e == cudaSuccess) e = jet::pool_alloc(reinterpret_cast<void **>(&p->hist), sizeof(unsigned long long) * nbins, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->hist, 0, sizeof(unsigned long long) * nbins, s);
   if (e == cudaSuccess) {
     size_t off = 0;

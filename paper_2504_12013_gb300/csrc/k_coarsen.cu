@@ -928,7 +928,7 @@ struct Scratch {
   T *get(int64_t count) {
     void *p = nullptr;
     const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
-    const cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    const cudaError_t e = jet::pool_alloc(&p, bytes, s);
     if (e != cudaSuccess) {
       if (err == cudaSuccess) err = e;
       return nullptr;

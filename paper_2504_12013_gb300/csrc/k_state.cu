@@ -161,7 +161,10 @@ __global__ void k_edge_codes(const int64_t *eptr, int32_t m, uint8_t *code) {
 
 // ---------------------------------------------------------------- pin counts
 // Warp per edge: histogram of the pins' blocks in shared memory, then one
-// coalesced store of the phi row and one ballot per mask word.
+// coalesced store of the phi row and one ballot per mask word.  An edge longer
+// than one segment (kSegPins pins: the hub rows of a row-net) would hold its
+// warp for thousands of steps; its warp only clears the row, and
+// k_pincounts_seg and k_masks_from_phi complete it.
 __global__ void __launch_bounds__(256) k_pincounts(const int64_t *eptr, const int32_t *pins, const int32_t *part,
                                                    int32_t m, int32_t k, int32_t kwp, int32_t *phi, uint32_t *mask,
                                                    Counters *cnt) {
@@ -172,10 +175,14 @@ __global__ void __launch_bounds__(256) k_pincounts(const int64_t *eptr, const in
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int err = 0;
   for (int64_t e = gw; e < m; e += nw) {
+    const int64_t p0 = eptr[e], p1 = eptr[e + 1];
+    if (p1 - p0 > kSegPins) {  // warp-uniform
+      for (int b = lane; b < k; b += 32) phi[e * k + b] = 0;
+      continue;
+    }
     for (int b = lane; b < k; b += 32) h[b] = 0;
     __syncwarp();
-    const int64_t p1 = eptr[e + 1];
-    for (int64_t p = eptr[e] + lane; p < p1; p += 32) {
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
       int b = part[pins[p]];
       if ((unsigned)b < (unsigned)k) atomicAdd(&h[b], 1);
       else err |= kErrPartRange;
@@ -193,6 +200,37 @@ __global__ void __launch_bounds__(256) k_pincounts(const int64_t *eptr, const in
       }
     }
     __syncwarp();
+  }
+  if (err) atomicOr(&cnt->err, err);
+}
+
+// The edges longer than one segment: a thread block per segment of at most
+// kSegPins pins (the afterburner's segment list, whose slot field is >= 0 for
+// exactly these edges) counts the blocks of its pins in shared memory and adds
+// the counts into the edge's row, cleared by k_pincounts: one atomic per block
+// of the partition that the segment touches.
+__global__ void __launch_bounds__(256) k_pincounts_seg(const int64_t *eptr, const int32_t *pins, const int32_t *part,
+                                                       const int4 *seg, int32_t nseg, int32_t k, int32_t *phi,
+                                                       Counters *cnt) {
+  __shared__ int s_h[kMaxK];
+  int err = 0;
+  for (int i = blockIdx.x; i < nseg; i += gridDim.x) {
+    const int4 sg = seg[i];  // edge, first pin (offset in the edge), pins, slot
+    if (sg.w < 0) continue;  // a one-segment edge: counted by k_pincounts (block-uniform)
+    for (int b = threadIdx.x; b < k; b += blockDim.x) s_h[b] = 0;
+    __syncthreads();
+    const int64_t p0 = eptr[sg.x] + sg.y;
+#pragma unroll 4
+    for (int j = threadIdx.x; j < sg.z; j += blockDim.x) {
+      const int b = part[pins[p0 + j]];
+      if ((unsigned)b < (unsigned)k) atomicAdd(&s_h[b], 1);
+      else err |= kErrPartRange;
+    }
+    __syncthreads();
+    int32_t *row = phi + (int64_t)sg.x * k;
+    for (int b = threadIdx.x; b < k; b += blockDim.x)
+      if (s_h[b]) atomicAdd(&row[b], s_h[b]);
+    __syncthreads();
   }
   if (err) atomicOr(&cnt->err, err);
 }
@@ -222,13 +260,15 @@ __global__ void k_block_weights(const int32_t *part, const int32_t *vwgt, int32_
   if (err) atomicOr(&cnt->err, err);
 }
 
-// Bitmasks of Lambda(e) and of the blocks with >= 2 pins from a dense phi (warp per edge).
+// Bitmasks of Lambda(e) and of the blocks with >= 2 pins from a dense phi
+// (warp per edge): of every edge, or of the m edges listed in `list`.
 __global__ void __launch_bounds__(256) k_masks_from_phi(const int32_t *phi, int32_t m, int32_t k, int32_t kwp,
-                                                        uint32_t *mask) {
+                                                        uint32_t *mask, const int32_t *list) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t e = gw; e < m; e += nw) {
+  for (int64_t i = gw; i < m; i += nw) {
+    const int64_t e = list ? list[i] : i;
     const int32_t *row = phi + e * k;
     for (int q = 0; q < kwp; ++q) {
       int b = q * 32 + lane;
@@ -346,9 +386,9 @@ static cudaError_t stable_partition(jet_ctx *c, const uint8_t *code, int32_t cou
   const int bs = 1024;
   const int nb = (int)((count + bs - 1) / bs);
   int32_t *d_cnt = nullptr, *d_off = nullptr;
-  cudaError_t e = cudaMallocAsync(&d_cnt, sizeof(int32_t) * kClasses * nb, c->stream);
+  cudaError_t e = jet::pool_alloc(&d_cnt, sizeof(int32_t) * kClasses * nb, c->stream);
   if (e != cudaSuccess) return e;
-  e = cudaMallocAsync(&d_off, sizeof(int32_t) * kClasses * nb, c->stream);
+  e = jet::pool_alloc(&d_off, sizeof(int32_t) * kClasses * nb, c->stream);
   if (e != cudaSuccess) { cudaFreeAsync(d_cnt, c->stream); return e; }
   std::vector<int32_t> h((size_t)kClasses * nb);
   k_class_count<<<nb, bs, 0, c->stream>>>(code, count, d_cnt);
@@ -386,7 +426,7 @@ cudaError_t launch_classify(jet_ctx *c, const int64_t *wdeg) {
   // of m + (mid count) entries: [tiny | mid | big | room for deferred mid edges]
   int64_t mx = c->n > c->m ? c->n : c->m;
   uint8_t *code = nullptr;
-  cudaError_t e = cudaMallocAsync(&code, mx > 0 ? mx : 1, c->stream);
+  cudaError_t e = jet::pool_alloc(&code, mx > 0 ? mx : 1, c->stream);
   if (e != cudaSuccess) return e;
   int32_t t[kClasses];
   if (c->n > 0) {
@@ -432,6 +472,13 @@ cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int6
     k_pincounts<<<grid_for((int64_t)c->m * 32, threads, c->launch_sms), threads, smem, s>>>(
         c->eptr, c->pins, part, c->m, c->k, c->kwp, phi, c->mask, c->cnt);
     ++c->kernel_launches;
+    if (c->n_slots > 0) {  // edges longer than one segment
+      k_pincounts_seg<<<grid_for(c->n_seg, 1, c->launch_sms), 256, 0, s>>>(c->eptr, c->pins, part, c->ab_seg,
+                                                                           c->n_seg, c->k, phi, c->cnt);
+      k_masks_from_phi<<<grid_for((int64_t)c->n_slots * 32, 256, c->launch_sms), 256, 0, s>>>(
+          phi, c->n_slots, c->k, c->kwp, c->mask, c->ab_slot_edge);
+      c->kernel_launches += 2;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (c->n > 0) {
@@ -447,7 +494,7 @@ cudaError_t launch_pincounts(jet_ctx *c, const int32_t *part, int32_t *phi, int6
 cudaError_t launch_masks_from_phi(jet_ctx *c, const int32_t *phi) {
   if (c->m > 0) {
     k_masks_from_phi<<<grid_for((int64_t)c->m * 32, 256, c->launch_sms), 256, 0, c->stream>>>(phi, c->m, c->k, c->kwp,
-                                                                                            c->mask);
+                                                                                            c->mask, nullptr);
     ++c->kernel_launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -29,7 +29,7 @@ EXPORTS = ("jet_ctx_create", "jet_ctx_destroy", "jet_last_error", "jet_build_pin
            "jet_job_footprint", "jet_server_create", "jet_server_submit", "jet_server_wait", "jet_server_load",
            "jet_server_last_error", "jet_server_destroy", "jet_profile_work", "jet_quotient_schedule",
            "jet_uncoarsen", "jet_cluster", "jet_contract", "jet_set_graph_path", "jet_rounds_host",
-           "jet_batch_set_team", "jet_batch_get_team", "jet_batch_autotune")
+           "jet_batch_set_team", "jet_batch_get_team", "jet_batch_autotune", "jet_release_memory")
 
 PROF_FAMILIES = ("pincounts", "candidates", "afterburner", "approve", "apply", "rebalance_targets",
                  "rebalance_select", "rebalance_control", "objective", "other")
@@ -395,6 +395,11 @@ def jet_set_graph_mode(ctx: Ctx, enable: bool = True):
 def jet_set_graph_path(ctx: Ctx, enable: bool = True):
     """Graph path (every edge two distinct pins): neighbour blocks instead of phi; phi is not maintained."""
     _check(load_library().jet_set_graph_path(ctx.handle, 1 if enable else 0), ctx)
+
+
+def jet_release_memory():
+    """Return the device memory the library keeps in its pools (one per device) to the driver."""
+    _check(load_library().jet_release_memory())
 
 
 def jet_profile_enable(ctx: Ctx, enable: bool = True):

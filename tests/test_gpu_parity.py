@@ -242,6 +242,18 @@ def test_rounds_host_entry_point(name):
     assert ei.value.code == -1
 
 
+def test_release_memory_between_host_calls():
+    """The library's pools may be emptied between calls: a host-buffer call after jet_release_memory gives the
+    same partition and statistics as before it."""
+    hg, k, part = INSTANCES["random10k_k8"]
+    p1, p2 = part.copy(), part.copy()
+    st1 = jet.jet_rounds_host(hg, jet.params(k), (3, 4), 2, p1)
+    jet.jet_release_memory()
+    st2 = jet.jet_rounds_host(hg, jet.params(k), (3, 4), 2, p2)
+    jet.jet_release_memory()
+    assert np.array_equal(p1, p2) and st1 == st2
+
+
 def test_errors_are_reported():
     hg, k, part, ctx = setup("random10k_k8")
     st = jet.JetState(ctx, part)
