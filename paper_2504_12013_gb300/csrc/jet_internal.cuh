@@ -309,6 +309,21 @@ long long team_pins(TeamPlan *p, int32_t i);
 // Sets the message returned by jet_last_error(NULL) (for entry points without a context).
 void set_global_error(const char *fmt, ...);
 
+// The lanes of the warp whose value equals this lane's (what __match_any_sync
+// returns) for values below 2^BITS, from BITS ballots: every lane calls it.
+// For a few bits the ballots are cheaper than the general match.
+template <int BITS>
+__device__ __forceinline__ unsigned match_bits(unsigned x) {
+  unsigned peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < BITS; ++b) {
+    const bool bit = (x >> b) & 1u;
+    const unsigned v = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? v : ~v;
+  }
+  return peers;
+}
+
 // Device memory of the library: stream-ordered allocations from a pool of its
 // own, one per device, which keeps the memory the library frees for its next
 // calls instead of returning it to the driver at each synchronization (a

@@ -165,9 +165,10 @@ __device__ __forceinline__ void count_work(Counters *cnt, unsigned long long ove
 
 // Top digit of the selection key K(v) = hi << vbits | v (the first radix
 // level), added with c(v) into the (block, digit) histogram: one atomic per
-// distinct (block, digit) in the warp.  Every lane of the warp calls it.
+// record.  (Grouping the warp's records by (block, digit) with
+// __match_any_sync first, one atomic per group, made the rebalancing rounds
+// slower: the vote costs more than the atomics it saves.)
 __device__ __forceinline__ void rb_first_level(const CandArgs &a, bool rec, int s, uint64_t hi, int v, int32_t c) {
-  const int lane = threadIdx.x & 31;
   const int lo = a.rb_tbits - a.rb_digit > 0 ? a.rb_tbits - a.rb_digit : 0;
   int d = 0;
   if (rec) {
@@ -179,11 +180,7 @@ __device__ __forceinline__ void rb_first_level(const CandArgs &a, bool rec, int 
       d = (int)((K >> lo) & ((1ull << (a.rb_tbits - lo)) - 1));
     }
   }
-  const int code = rec ? (s << 16) | d : -1 - lane;
-  const unsigned grp = __match_any_sync(kFull, code);
-  const unsigned sum = __reduce_add_sync(grp, rec ? (unsigned)c : 0u);
-  if (rec && lane == __ffs(grp) - 1)
-    atomicAdd(&a.rb_hist[((int64_t)s << a.rb_digit) + d], (unsigned long long)sum);
+  if (rec) atomicAdd(&a.rb_hist[((int64_t)s << a.rb_digit) + d], (unsigned long long)c);
 }
 
 template <int KWP>

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long 
     const bool have = i < n;
     const unsigned long long key = have ? in[i] : 0ull;
     const int d = have ? (int)((key >> shift) & 255) : 256;
-    const unsigned peers = __match_any_sync(kFull, d);
+    const unsigned peers = match_bits<9>((unsigned)d);  // d <= 256
     const int rank = __popc(peers & ((1u << lane) - 1));
     if (have && rank == 0) s_wc[wid][d] = __popc(peers);
     __syncthreads();

@@ -211,10 +211,9 @@ __device__ __forceinline__ KT rb_prefix(const RbBlock &r) {
 }
 
 // One level: digit = bits [lo, lo + w) of K(v) for the records whose higher bits
-// equal their block's prefix; weights aggregated per warp and (block, digit).
+// equal their block's prefix; one atomic per matching record.
 template <class KT>
 __global__ void __launch_bounds__(256) k_rb_level(RbArgs a, int lo, int w) {
-  const int lane = threadIdx.x & 31;
   const int up = lo + w;
   const KT dmask = ((KT)1 << w) - 1;
   const long long nrec = (long long)a.cnt->n_rec;
@@ -234,11 +233,7 @@ __global__ void __launch_bounds__(256) k_rb_level(RbArgs a, int lo, int w) {
         c = (unsigned)(ct >> 16);
       }
     }
-    if (!__any_sync(kFull, m)) continue;  // after the first level few records still match: skip the grouping
-    const int code = m ? (b << 16) | d : -1 - lane;
-    const unsigned grp = __match_any_sync(kFull, code);
-    const unsigned sum = __reduce_add_sync(grp, c);
-    if (m && lane == __ffs(grp) - 1) atomicAdd(&a.hist[(int64_t)b * a.bins + d], (unsigned long long)sum);
+    if (m) atomicAdd(&a.hist[(int64_t)b * a.bins + d], (unsigned long long)c);
   }
 }
 

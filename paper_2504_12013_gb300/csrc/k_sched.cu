@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(32) k_schedule(const uint32_t *q, int32_t k, i
     for (int c0 = 0; c0 < k; c0 += 32) {
       const int j = c0 + lane;
       const int key = j < k ? 255 - s_deg[j] : 256 + lane;
-      const unsigned peers = __match_any_sync(kFull, key);
+      const unsigned peers = match_bits<9>((unsigned)key);  // key <= 256 + 31
       const int rank = __popc(peers & lt);
       const int base = j < k ? s_cnt[key] : 0;
       __syncwarp();

@@ -104,6 +104,7 @@ __global__ void k_validate_degrees(const int64_t *vptr, const int32_t *inc, cons
 // ---------------------------------------------------------------- classes
 // Stable partition of ids [0, count) by class code (0 .. kClasses-1).
 constexpr int kClasses = 24;
+static_assert(kClasses < 32, "class codes and the no-class code fit match_bits<5>");
 
 __global__ void k_class_count(const uint8_t *code, int32_t count, int32_t *blk_counts) {
   __shared__ int s_c[kClasses];
@@ -111,7 +112,7 @@ __global__ void k_class_count(const uint8_t *code, int32_t count, int32_t *blk_c
   __syncthreads();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int c = i < count ? code[i] : kClasses;
-  const unsigned grp = __match_any_sync(kFull, c);
+  const unsigned grp = match_bits<5>((unsigned)c);  // c <= kClasses < 32
   if (c < kClasses && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&s_c[c], __popc(grp));
   __syncthreads();
   if (threadIdx.x < kClasses) blk_counts[blockIdx.x * kClasses + threadIdx.x] = s_c[threadIdx.x];
@@ -124,7 +125,7 @@ __global__ void k_class_scatter(const uint8_t *code, int32_t count, const int32_
   __syncthreads();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int c = i < count ? code[i] : kClasses;
-  const unsigned grp = __match_any_sync(kFull, c);
+  const unsigned grp = match_bits<5>((unsigned)c);  // c <= kClasses < 32
   const unsigned rank = __popc(grp & ((1u << lane) - 1));
   if (c < kClasses && lane == __ffs(grp) - 1) s_w[w][c] = __popc(grp);
   __syncthreads();
