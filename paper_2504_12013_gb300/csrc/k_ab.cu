@@ -142,6 +142,9 @@ constexpr int kAbWarps = 8;
 // Warp per edge (32 < |e| <= 32 PPL): the per-block form of the replay in
 // shared memory, one table per warp: max key of the departures and min key
 // of the arrivals of every block, and the blocks holding a non-candidate pin.
+// A 64-bit key is kept as two 32-bit words, found in two rounds of 32-bit
+// shared-memory atomics (the high words, then the low words of the keys
+// whose high word is the extreme one): cheaper than 64-bit atomic max / min.
 // A key is never 0 (its high word is INT32_MAX - gain >= 1), so max = 0 means
 // "no departure" and min = ~0 "no arrival".  Only the entries (and mask
 // words) of blocks some candidate of the edge leaves or enters are reset and
@@ -153,11 +156,11 @@ constexpr int kAbWarps = 8;
 // current edge is decided.
 template <int PPL>
 __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
-  extern __shared__ unsigned long long s_tab[];  // per warp: maxd[k], mina[k]
+  extern __shared__ unsigned long long s_tab[];  // per warp: the high and low words of maxd[k], mina[k]
   __shared__ uint32_t s_nm[kAbWarps][kMaxK / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long *maxd = s_tab + (size_t)w * 2 * a.k;
-  unsigned long long *mina = maxd + a.k;
+  uint32_t *dh = reinterpret_cast<uint32_t *>(s_tab + (size_t)w * 2 * a.k);
+  uint32_t *dl = dh + a.k, *ah = dl + a.k, *al = ah + a.k;
   uint32_t *nm = s_nm[w];
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -187,10 +190,8 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
       if (r[q]) {
         any = true;
         const int s = cand_s(r[q]), t = cand_t(r[q]);
-        maxd[s] = 0ull;
-        mina[s] = ~0ull;
-        maxd[t] = 0ull;
-        mina[t] = ~0ull;
+        dh[s] = 0u; dl[s] = 0u; ah[s] = ~0u; al[s] = ~0u;
+        dh[t] = 0u; dl[t] = 0u; ah[t] = ~0u; al[t] = ~0u;
         nm[s >> 5] = 0u;
         nm[t >> 5] = 0u;
       }
@@ -200,12 +201,21 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
 #pragma unroll
     for (int q = 0; q < PPL; ++q) {
       if (r[q]) {
-        const uint64_t K = cand_key(r[q], v[q]);
-        atomicMax(&maxd[cand_s(r[q])], (unsigned long long)K);
-        atomicMin(&mina[cand_t(r[q])], (unsigned long long)K);
+        const uint32_t kh = (uint32_t)(cand_key(r[q], v[q]) >> 32);
+        atomicMax(&dh[cand_s(r[q])], kh);
+        atomicMin(&ah[cand_t(r[q])], kh);
       } else if (b[q] >= 0) {
         atomicOr(&nm[b[q] >> 5], 1u << (b[q] & 31));
       }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {  // the low words among the keys with the extreme high word
+      if (!r[q]) continue;
+      const uint32_t kh = (uint32_t)(cand_key(r[q], v[q]) >> 32);
+      const int s = cand_s(r[q]), t = cand_t(r[q]);
+      if (dh[s] == kh) atomicMax(&dl[s], (uint32_t)v[q]);
+      if (ah[t] == kh) atomicMin(&al[t], (uint32_t)v[q]);
     }
     __syncwarp();
     const int wt = a.ewgt[e];
@@ -214,11 +224,13 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp(AbArgs a) {
       if (!r[q]) continue;
       const uint64_t K = cand_key(r[q], v[q]);
       const int s = cand_s(r[q]), t = cand_t(r[q]);
+      const uint64_t maxd_s = ((uint64_t)dh[s] << 32) | dl[s], mina_s = ((uint64_t)ah[s] << 32) | al[s];
+      const uint64_t maxd_t = ((uint64_t)dh[t] << 32) | dl[t], mina_t = ((uint64_t)ah[t] << 32) | al[t];
       int delta = 0;
       // last departure from s, no arrival to s before it, no pin of e staying in s
-      if (maxd[s] == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina[s] == ~0ull || K < mina[s])) delta += wt;
+      if (maxd_s == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina_s == ~0ull || K < mina_s)) delta += wt;
       // first arrival to t, every departure from t before it, no pin of e staying in t
-      if (mina[t] == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd[t] < K) delta -= wt;
+      if (mina_t == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd_t < K) delta -= wt;
       if (delta) atomicAdd(&a.rg[v[q]], delta);
     }
     __syncwarp();
@@ -236,11 +248,11 @@ template <int G>
 __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp_small(AbArgs a) {
   static_assert(G == 16 || G == 32, "a group is a half warp or a warp");
   constexpr int kGroups = kAbWarps * (32 / G);
-  extern __shared__ unsigned long long s_tab[];  // per group: maxd[k], mina[k]
+  extern __shared__ unsigned long long s_tab[];  // per group: the high and low words of maxd[k], mina[k]
   __shared__ uint32_t s_nm[kGroups][kMaxK / 32];
   const int li = threadIdx.x % G, grp = threadIdx.x / G;
-  unsigned long long *maxd = s_tab + (size_t)grp * 2 * a.k;
-  unsigned long long *mina = maxd + a.k;
+  uint32_t *dh = reinterpret_cast<uint32_t *>(s_tab + (size_t)grp * 2 * a.k);
+  uint32_t *dl = dh + a.k, *ah = dl + a.k, *al = ah + a.k;
   uint32_t *nm = s_nm[grp];
   const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
   const long long nw = (gridDim.x * (long long)blockDim.x) / G;
@@ -294,29 +306,35 @@ __global__ void __launch_bounds__(kAbWarps * 32) k_ab_warp_small(AbArgs a) {
     const uint64_t r = r0;
     const int s = cand_s(r), t = cand_t(r);
     if (r) {
-      maxd[s] = 0ull;
-      mina[s] = ~0ull;
-      maxd[t] = 0ull;
-      mina[t] = ~0ull;
+      dh[s] = 0u; dl[s] = 0u; ah[s] = ~0u; al[s] = ~0u;
+      dh[t] = 0u; dl[t] = 0u; ah[t] = ~0u; al[t] = ~0u;
       nm[s >> 5] = 0u;
       nm[t >> 5] = 0u;
     }
     if (__any_sync(kFull, r != 0)) {
       __syncwarp();
       const uint64_t K = cand_key(r, v0);
+      const uint32_t kh = (uint32_t)(K >> 32), kl = (uint32_t)K;
       if (r) {
-        atomicMax(&maxd[s], (unsigned long long)K);
-        atomicMin(&mina[t], (unsigned long long)K);
+        atomicMax(&dh[s], kh);
+        atomicMin(&ah[t], kh);
       } else if (v0 >= 0) {
         const int b = b0 & 255;
         atomicOr(&nm[b >> 5], 1u << (b & 31));
       }
       __syncwarp();
+      if (r) {  // the low words among the keys with the extreme high word
+        if (dh[s] == kh) atomicMax(&dl[s], kl);
+        if (ah[t] == kh) atomicMin(&al[t], kl);
+      }
+      __syncwarp();
       if (r) {
         const int wt = a.ewgt[e0];
+        const uint64_t maxd_s = ((uint64_t)dh[s] << 32) | dl[s], mina_s = ((uint64_t)ah[s] << 32) | al[s];
+        const uint64_t maxd_t = ((uint64_t)dh[t] << 32) | dl[t], mina_t = ((uint64_t)ah[t] << 32) | al[t];
         int delta = 0;
-        if (maxd[s] == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina[s] == ~0ull || K < mina[s])) delta += wt;
-        if (mina[t] == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd[t] < K) delta -= wt;
+        if (maxd_s == K && !((nm[s >> 5] >> (s & 31)) & 1u) && (mina_s == ~0ull || K < mina_s)) delta += wt;
+        if (mina_t == K && !((nm[t >> 5] >> (t & 31)) & 1u) && maxd_t < K) delta -= wt;
         if (delta) atomicAdd(&a.rg[v0], delta);
       }
       __syncwarp();
@@ -362,15 +380,17 @@ __device__ __forceinline__ void ab_decide(const AbArgs &a, int b, unsigned long 
 __global__ void __launch_bounds__(kSegThreads) k_ab_block(SegArgs sa) {
   const AbArgs &a = sa.ab;
   extern __shared__ unsigned long long s_mem[];
-  unsigned long long *s_maxd = s_mem;        // k: max key among departures
-  unsigned long long *s_mina = s_mem + a.k;  // k: min key among arrivals
+  // high and low words of the max key among departures (dh, dl) and of the min key among arrivals (ah, al)
+  uint32_t *dh = reinterpret_cast<uint32_t *>(s_mem), *dl = dh + a.k, *ah = dl + a.k, *al = ah + a.k;
   __shared__ uint32_t s_nm[kMaxK / 32];      // blocks holding a non-candidate pin
   constexpr int kPer = kSegPins / kSegThreads;
   for (int i = blockIdx.x; i < sa.nseg; i += gridDim.x) {
     const int4 sg = sa.seg[i];
     for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
-      s_maxd[b] = 0ull;
-      s_mina[b] = ~0ull;
+      dh[b] = 0u;
+      dl[b] = 0u;
+      ah[b] = ~0u;
+      al[b] = ~0u;
     }
     if (threadIdx.x < kMaxK / 32) s_nm[threadIdx.x] = 0;
     __syncthreads();
@@ -388,9 +408,9 @@ __global__ void __launch_bounds__(kSegThreads) k_ab_block(SegArgs sa) {
     for (int q = 0; q < kPer; ++q) {
       if (v[q] < 0) continue;
       if (r[q]) {
-        const uint64_t K = cand_key(r[q], v[q]);
-        atomicMax(&s_maxd[cand_s(r[q])], (unsigned long long)K);
-        atomicMin(&s_mina[cand_t(r[q])], (unsigned long long)K);
+        const uint32_t kh = (uint32_t)(cand_key(r[q], v[q]) >> 32);
+        atomicMax(&dh[cand_s(r[q])], kh);
+        atomicMin(&ah[cand_t(r[q])], kh);
       } else {
         const int b = a.part[v[q]] & 255;
         const uint32_t bit = 1u << (b & 31);
@@ -398,15 +418,27 @@ __global__ void __launch_bounds__(kSegThreads) k_ab_block(SegArgs sa) {
       }
     }
     __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {  // the low words among the keys with the extreme high word
+      if (!r[q]) continue;
+      const uint32_t kh = (uint32_t)(cand_key(r[q], v[q]) >> 32), kl = (uint32_t)v[q];
+      const int s = cand_s(r[q]), t = cand_t(r[q]);
+      if (dh[s] == kh) atomicMax(&dl[s], kl);
+      if (ah[t] == kh) atomicMin(&al[t], kl);
+    }
+    __syncthreads();
     if (sg.w < 0) {  // the whole edge: decide here
       const int w = a.ewgt[sg.x];
       for (int b = threadIdx.x; b < a.k; b += blockDim.x)
-        ab_decide(a, b, s_maxd[b], s_mina[b], (s_nm[b >> 5] >> (b & 31)) & 1u, w);
+        ab_decide(a, b, ((unsigned long long)dh[b] << 32) | dl[b], ((unsigned long long)ah[b] << 32) | al[b],
+                  (s_nm[b >> 5] >> (b & 31)) & 1u, w);
     } else {  // one segment of a longer edge: merge into its slot
       unsigned long long *tmax = sa.tab + (size_t)sg.w * 2 * a.k, *tmin = tmax + a.k;
       for (int b = threadIdx.x; b < a.k; b += blockDim.x) {
-        if (s_maxd[b] != 0ull) atomicMax(&tmax[b], s_maxd[b]);
-        if (s_mina[b] != ~0ull) atomicMin(&tmin[b], s_mina[b]);
+        const unsigned long long md = ((unsigned long long)dh[b] << 32) | dl[b];
+        const unsigned long long ma = ((unsigned long long)ah[b] << 32) | al[b];
+        if (md != 0ull) atomicMax(&tmax[b], md);
+        if (ma != ~0ull) atomicMin(&tmin[b], ma);
       }
       if (threadIdx.x < kMaxK / 32 && s_nm[threadIdx.x]) atomicOr(&sa.nmw[sg.w * 8 + threadIdx.x], s_nm[threadIdx.x]);
     }
