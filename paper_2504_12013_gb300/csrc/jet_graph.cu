@@ -317,8 +317,11 @@ int build_batch(jet_batch *b, const int32_t *tau, int32_t n_tau, int32_t limit, 
     c->capturing = 1;
     e = jet::capture_refine(c, tau, n_tau, limit, part[i], phi[i], block_w[i], &b->res_host[i]);
     c->capturing = 0;
-    if (e == cudaSuccess) e = cudaEventRecord(b->join, c->cap_stream[0]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join, 0);
+    // join the branch back even after a failed capture, so that the origin's capture ends with every
+    // forked stream joined (and is then discarded) instead of leaving a stream in an open capture
+    cudaError_t ej = cudaEventRecord(b->join, c->cap_stream[0]);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->origin, b->join, 0);
+    if (e == cudaSuccess) e = ej;
     if (e != cudaSuccess) rc = bfail(b, JET_ERR_CUDA, c->err[0] ? c->err : "batch capture", e);
   }
   cudaGraph_t done = nullptr;
