@@ -927,9 +927,16 @@ def roofline_block(args, r, hbm, peak_src):
     def family_roofline(fam, kernel, nbytes, traffic_kernel):
         fms, fl = prof[fam]["ms"], prof[fam]["launches"]
         ach = nbytes / (fms / 1e3) / 1e9 if fms > 0 else None
+        tr = ncu_traffic(workload, traffic_kernel) if traffic_kernel else None
+        # the DRAM bytes the family moves at sector granularity (ncu mean per launch x launches) over its time
+        tr_ach = tr * fl / (fms / 1e3) / 1e9 if tr and fms > 0 else None
         return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": (ach / hbm) if ach else None,
-                "traffic": ncu_traffic(workload, traffic_kernel) if traffic_kernel else None,
+                "traffic": tr,
+                "traffic_achieved": tr_ach, "traffic_frac": (tr_ach / hbm) if tr_ach else None,
+                "traffic_frac_note": "measured DRAM bytes per launch (ncu, cold L2) x launches per step over the "
+                                     "family's replay time: the share of HBM bandwidth the kernels use at sector "
+                                     "granularity, beside frac, which counts algorithmic bytes only",
                 "traffic_note": (f"mean DRAM bytes per launch, cold L2 (profiles/{traffic_kernel}.md); null when the "
                                  "kernel source changed since that capture" if traffic_kernel
                                  else "no capture for this kernel"),
